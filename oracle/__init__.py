@@ -1,0 +1,246 @@
+"""Plain CPU oracle of the Accessibility Field hot path (ctypes over af_oracle.c).
+
+TEST INFRASTRUCTURE. The oracle is the correctness reference for the CUDA
+path: scan-centric TSDF integration with positive clamping (Sec. 3.2), the
+ray-cleared free band (Sec. 3.4), the weight cap (Sec. 3.6), the occupied /
+known view, and accessibility scoring against tool and corridor kernels
+(Sec. 3.4, 3.5). Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import it. It imports nothing from the
+product package and the product imports nothing from here.
+
+All arithmetic lives in ``af_oracle.c``; this module only marshals arrays.
+Parity status of each function is recorded in the module docstrings of the
+tests that pin it (``tests/test_oracle_*.py``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "af_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+UNSCORED, ACCESSIBLE, BLOCKED = 0, 1, 2
+KERNEL_TOOL, KERNEL_CORRIDOR = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile af_oracle.c with strict IEEE single-precision semantics."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Config(C.Structure):
+    _fields_ = [("v", C.c_float), ("tau", C.c_float), ("r_c", C.c_float),
+                ("cone_cos", C.c_float), ("range_min", C.c_float),
+                ("range_max", C.c_float), ("clear_lo", C.c_float),
+                ("clear_hi", C.c_float), ("cube_radius", C.c_int32),
+                ("clear_samples", C.c_int32), ("w_min", C.c_uint32),
+                ("w_cap", C.c_uint32), ("dom_min", C.c_int32 * 3),
+                ("dom_size", C.c_int32 * 3)]
+
+
+class _Tool(C.Structure):
+    _fields_ = [("radius", C.c_float), ("length", C.c_float),
+                ("self_excl", C.c_float), ("corr_radius", C.c_float),
+                ("corr_length", C.c_float), ("cos_theta_max", C.c_float),
+                ("n_c", C.c_uint32), ("strict", C.c_int32)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        lib.or_map_new.restype = P
+        lib.or_map_new.argtypes = [C.POINTER(_Config)]
+        lib.or_map_free.argtypes = [P]
+        lib.or_integrate.restype = C.c_int64
+        lib.or_integrate.argtypes = [P, P, C.c_int64, P]
+        lib.or_get_voxel.restype = C.c_int
+        lib.or_get_voxel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32,
+                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
+                                     C.POINTER(C.c_int32)]
+        lib.or_set_voxel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32,
+                                     C.c_uint64, C.c_uint32, C.c_int32]
+        lib.or_set_voxels.argtypes = [P, C.c_int64, P, P, P, P]
+        lib.or_voxel_count.restype = C.c_int64
+        lib.or_voxel_count.argtypes = [P]
+        lib.or_export.argtypes = [P, P, P, P, P, P, P]
+        lib.or_occ.restype = C.c_int
+        lib.or_occ.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
+        lib.or_known.restype = C.c_int
+        lib.or_known.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
+        lib.or_kernel_offsets.restype = C.c_int64
+        lib.or_kernel_offsets.argtypes = [C.POINTER(_Tool), C.c_float, P, C.c_int, P,
+                                          C.c_int64]
+        lib.or_arm_offsets.argtypes = [C.c_float, C.c_float, P, P]
+        lib.or_score.argtypes = [P, C.POINTER(_Tool), P, C.c_int32, P, P, C.c_int64,
+                                 P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class Config:
+    """Map parameters (Sec. 3.2-3.6); voxel box = [dom_min, dom_min + dom_size)."""
+    v: float
+    tau: float
+    r_c: float
+    cube_radius: int
+    clear_samples: int
+    dom_min: tuple
+    dom_size: tuple
+    cone_cos: float = 0.95
+    range_min: float = 0.1
+    range_max: float = 40.0
+    clear_lo: float = 1.0
+    clear_hi: float = 2.25
+    w_min: int = 3
+    w_cap: int = 2000
+
+    def _c(self) -> _Config:
+        c = _Config()
+        for k in ("v", "tau", "r_c", "cone_cos", "range_min", "range_max",
+                  "clear_lo", "clear_hi", "cube_radius", "clear_samples",
+                  "w_min", "w_cap"):
+            setattr(c, k, getattr(self, k))
+        c.dom_min[:] = [int(x) for x in self.dom_min]
+        c.dom_size[:] = [int(x) for x in self.dom_size]
+        return c
+
+
+@dataclass
+class Tool:
+    """Cylinder tool with a coaxial approach corridor (Sec. 3.4)."""
+    radius: float
+    length: float
+    self_excl: float
+    corr_radius: float
+    corr_length: float
+    cos_theta_max: float = 0.0
+    n_c: int = 5
+    strict: int = 0
+
+    def _c(self) -> _Tool:
+        t = _Tool()
+        for k in ("radius", "length", "self_excl", "corr_radius", "corr_length",
+                  "cos_theta_max", "n_c", "strict"):
+            setattr(t, k, getattr(self, k))
+        return t
+
+
+class Map:
+    """Voxel map of the oracle: S (units of 2^-20 m), w, cleared per voxel."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        self._cc = cfg._c()
+        self._lib = _load()
+        self._h = self._lib.or_map_new(C.byref(self._cc))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.or_map_free(self._h)
+            self._h = None
+
+    def integrate(self, pts: np.ndarray, pose: np.ndarray | None = None) -> int:
+        pts = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 3)
+        pose = np.eye(4, dtype=np.float32) if pose is None else \
+            np.ascontiguousarray(pose, dtype=np.float32).reshape(4, 4)
+        return int(self._lib.or_integrate(self._h, _ptr(pts), len(pts), _ptr(pose)))
+
+    def voxel(self, i: int, j: int, k: int):
+        S, w, cl = C.c_uint64(), C.c_uint32(), C.c_int32()
+        self._lib.or_get_voxel(self._h, i, j, k, C.byref(S), C.byref(w), C.byref(cl))
+        return int(S.value), int(w.value), int(cl.value)
+
+    def set_voxel(self, i: int, j: int, k: int, S: int, w: int, cleared: int = 0):
+        self._lib.or_set_voxel(self._h, i, j, k, S, w, cleared)
+
+    def set_voxels(self, ijk: np.ndarray, S: np.ndarray, w: np.ndarray,
+                   cleared: np.ndarray | None = None):
+        ijk = np.ascontiguousarray(ijk, np.int32).reshape(-1, 3)
+        n = len(ijk)
+        S = np.ascontiguousarray(np.broadcast_to(S, (n,)), np.uint64)
+        w = np.ascontiguousarray(np.broadcast_to(w, (n,)), np.uint32)
+        cl = np.zeros(n, np.uint8) if cleared is None else \
+            np.ascontiguousarray(np.broadcast_to(cleared, (n,)), np.uint8)
+        self._lib.or_set_voxels(self._h, n, _ptr(ijk), _ptr(S), _ptr(w), _ptr(cl))
+
+    def occ(self, i: int, j: int, k: int) -> int:
+        return int(self._lib.or_occ(self._h, i, j, k))
+
+    def known(self, i: int, j: int, k: int) -> int:
+        return int(self._lib.or_known(self._h, i, j, k))
+
+    def __len__(self):
+        return int(self._lib.or_voxel_count(self._h))
+
+    def export(self) -> dict:
+        """All stored voxels, sorted by (z, y, x)."""
+        n = len(self)
+        ijk = np.zeros((n, 3), np.int32)
+        S = np.zeros(n, np.uint64)
+        w = np.zeros(n, np.uint32)
+        cl = np.zeros(n, np.uint8)
+        occ = np.zeros(n, np.uint8)
+        kn = np.zeros(n, np.uint8)
+        self._lib.or_export(self._h, _ptr(ijk), _ptr(S), _ptr(w), _ptr(cl), _ptr(occ),
+                            _ptr(kn))
+        order = np.lexsort((ijk[:, 0], ijk[:, 1], ijk[:, 2]))
+        return dict(ijk=ijk[order], S=S[order], w=w[order], cleared=cl[order],
+                    occ=occ[order], known=kn[order])
+
+    def score(self, tool: Tool, dirs: np.ndarray, pts: np.ndarray, normals: np.ndarray,
+              dir_scores: bool = False):
+        dirs = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+        pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
+        normals = np.ascontiguousarray(normals, np.float32).reshape(-1, 3)
+        m, G = len(pts), len(dirs)
+        label = np.zeros(m, np.uint8)
+        best = np.zeros(m, np.int16)
+        ds = np.zeros((m, G), np.int32) if dir_scores else None
+        tc = tool._c()
+        self._lib.or_score(self._h, C.byref(tc), _ptr(dirs), G, _ptr(pts), _ptr(normals), m,
+                           _ptr(label), _ptr(best), _ptr(ds) if ds is not None else None)
+        return (label, best, ds) if dir_scores else (label, best)
+
+
+def kernel_offsets(tool: Tool, v: float, u, which: int) -> np.ndarray:
+    """Voxel offsets of the tool (which=0) or corridor (which=1) kernel of u."""
+    lib = _load()
+    u = np.ascontiguousarray(u, np.float32).reshape(3)
+    tc = tool._c()
+    n = lib.or_kernel_offsets(C.byref(tc), v, _ptr(u), which, None, 0)
+    out = np.zeros((max(n, 1), 3), np.int32)
+    lib.or_kernel_offsets(C.byref(tc), v, _ptr(u), which, _ptr(out), n)
+    return out[:n]
+
+
+def arm_offsets(v: float, tau: float, u) -> np.ndarray:
+    """The three arm-path sample offsets (rows: 0.6, 1.25, 2.25 tau)."""
+    lib = _load()
+    u = np.ascontiguousarray(u, np.float32).reshape(3)
+    out = np.zeros((3, 3), np.int32)
+    lib.or_arm_offsets(C.c_float(v), C.c_float(tau), _ptr(u), _ptr(out))
+    return out

@@ -1,0 +1,475 @@
+/*
+ * af_oracle.c -- plain, single-threaded CPU statement of the Accessibility
+ * Field hot path: scan-centric TSDF integration with positive clamping
+ * (Sec. 3.2), the ray-cleared free band (Sec. 3.4), the weight cap
+ * (Sec. 3.6), the occupied / known view of the TSDF, and accessibility
+ * scoring of surface points against tool and corridor voxel kernels
+ * (Sec. 3.4, 3.5).
+ *
+ * TEST INFRASTRUCTURE. This file is the correctness reference that the CUDA
+ * path is compared against. Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product never does.
+ *
+ * It is written for a reader checking it against the paper, not for speed:
+ * one voxel at a time, one return at a time, one direction at a time, every
+ * direction scored in full (no early exits), a hash map of single voxels.
+ *
+ * Floating point. Every decision that yields an integer (the behind-surface
+ * cone, the quantised contribution, the voxel a point falls in) is taken in
+ * IEEE single precision, one correctly rounded operation at a time, in the
+ * order written here; build with -ffp-contract=off and without -ffast-math.
+ * The kernel tables are rasterised in double precision.
+ *
+ * Readings of the paper that this file implements (the paper leaves them
+ * open):
+ *  - The cone test of Sec. 3.2 EXCLUDES voxels with cos(theta) > cone_cos,
+ *    theta the angle between x - p and p - q: the narrow cone behind the
+ *    return along its ray. A voxel whose centre coincides with p is kept.
+ *  - The "+-tau cube" of Sec. 3.2 is the index-space cube of half-width
+ *    m = ceil(tau/v) around the voxel holding p (the (2m+1)^3 cube of
+ *    Sec. 3.6).
+ *  - Contributions are accumulated exactly: S += round(d * 2^20) in integers
+ *    and w += 1, so the result does not depend on the order of the returns.
+ *  - The weight cap of Sec. 3.6 is applied once at the end of each scan:
+ *    w > w_cap => S = floor(S * w_cap / w), w = w_cap.
+ *  - The cleared band (clear_lo*tau, clear_hi*tau] is sampled at N_s points
+ *    dist_j = clear_lo*tau + j*((clear_hi - clear_lo)*tau / N_s), j = 1..N_s,
+ *    along the unit vector from p toward q; the voxel holding each sample is
+ *    marked cleared.
+ *  - occ = (w >= 1) and (S < round(r_c * 2^20) * w), i.e. TSDF < r_c;
+ *    known = (w >= 1) or cleared.
+ *  - Approach directions are a table of unit vectors shared by both sides;
+ *    a direction is a candidate for a point when n . u > cos_theta_max.
+ *  - Tool kernel of direction u: voxel offsets o with e = o*v, a = e.u,
+ *    0 <= a <= L, |e - a u|^2 <= r^2 and |e|^2 > r_s^2. Corridor kernel:
+ *    L < a <= L + L_c and |e - a u|^2 <= r_corr^2.
+ *  - Arm samples: offsets floor(0.5 + (f*tau) * u_k / v), f in
+ *    {0.6, 1.25, 2.25}; blocked when occupied or unknown (Sec. 3.4).
+ *  - Corridor voxels block when occupied (unknown reads free, as for the
+ *    tool kernel); with `strict`, unknown corridor voxels block as well.
+ *  - Direction score: blocked (arm or corridor) => n_c + 1, else
+ *    min(count, n_c); best = lowest index of the minimum; ACCESSIBLE iff the
+ *    best score is below n_c; no candidate => BLOCKED with best = -1.
+ *  - Points whose voxel has w < w_min are UNSCORED with best = -1.
+ *  - The map is confined to a fixed box of voxels (the paper's bounded
+ *    window, Sec. 3.3): a return whose cube leaves the box is dropped, and
+ *    cleared-band samples outside the box are skipped. Voxels outside the
+ *    box read w = 0, not cleared.
+ */
+#include "af_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_SCALE 1048576.0f /* 2^20: fixed-point scale of the SDF sum */
+
+/* ------------------------------------------------------------------------- */
+/* Voxel store: open addressing over packed voxel indices.                   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    uint64_t key; /* 0 = empty slot */
+    uint64_t S;   /* sum of quantised contributions, units of 2^-20 m */
+    uint32_t w;   /* number of contributions */
+    int32_t cleared;
+} or_voxel;
+
+struct or_map {
+    or_config cfg;
+    or_voxel *slot;
+    uint64_t cap; /* power of two */
+    uint64_t count;
+};
+
+static uint64_t pack_key(int32_t ix, int32_t iy, int32_t iz) {
+    /* 21 bits per axis, offset so that the packed key is never 0. */
+    uint64_t x = (uint64_t)(uint32_t)(ix + (1 << 20)) & 0x1FFFFFu;
+    uint64_t y = (uint64_t)(uint32_t)(iy + (1 << 20)) & 0x1FFFFFu;
+    uint64_t z = (uint64_t)(uint32_t)(iz + (1 << 20)) & 0x1FFFFFu;
+    return (x | (y << 21) | (z << 42)) + 1u;
+}
+
+static void unpack_key(uint64_t key, int32_t *ix, int32_t *iy, int32_t *iz) {
+    uint64_t k = key - 1u;
+    *ix = (int32_t)(k & 0x1FFFFFu) - (1 << 20);
+    *iy = (int32_t)((k >> 21) & 0x1FFFFFu) - (1 << 20);
+    *iz = (int32_t)((k >> 42) & 0x1FFFFFu) - (1 << 20);
+}
+
+static uint64_t mix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    return k;
+}
+
+static or_voxel *find_slot(const or_map *m, uint64_t key) {
+    uint64_t h = mix64(key) & (m->cap - 1);
+    for (;;) {
+        or_voxel *s = &m->slot[h];
+        if (s->key == key || s->key == 0) return s;
+        h = (h + 1) & (m->cap - 1);
+    }
+}
+
+static void grow(or_map *m) {
+    or_voxel *old = m->slot;
+    uint64_t oldcap = m->cap;
+    m->cap *= 2;
+    m->slot = (or_voxel *)calloc(m->cap, sizeof(or_voxel));
+    for (uint64_t k = 0; k < oldcap; ++k)
+        if (old[k].key) *find_slot(m, old[k].key) = old[k];
+    free(old);
+}
+
+static or_voxel *voxel_ref(or_map *m, int32_t ix, int32_t iy, int32_t iz) {
+    if (2 * (m->count + 1) > m->cap) grow(m);
+    uint64_t key = pack_key(ix, iy, iz);
+    or_voxel *s = find_slot(m, key);
+    if (s->key == 0) {
+        s->key = key;
+        s->S = 0;
+        s->w = 0;
+        s->cleared = 0;
+        m->count++;
+    }
+    return s;
+}
+
+static const or_voxel *voxel_get(const or_map *m, int32_t ix, int32_t iy, int32_t iz) {
+    const or_voxel *s = find_slot(m, pack_key(ix, iy, iz));
+    return s->key ? s : NULL;
+}
+
+static int in_domain(const or_config *c, int32_t ix, int32_t iy, int32_t iz) {
+    return ix >= c->dom_min[0] && ix < c->dom_min[0] + c->dom_size[0] &&
+           iy >= c->dom_min[1] && iy < c->dom_min[1] + c->dom_size[1] &&
+           iz >= c->dom_min[2] && iz < c->dom_min[2] + c->dom_size[2];
+}
+
+or_map *or_map_new(const or_config *cfg) {
+    or_map *m = (or_map *)calloc(1, sizeof(or_map));
+    m->cfg = *cfg;
+    m->cap = 1024;
+    m->slot = (or_voxel *)calloc(m->cap, sizeof(or_voxel));
+    return m;
+}
+
+void or_map_free(or_map *m) {
+    if (!m) return;
+    free(m->slot);
+    free(m);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Scan-centric integration (Sec. 3.2, 3.4, 3.6).                            */
+/* ------------------------------------------------------------------------- */
+
+/* Voxel index of a coordinate: floor(c / v) in single precision. Returns 0
+ * when the index is not representable. */
+static int voxel_index(float c, float v, int32_t *out) {
+    float f = floorf(c / v);
+    if (!(f >= -1.0e9f && f <= 1.0e9f)) return 0;
+    *out = (int32_t)f;
+    return 1;
+}
+
+static float voxel_centre(int32_t i, float v) { return ((float)i + 0.5f) * v; }
+
+int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16]) {
+    const or_config *c = &m->cfg;
+    const float v = c->v, tau = c->tau;
+    const int32_t mr = c->cube_radius;
+    /* sensor origin q = translation of the world_from_sensor pose */
+    const float q[3] = {pose[3], pose[7], pose[11]};
+    int64_t accepted = 0;
+
+    for (int64_t k = 0; k < n; ++k) {
+        const float *ps = pts + 3 * k;
+        if (!isfinite(ps[0]) || !isfinite(ps[1]) || !isfinite(ps[2])) continue;
+
+        /* p_i = R ps + t, one rounding per operation */
+        float p[3];
+        for (int r = 0; r < 3; ++r)
+            p[r] = ((pose[4 * r + 0] * ps[0] + pose[4 * r + 1] * ps[1]) + pose[4 * r + 2] * ps[2]) +
+                   pose[4 * r + 3];
+
+        /* b = p_i - q, the ray from the sensor to the return */
+        const float b[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+        const float bb = (b[0] * b[0] + b[1] * b[1]) + b[2] * b[2];
+        const float range = sqrtf(bb); /* ||p_i - q|| */
+        if (!(range >= c->range_min && range <= c->range_max)) continue;
+
+        int32_t ip[3];
+        if (!voxel_index(p[0], v, &ip[0]) || !voxel_index(p[1], v, &ip[1]) ||
+            !voxel_index(p[2], v, &ip[2]))
+            continue;
+        if (!in_domain(c, ip[0] - mr, ip[1] - mr, ip[2] - mr) ||
+            !in_domain(c, ip[0] + mr, ip[1] + mr, ip[2] + mr))
+            continue;
+        accepted++;
+
+        /* every voxel x of the (2m+1)^3 cube around p_i */
+        for (int32_t oz = -mr; oz <= mr; ++oz)
+            for (int32_t oy = -mr; oy <= mr; ++oy)
+                for (int32_t ox = -mr; ox <= mr; ++ox) {
+                    const int32_t j[3] = {ip[0] + ox, ip[1] + oy, ip[2] + oz};
+                    const float x[3] = {voxel_centre(j[0], v), voxel_centre(j[1], v),
+                                        voxel_centre(j[2], v)};
+                    /* theta: angle between x - p_i and p_i - q */
+                    const float a[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+                    const float aa = (a[0] * a[0] + a[1] * a[1]) + a[2] * a[2];
+                    if (aa > 0.0f) {
+                        const float cos_theta =
+                            ((a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]) / (sqrtf(aa) * range);
+                        if (cos_theta > c->cone_cos) continue; /* behind the surface */
+                    }
+                    /* d = ||p_i - q|| - ||x - q||, clamped to [0, tau] */
+                    const float e[3] = {x[0] - q[0], x[1] - q[1], x[2] - q[2]};
+                    const float ee = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+                    float d = range - sqrtf(ee);
+                    if (d < 0.0f) d = 0.0f;
+                    if (d > tau) d = tau;
+                    const uint64_t dq = (uint64_t)rintf(d * OR_SCALE);
+                    or_voxel *vx = voxel_ref(m, j[0], j[1], j[2]);
+                    vx->S += dq;
+                    vx->w += 1;
+                }
+
+        /* ray-cleared band toward the sensor: (clear_lo*tau, clear_hi*tau] */
+        const float u[3] = {(q[0] - p[0]) / range, (q[1] - p[1]) / range, (q[2] - p[2]) / range};
+        const float step = ((c->clear_hi - c->clear_lo) * tau) / (float)c->clear_samples;
+        const float start = c->clear_lo * tau;
+        for (int32_t s = 1; s <= c->clear_samples; ++s) {
+            const float dist = start + (float)s * step;
+            int32_t js[3];
+            if (!voxel_index(p[0] + dist * u[0], v, &js[0]) ||
+                !voxel_index(p[1] + dist * u[1], v, &js[1]) ||
+                !voxel_index(p[2] + dist * u[2], v, &js[2]))
+                continue;
+            if (!in_domain(c, js[0], js[1], js[2])) continue;
+            voxel_ref(m, js[0], js[1], js[2])->cleared = 1;
+        }
+    }
+
+    /* weight cap with proportional rescale of the sum (Sec. 3.6) */
+    for (uint64_t k = 0; k < m->cap; ++k) {
+        or_voxel *vx = &m->slot[k];
+        if (vx->key && vx->w > c->w_cap) {
+            vx->S = (uint64_t)(((unsigned __int128)vx->S * c->w_cap) / vx->w);
+            vx->w = c->w_cap;
+        }
+    }
+    return accepted;
+}
+
+int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz, uint64_t *S,
+                 uint32_t *w, int32_t *cleared) {
+    const or_voxel *vx = voxel_get(m, ix, iy, iz);
+    *S = vx ? vx->S : 0;
+    *w = vx ? vx->w : 0;
+    *cleared = vx ? vx->cleared : 0;
+    return vx != NULL;
+}
+
+void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz, uint64_t S, uint32_t w,
+                  int32_t cleared) {
+    or_voxel *vx = voxel_ref(m, ix, iy, iz);
+    vx->S = S;
+    vx->w = w;
+    vx->cleared = cleared;
+}
+
+void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const uint64_t *S,
+                   const uint32_t *w, const uint8_t *cleared) {
+    for (int64_t k = 0; k < n; ++k)
+        or_set_voxel(m, ijk[3 * k], ijk[3 * k + 1], ijk[3 * k + 2], S[k], w[k], cleared[k]);
+}
+
+int64_t or_voxel_count(const or_map *m) { return (int64_t)m->count; }
+
+/* TSDF < r_c, with r_c on the same 2^-20 m grid as S. */
+static int occ_of(const or_map *m, const or_voxel *vx) {
+    if (!vx || vx->w == 0) return 0;
+    const uint64_t rcq = (uint64_t)rintf(m->cfg.r_c * OR_SCALE);
+    return vx->S < rcq * (uint64_t)vx->w;
+}
+
+static int known_of(const or_voxel *vx) { return vx && (vx->w >= 1 || vx->cleared); }
+
+int or_occ(const or_map *m, int32_t ix, int32_t iy, int32_t iz) {
+    if (!in_domain(&m->cfg, ix, iy, iz)) return 0;
+    return occ_of(m, voxel_get(m, ix, iy, iz));
+}
+
+int or_known(const or_map *m, int32_t ix, int32_t iy, int32_t iz) {
+    if (!in_domain(&m->cfg, ix, iy, iz)) return 0;
+    return known_of(voxel_get(m, ix, iy, iz));
+}
+
+void or_export(const or_map *m, int32_t *ijk, uint64_t *S, uint32_t *w, uint8_t *cleared,
+               uint8_t *occ, uint8_t *known) {
+    uint64_t o = 0;
+    for (uint64_t k = 0; k < m->cap; ++k) {
+        const or_voxel *vx = &m->slot[k];
+        if (!vx->key) continue;
+        unpack_key(vx->key, &ijk[3 * o], &ijk[3 * o + 1], &ijk[3 * o + 2]);
+        S[o] = vx->S;
+        w[o] = vx->w;
+        cleared[o] = (uint8_t)vx->cleared;
+        occ[o] = (uint8_t)occ_of(m, vx);
+        known[o] = (uint8_t)known_of(vx);
+        ++o;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tool and corridor kernels (Sec. 3.4), rasterised in double precision.     */
+/* ------------------------------------------------------------------------- */
+
+static int in_kernel(const or_tool *t, double v, const double u[3], int32_t ox, int32_t oy,
+                     int32_t oz, int which) {
+    const double e[3] = {(double)ox * v, (double)oy * v, (double)oz * v};
+    const double a = (e[0] * u[0] + e[1] * u[1]) + e[2] * u[2]; /* distance along u */
+    const double r[3] = {e[0] - a * u[0], e[1] - a * u[1], e[2] - a * u[2]};
+    const double rho2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]; /* squared axis distance */
+    const double L = (double)t->length;
+    if (which == OR_KERNEL_TOOL) {
+        const double ee = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+        const double rad = (double)t->radius, rs = (double)t->self_excl;
+        return a >= 0.0 && a <= L && rho2 <= rad * rad && ee > rs * rs;
+    } else {
+        const double rad = (double)t->corr_radius;
+        return a > L && a <= L + (double)t->corr_length && rho2 <= rad * rad;
+    }
+}
+
+int64_t or_kernel_offsets(const or_tool *t, float v, const float u[3], int which, int32_t *out,
+                          int64_t cap) {
+    const double dv = (double)v;
+    const double du[3] = {(double)u[0], (double)u[1], (double)u[2]};
+    /* Every kernel point lies within reach of the tip; enumerate the cube
+     * that contains that ball, with one voxel of margin. */
+    const double reach = (double)t->length + (double)t->corr_length +
+                         ((double)t->radius > (double)t->corr_radius ? (double)t->radius
+                                                                     : (double)t->corr_radius);
+    const int32_t B = (int32_t)ceil(reach / dv) + 1;
+    int64_t count = 0;
+    for (int32_t oz = -B; oz <= B; ++oz)
+        for (int32_t oy = -B; oy <= B; ++oy)
+            for (int32_t ox = -B; ox <= B; ++ox)
+                if (in_kernel(t, dv, du, ox, oy, oz, which)) {
+                    if (count < cap) {
+                        out[3 * count + 0] = ox;
+                        out[3 * count + 1] = oy;
+                        out[3 * count + 2] = oz;
+                    }
+                    ++count;
+                }
+    return count;
+}
+
+void or_arm_offsets(float v, float tau, const float u[3], int32_t out[9]) {
+    static const double frac[3] = {0.6, 1.25, 2.25};
+    for (int s = 0; s < 3; ++s)
+        for (int k = 0; k < 3; ++k)
+            out[3 * s + k] =
+                (int32_t)floor(0.5 + ((frac[s] * (double)tau) * (double)u[k]) / (double)v);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Accessibility scoring (Sec. 3.4, 3.5).                                    */
+/* ------------------------------------------------------------------------- */
+
+void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G, const float *pts,
+              const float *normals, int64_t npts, uint8_t *label, int16_t *best,
+              int32_t *dir_score) {
+    const or_config *c = &m->cfg;
+    const float v = c->v;
+    const int32_t n_c = (int32_t)t->n_c;
+
+    /* Precomputed kernels, one per direction, no run-time rotation (Sec. 3.6). */
+    int32_t **tool = (int32_t **)calloc((size_t)G, sizeof(int32_t *));
+    int32_t **corr = (int32_t **)calloc((size_t)G, sizeof(int32_t *));
+    int64_t *ntool = (int64_t *)calloc((size_t)G, sizeof(int64_t));
+    int64_t *ncorr = (int64_t *)calloc((size_t)G, sizeof(int64_t));
+    int32_t *arm = (int32_t *)calloc((size_t)G * 9, sizeof(int32_t));
+    for (int32_t g = 0; g < G; ++g) {
+        const float *u = dirs + 3 * g;
+        ntool[g] = or_kernel_offsets(t, v, u, OR_KERNEL_TOOL, NULL, 0);
+        tool[g] = (int32_t *)malloc((size_t)(3 * ntool[g] + 1) * sizeof(int32_t));
+        or_kernel_offsets(t, v, u, OR_KERNEL_TOOL, tool[g], ntool[g]);
+        ncorr[g] = or_kernel_offsets(t, v, u, OR_KERNEL_CORRIDOR, NULL, 0);
+        corr[g] = (int32_t *)malloc((size_t)(3 * ncorr[g] + 1) * sizeof(int32_t));
+        or_kernel_offsets(t, v, u, OR_KERNEL_CORRIDOR, corr[g], ncorr[g]);
+        or_arm_offsets(v, c->tau, u, arm + 9 * g);
+    }
+
+    for (int64_t k = 0; k < npts; ++k) {
+        const float *s = pts + 3 * k, *nrm = normals + 3 * k;
+        int32_t *ds = dir_score ? dir_score + (int64_t)G * k : NULL;
+        if (ds)
+            for (int32_t g = 0; g < G; ++g) ds[g] = -1;
+        label[k] = OR_UNSCORED;
+        best[k] = -1;
+
+        /* the point's voxel and its confidence (Sec. 3.5) */
+        int32_t i[3];
+        if (!voxel_index(s[0], v, &i[0]) || !voxel_index(s[1], v, &i[1]) ||
+            !voxel_index(s[2], v, &i[2]))
+            continue;
+        uint32_t w = 0;
+        if (in_domain(c, i[0], i[1], i[2])) {
+            const or_voxel *vx = voxel_get(m, i[0], i[1], i[2]);
+            w = vx ? vx->w : 0;
+        }
+        if (w < c->w_min) continue;
+
+        int32_t best_score = -1, best_g = -1;
+        for (int32_t g = 0; g < G; ++g) {
+            const float *u = dirs + 3 * g;
+            /* normal filter: candidate iff n . u > cos(theta_max) */
+            const float nu = (nrm[0] * u[0] + nrm[1] * u[1]) + nrm[2] * u[2];
+            if (!(nu > t->cos_theta_max)) continue;
+
+            /* arm path: any sample occupied or unknown blocks */
+            int blocked = 0;
+            for (int sIdx = 0; sIdx < 3; ++sIdx) {
+                const int32_t *o = arm + 9 * g + 3 * sIdx;
+                const int32_t x = i[0] + o[0], y = i[1] + o[1], z = i[2] + o[2];
+                if (or_occ(m, x, y, z) || !or_known(m, x, y, z)) blocked = 1;
+            }
+            /* approach corridor: any occupied (strict: or unknown) voxel blocks */
+            for (int64_t q = 0; q < ncorr[g]; ++q) {
+                const int32_t *o = corr[g] + 3 * q;
+                const int32_t x = i[0] + o[0], y = i[1] + o[1], z = i[2] + o[2];
+                if (or_occ(m, x, y, z) || (t->strict && !or_known(m, x, y, z))) blocked = 1;
+            }
+            /* tool kernel: collision count (Sec. 3.4) */
+            int64_t count = 0;
+            for (int64_t q = 0; q < ntool[g]; ++q) {
+                const int32_t *o = tool[g] + 3 * q;
+                count += or_occ(m, i[0] + o[0], i[1] + o[1], i[2] + o[2]);
+            }
+            const int32_t score = blocked ? n_c + 1 : (count < n_c ? (int32_t)count : n_c);
+            if (ds) ds[g] = score;
+            if (best_g < 0 || score < best_score) {
+                best_score = score;
+                best_g = g;
+            }
+        }
+        best[k] = (int16_t)best_g;
+        label[k] = (best_g >= 0 && best_score < n_c) ? OR_ACCESSIBLE : OR_BLOCKED;
+    }
+
+    for (int32_t g = 0; g < G; ++g) {
+        free(tool[g]);
+        free(corr[g]);
+    }
+    free(tool);
+    free(corr);
+    free(ntool);
+    free(ncorr);
+    free(arm);
+}

@@ -1,0 +1,96 @@
+/*
+ * af_oracle.h -- declarations of the plain CPU oracle for the Accessibility
+ * Field hot path.
+ *
+ * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this code. The product (the CUDA library
+ * and its Python binding) never includes, links or calls it, and this file
+ * includes nothing from the product.
+ *
+ * Units: metres. Voxel indices are integers i with voxel i covering
+ * [i*v, (i+1)*v) on each axis; its centre is ((float)i + 0.5f) * v.
+ */
+#ifndef AF_ORACLE_H
+#define AF_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    float v;            /* voxel size (Sec. 3.2)                                  */
+    float tau;          /* truncation distance tau (Sec. 3.2)                     */
+    float r_c;          /* collision threshold on the TSDF (Sec. 3.4)             */
+    float cone_cos;     /* behind-surface cone, cos(theta) > cone_cos excluded    */
+    float range_min;    /* returns with |p - q| outside [range_min, range_max]   */
+    float range_max;    /*   are dropped                                          */
+    float clear_lo;     /* ray-cleared band (clear_lo*tau, clear_hi*tau]          */
+    float clear_hi;     /*   toward the sensor (Sec. 3.4)                         */
+    int32_t cube_radius;   /* m = ceil(tau / v): cube (2m+1)^3 (Sec. 3.6)        */
+    int32_t clear_samples; /* N_s samples in the cleared band                    */
+    uint32_t w_min;     /* confidence gate: scored iff w >= w_min (Sec. 3.5)      */
+    uint32_t w_cap;     /* weight cap with proportional rescale of S (Sec. 3.6)   */
+    int32_t dom_min[3]; /* map domain: voxel indices [dom_min, dom_min+dom_size) */
+    int32_t dom_size[3];
+} or_config;
+
+typedef struct {
+    float radius;          /* tool cylinder radius r                              */
+    float length;          /* tool cylinder length L (tip at the surface point)   */
+    float self_excl;       /* self-exclusion radius r_s (Sec. 3.4)                */
+    float corr_radius;     /* approach corridor radius                            */
+    float corr_length;     /* approach corridor length beyond the tool            */
+    float cos_theta_max;   /* candidate iff n . u > cos_theta_max (Sec. 3.4)      */
+    uint32_t n_c;          /* collision-count threshold n_c (Sec. 3.4, 4.1)       */
+    int32_t strict;        /* 1: unknown voxels block the corridor too            */
+} or_tool;
+
+typedef struct or_map or_map;
+
+enum { OR_UNSCORED = 0, OR_ACCESSIBLE = 1, OR_BLOCKED = 2 };
+enum { OR_KERNEL_TOOL = 0, OR_KERNEL_CORRIDOR = 1 };
+
+or_map *or_map_new(const or_config *cfg);
+void or_map_free(or_map *m);
+
+/* One scan (Sec. 3.2 scan-centric update, Sec. 3.4 ray-cleared band,
+ * Sec. 3.6 weight cap). pts: n x 3 floats in the sensor frame; pose: 4x4
+ * row-major world_from_sensor. Returns the number of accepted returns. */
+int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16]);
+
+/* Voxel state. Absent voxels report S = 0, w = 0, cleared = 0. */
+int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz,
+                 uint64_t *S, uint32_t *w, int32_t *cleared);
+void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz,
+                  uint64_t S, uint32_t w, int32_t cleared);
+void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const uint64_t *S,
+                   const uint32_t *w, const uint8_t *cleared);
+int64_t or_voxel_count(const or_map *m);
+/* Writes every stored voxel: ijk (count x 3), S, w, cleared, occ, known. */
+void or_export(const or_map *m, int32_t *ijk, uint64_t *S, uint32_t *w,
+               uint8_t *cleared, uint8_t *occ, uint8_t *known);
+int or_occ(const or_map *m, int32_t ix, int32_t iy, int32_t iz);
+int or_known(const or_map *m, int32_t ix, int32_t iy, int32_t iz);
+
+/* Tool / corridor voxel kernel for one approach direction u (Sec. 3.4).
+ * Writes up to cap offsets (x,y,z int32 triples) in z-major, then y, then x
+ * order; returns the full count. */
+int64_t or_kernel_offsets(const or_tool *t, float v, const float u[3], int which,
+                          int32_t *out, int64_t cap);
+/* The three arm-path sample offsets {0.6, 1.25, 2.25} tau along u (Sec. 3.4). */
+void or_arm_offsets(float v, float tau, const float u[3], int32_t out[9]);
+
+/* Accessibility scoring (Sec. 3.4, 3.5). dirs: G x 3 unit vectors.
+ * label[k] in {UNSCORED, ACCESSIBLE, BLOCKED}; best[k] = index into dirs or -1.
+ * dir_score (optional, m x G int32) receives each direction's score, or -1
+ * for directions that are not candidates / points that are not scored. */
+void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G,
+              const float *pts, const float *normals, int64_t npts,
+              uint8_t *label, int16_t *best, int32_t *dir_score);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

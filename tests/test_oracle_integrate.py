@@ -1,0 +1,200 @@
+"""Pins of the oracle's TSDF integration against what the paper and geometry fix.
+
+Each test checks the oracle (oracle/af_oracle.c) against a value that does
+not come from the oracle itself: hand-worked fixtures (tests/golden), the
+analytic signed distance of a sphere and of a plane, exact invariances (pose,
+order, splitting), and the rejection rules. Parity status: pinned.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden
+
+BIG = (-4096, -4096, -4096), (8192, 8192, 8192)
+
+
+def _cfg(v, tau, m, ns, dom=BIG, **kw):
+    return oracle.Config(v=v, tau=tau, r_c=v / 2, cube_radius=m, clear_samples=ns,
+                         dom_min=dom[0], dom_size=dom[1], **kw)
+
+
+def _pose(t, R=None):
+    T = np.eye(4, dtype=np.float32)
+    if R is not None:
+        T[:3, :3] = R
+    T[:3, 3] = t
+    return T
+
+
+def _triples(s):
+    return [tuple(int(x) for x in part.split()) for part in s.split(";")]
+
+
+def test_single_return_hand_count():
+    """Sec. 3.2 cube/cone/clamp and Sec. 3.4 cleared band, worked by hand."""
+    g = golden("single_return.txt")
+    v, tau = float(g["v"]), float(g["tau"])
+    mp = oracle.Map(_cfg(v, tau, int(g["cube_radius"]), int(g["clear_samples"])))
+    q = [float(x) for x in g["sensor"].split()]
+    ps = np.array([[float(x) for x in g["return_sensor_frame"].split()]], np.float32)
+    assert mp.integrate(ps, _pose(q)) == 1
+    e = mp.export()
+    assert int((e["w"] == 1).sum()) == int(g["updated_voxels"])
+    assert int(e["w"].max()) == 1
+    for ijk in _triples(g["excluded"]):
+        assert mp.voxel(*ijk)[1] == 0
+    for i, j, k, S in _triples(g["S_on_axis"]):
+        assert mp.voxel(i, j, k)[:2] == (S, 1)
+    cleared = {tuple(x) for x in e["ijk"][e["cleared"] == 1]}
+    assert cleared == set(_triples(g["cleared"]))
+    free = {tuple(x) for x in e["ijk"][(e["known"] == 1) & (e["w"] == 0)]}
+    assert free == set(_triples(g["known_free"]))
+    # the cube lies in 7 x 7 x 7 voxels centred on (64, 0, 0)
+    upd = e["ijk"][e["w"] == 1]
+    assert upd.min(0).tolist() == [61, -3, -3] and upd.max(0).tolist() == [67, 3, 3]
+
+
+def test_weight_cap_rescales_sum():
+    """Sec. 3.6: weights capped at 2000 with proportional rescaling of S."""
+    g = golden("single_return.txt")
+    v, tau = float(g["v"]), float(g["tau"])
+    mp = oracle.Map(_cfg(v, tau, 3, 8))
+    q = [float(x) for x in g["sensor"].split()]
+    ps = np.array([[float(x) for x in g["return_sensor_frame"].split()]], np.float32)
+    n = int(g["cap_repeats"])
+    mp.integrate(np.repeat(ps, n, 0), _pose(q))
+    S, w, _ = mp.voxel(63, 0, 0)
+    assert w == int(g["cap_w"]) and S == int(g["cap_S_63"])
+    # below the cap nothing is rescaled
+    mp2 = oracle.Map(_cfg(v, tau, 3, 8))
+    mp2.integrate(np.repeat(ps, 1999, 0), _pose(q))
+    assert mp2.voxel(63, 0, 0)[:2] == (1999 * 32768, 1999)
+
+
+def test_concentric_sphere_tsdf_is_signed_distance():
+    """All returns at range R from q: every contribution is d = R - |x - q|,
+    so S/w equals the analytic clamp(R - |x - q|, 0, tau) (Sec. 3.2)."""
+    rng = np.random.default_rng(7)
+    v, tau = 0.02, 0.06
+    q = np.array([0.3, -0.2, 0.1])
+    R = 1.7
+    d = rng.normal(size=(3000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d[d[:, 0] > 0.3]                      # a cap of the sphere
+    pts = (R * d).astype(np.float32)          # sensor frame, pose = translation q
+    mp = oracle.Map(_cfg(v, tau, 3, 8))
+    assert mp.integrate(pts, _pose(q)) == len(pts)
+    e = mp.export()
+    has = e["w"] > 0
+    centre = (e["ijk"][has] + 0.5) * np.float64(np.float32(v))
+    sdf = np.clip(R - np.linalg.norm(centre - q, axis=1), 0.0, tau)
+    got = e["S"][has].astype(np.float64) / e["w"][has] / 2.0 ** 20
+    # quantisation 2^-21 m plus single-precision range rounding
+    assert np.max(np.abs(got - sdf)) < 1e-5
+    # both clamp ends are reached, so the test covers the clamp
+    assert (sdf == 0).sum() > 100 and (sdf == tau).sum() > 100
+
+
+def test_planar_wall_tsdf_within_bound():
+    """Head-on wall at distance D: S/w matches the signed distance to the plane
+    clamp(D - x_c, 0, tau) within rho^2 / (2 (D - tau)), rho the largest
+    lateral offset of a return or voxel centre from the sensor axis."""
+    rng = np.random.default_rng(3)
+    v, tau, D = 0.02, 0.06, 30.0
+    yz = rng.uniform(-0.1, 0.1, size=(4000, 2))
+    pts = np.concatenate([np.full((4000, 1), D), yz], 1).astype(np.float32)
+    mp = oracle.Map(_cfg(v, tau, 3, 8))
+    mp.integrate(pts, _pose([0, 0, 0]))
+    e = mp.export()
+    has = e["w"] > 0
+    centre = (e["ijk"][has] + 0.5) * np.float64(np.float32(v))
+    sdf = np.clip(np.float64(np.float32(D)) - centre[:, 0], 0.0, tau)
+    got = e["S"][has].astype(np.float64) / e["w"][has] / 2.0 ** 20
+    rho = max(np.abs(yz).max() * math.sqrt(2), np.linalg.norm(centre[:, 1:], axis=1).max())
+    bound = rho ** 2 / (2 * (D - tau)) + 1e-5
+    assert np.max(np.abs(got - sdf)) <= bound
+    assert bound < 0.1 * v      # the bound is tight enough to catch a half-voxel slip
+
+
+def test_rotated_sensor_frame_gives_same_map():
+    """p = R ps + t (Sec. 3.1: points arrive with their sensor pose). With an
+    exact 90 degree yaw and grid-exact coordinates the map must be identical
+    to integrating the world points with the identity rotation."""
+    rng = np.random.default_rng(5)
+    t = np.array([0.25, -0.5, 0.125])
+    world = np.round(rng.uniform(-1, 1, size=(500, 3)) * 1024) / 1024 + [2.0, 0.0, 0.0]
+    Rz = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]], np.float64)
+    a = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    b = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    na = a.integrate((world - t).astype(np.float32), _pose(t))
+    nb = b.integrate(((world - t) @ Rz).astype(np.float32), _pose(t, Rz))
+    assert na == nb == 500
+    ea, eb = a.export(), b.export()
+    for k in ea:
+        np.testing.assert_array_equal(ea[k], eb[k])
+    # a transposed rotation would be a different map
+    c = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    c.integrate(((world - t) @ Rz.T).astype(np.float32), _pose(t, Rz))
+    assert not np.array_equal(c.export()["ijk"], ea["ijk"])
+
+
+def test_order_and_split_invariance():
+    """Integer accumulation: shuffling returns, or splitting a scan into two
+    calls (below the cap), leaves every voxel identical."""
+    rng = np.random.default_rng(11)
+    pts = (rng.normal(size=(3000, 3)) * 0.1 + [2.0, 0.0, 0.0]).astype(np.float32)
+    a = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    b = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    c = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    a.integrate(pts)
+    b.integrate(pts[rng.permutation(len(pts))])
+    c.integrate(pts[:1234])
+    c.integrate(pts[1234:])
+    ea, eb, ec = a.export(), b.export(), c.export()
+    for k in ea:
+        np.testing.assert_array_equal(ea[k], eb[k])
+        np.testing.assert_array_equal(ea[k], ec[k])
+
+
+def test_invalid_returns_are_dropped():
+    """Non-finite points and ranges outside [0.1, 40] m contribute nothing."""
+    mp = oracle.Map(_cfg(0.02, 0.06, 3, 8))
+    bad = np.array([[np.nan, 0, 0], [np.inf, 0, 0], [0.05, 0, 0], [41.0, 0, 0],
+                    [0, 0, 0]], np.float32)
+    assert mp.integrate(bad) == 0 and len(mp) == 0
+    good = np.array([[2.0, 0, 0], [0.2, 0.0, 0.0], [39.0, 0, 0]], np.float32)
+    assert mp.integrate(good) == 3
+
+
+def test_domain_confines_the_map():
+    """A return whose cube leaves the voxel box is dropped (Sec. 3.3 bounded
+    window); one whose cube fits is kept; band samples outside are skipped."""
+    v = 0.03125
+    dom = ((58, -3, -3), (10, 7, 7))          # x in [58, 68), y, z in [-3, 4)
+    mp = oracle.Map(_cfg(v, 3 * v, 3, 8, dom=dom))
+    q = [0.0, v / 2, v / 2]
+    ps = np.array([[64.5 * v, 0, 0]], np.float32)
+    assert mp.integrate(ps, _pose(q)) == 1    # cube x 61..67 inside
+    e = mp.export()
+    assert set(map(tuple, e["ijk"][e["cleared"] == 1])) == {(61, 0, 0), (60, 0, 0),
+                                                            (59, 0, 0), (58, 0, 0)}
+    ps2 = np.array([[65.5 * v, 0, 0]], np.float32)   # cube x 62..68: leaves the box
+    assert mp.integrate(ps2, _pose(q)) == 0
+
+
+@pytest.mark.parametrize("m,updated", [(2, 125 - 2), (4, 729 - 8)])
+def test_cube_size_follows_truncation(m, updated):
+    """(2 ceil(tau/v) + 1)^3 voxels around a return (Sec. 3.6) minus the
+    behind-surface cone cos(theta) > 0.95 (Sec. 3.2), counted by hand for a
+    ray along +x through a voxel centre:
+    m = 2: only (1,0,0), (2,0,0) (the next, (2,1,0), has cos = 2/sqrt 5 = 0.894);
+    m = 4: (1..4,0,0) and (4,+-1,0), (4,0,+-1) with cos = 4/sqrt 17 = 0.970
+    ((3,1,0): 0.949 and (4,1,1): 0.943 stay)."""
+    v = 0.03125
+    mp = oracle.Map(_cfg(v, m * v, m, 8))
+    mp.integrate(np.array([[64.5 * v, 0, 0]], np.float32), _pose([0.0, v / 2, v / 2]))
+    e = mp.export()
+    assert int((e["w"] == 1).sum()) == updated
