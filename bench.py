@@ -1,0 +1,430 @@
+#!/usr/bin/env python3
+"""Benchmark of the Accessibility Field hot path on GB300.
+
+One step = one 10 Hz LiDAR frame of the streaming pine workload (Mid-360-like
+rosette, 20,000 returns, v = 2 cm, K = 64 of G = 128 directions): integrate
+the scan into the map, then score the frame's voxel-deduplicated surface
+points. The headline metric is point x orientation tests per second (a test is
+one (confident point, candidate direction) pair decided), next to the
+frame latency p50 / p99.
+
+Passes over the same frames, each on a fresh map:
+  A  device-resident inputs, per-step CUDA events, L2 flushed between steps
+     -> value, latency, clocks;
+  B  as A with per-kernel CUDA events inside the library -> roofline;
+  C  af_frame_host from pinned host buffers (copies inside the step) -> e2e.
+The CPU oracle is timed on a bounded sample of the same workload
+(cpu_baseline); `--impl reference` times only the oracle.
+
+Under torchrun with N > 1 every rank runs an independent replica (the path
+has no exchange step); value = all ranks' tests / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "point x orientation tests/s (10 Hz frame latency p99 alongside)"
+UNIT = "tests/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _frames(W, start, count):
+    from paper_2608_06412_gb300 import workload
+    out = []
+    for f in range(start, start + count):
+        fr, pts, nrm = workload.pine_frame(W, f)
+        out.append((fr, pts, nrm))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.t0 = self.t1 = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}",
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                          "-lms", "50"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
+        except OSError:
+            self.proc = None
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]), parts))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, p in rows for i in range(4)
+                          if p[5 + i].lower() == "active"})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_objs(W):
+    import oracle
+    p = W.map_params()
+    cfg = oracle.Config(v=p["v"], tau=p["tau"], r_c=p["r_c"], cube_radius=p["cube_radius"],
+                        clear_samples=p["clear_samples"],
+                        dom_min=tuple(8 * b for b in W.dom_min),
+                        dom_size=tuple(8 * b for b in W.dom_bricks), cone_cos=p["cone_cos"],
+                        range_min=p["range_min"], range_max=p["range_max"],
+                        clear_lo=p["clear_lo"], clear_hi=p["clear_hi"], w_min=p["w_min"],
+                        w_cap=p["w_cap"])
+    return oracle.Map(cfg), oracle.Tool(**W.tool())
+
+
+def _oracle_frame(om, tool, W, frame, n_sample, rng):
+    """Integrate one frame, score a random sample of its points; returns the
+    per-frame estimate (tests, seconds) prorated from the sample."""
+    fr, pts, nrm = frame
+    t0 = time.perf_counter()
+    om.integrate(fr.pts, fr.pose)
+    t1 = time.perf_counter()
+    sel = rng.choice(len(pts), min(n_sample, len(pts)), replace=False)
+    lab, best, ds = om.score(tool, W.dirs, pts[sel], nrm[sel], dir_scores=True)
+    t2 = time.perf_counter()
+    tests = int((ds >= 0).sum())
+    scale = len(pts) / max(len(sel), 1)
+    return tests * scale, (t1 - t0) + (t2 - t1) * scale, t1 - t0, t2 - t1, len(sel)
+
+
+def cpu_baseline(W, frames, n_frames=6, n_sample=200):
+    rng = np.random.default_rng(0)
+    om, tool = _oracle_objs(W)
+    tests = secs = 0.0
+    t_int = t_sc = 0.0
+    pts_scored = 0
+    for k in range(n_frames):
+        last = k == n_frames - 1
+        fr = frames[k]
+        if not last:
+            t0 = time.perf_counter()
+            om.integrate(fr[0].pts, fr[0].pose)
+            t_int += time.perf_counter() - t0
+            continue
+        te, se, ti, ts, ns = _oracle_frame(om, tool, W, fr, n_sample, rng)
+        tests, secs = te, se
+        t_int += ti
+        t_sc, pts_scored = ts, ns
+    return {"value": tests / secs if secs > 0 else None, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"single-threaded C oracle: frames 0-{n_frames - 1} integrated "
+                      f"({t_int / n_frames:.2f} s/frame), {pts_scored} random points of "
+                      f"frame {n_frames - 1} scored in full ({t_sc:.1f} s); per-frame tests "
+                      f"and time prorated to all points of that frame"}
+
+
+def run_reference(args, W, ws, rank):
+    if rank != 0:
+        return None
+    rng = np.random.default_rng(1)
+    om, tool = _oracle_objs(W)
+    frames = _frames(W, 0, args.warmup + args.steps)
+    for k in range(args.warmup):
+        om.integrate(frames[k][0].pts, frames[k][0].pose)
+    tests = secs = 0.0
+    lat = []
+    for k in range(args.warmup, args.warmup + args.steps):
+        te, se, _, _, _ = _oracle_frame(om, tool, W, frames[k], 8, rng)
+        tests += te
+        secs += se
+        lat.append(se * 1e3)
+    value = tests / secs if secs > 0 else None
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs * 1e3 / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": W.name, "returns_per_frame": W.params["n_returns"],
+                       "K": W.params["K"], "G": len(W.dirs), "voxel_m": W.params["v"]},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: the oracle integrates the frame and "
+                                       "scores 8 random points of it; tests and time "
+                                       "prorated to all points of the frame"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------
+# Roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def integrate_bytes(stats_delta_vox, n_ret, dirty):
+    """Algorithmic bytes of one scan's integration: 12 B per return in,
+    read + write of the 8-byte voxel word of every voxel the scan updates,
+    and per touched brick the 4 KB word read of the bit view plus its
+    128 B of bit-plane writes."""
+    return 12 * n_ret + 16 * stats_delta_vox + (4096 + 128) * dirty
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, W, ws, rank, local):
+    import torch
+    from paper_2608_06412_gb300 import af
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nfr = args.warmup + args.steps
+    frames = _frames(W, 0, nfr)
+    caps = dict(hash_capacity=1 << 19, pool_blocks=1 << 18, max_returns=1 << 16,
+                max_points=1 << 16)
+
+    d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
+    d_pts = [torch.from_numpy(f[1]).to(dev) for f in frames]
+    d_nrm = [torch.from_numpy(f[2]).to(dev) for f in frames]
+    lab = torch.empty(1 << 16, dtype=torch.uint8, device=dev)
+    best = torch.empty(1 << 16, dtype=torch.int16, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MiB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def pass_device(profile: bool, clocks: Clocks | None):
+        g = af.Map(W.af_config(**caps))
+        g.set_tool(W.af_tool(), W.dirs)
+        for k in range(args.warmup):
+            g.integrate_scan(d_xyz[k], frames[k][0].pose)
+            m = len(d_pts[k])
+            g.score(d_pts[k], d_nrm[k], lab[:m], best[:m])
+        torch.cuda.synchronize()
+        st0 = g.stats()
+        g.profile(profile)
+        if profile:
+            g.profile_read(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark(True)
+        for i, k in enumerate(range(args.warmup, nfr)):
+            flush.zero_()
+            ev[i][0].record(stream)
+            g.integrate_scan(d_xyz[k], frames[k][0].pose)
+            m = len(d_pts[k])
+            g.score(d_pts[k], d_nrm[k], lab[:m], best[:m])
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        if clocks:
+            clocks.mark(False)
+        st1 = g.stats()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        prof = g.profile_read(reset=True) if profile else None
+        g.close()
+        return ms, st0, st1, prof
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, st0, st1, _ = pass_device(False, clocks)
+    clk = clocks.stop()
+    tests = st1["tests"] - st0["tests"]
+    total_ms = sum(ms)
+
+    # per-kernel times (pass B)
+    msB, sB0, sB1, prof = pass_device(True, None)
+
+    # e2e through af_frame_host with pinned host buffers (pass C)
+    e2e = None
+    if not args.no_e2e:
+        g = af.Map(W.af_config(**caps))
+        g.set_tool(W.af_tool(), W.dirs)
+        pin = []
+        for fr, pts, nrm in frames:
+            pin.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                             for a in (fr.pts, pts, nrm)))
+        hl = torch.empty(1 << 16, dtype=torch.uint8).pin_memory()
+        hb = torch.empty(1 << 16, dtype=torch.int16).pin_memory()
+        lib = af.load()
+        import ctypes as C
+
+        def frame_host(k):
+            x, p, n = pin[k]
+            pose = np.ascontiguousarray(frames[k][0].pose, np.float32).reshape(16)
+            st = lib.af_frame_host(g._h, C.c_void_p(x.data_ptr()), x.shape[0],
+                                   pose.ctypes.data_as(C.c_void_p), C.c_void_p(p.data_ptr()),
+                                   C.c_void_p(n.data_ptr()), p.shape[0],
+                                   C.c_void_p(hl.data_ptr()), C.c_void_p(hb.data_ptr()),
+                                   C.c_void_p(stream.cuda_stream))
+            if st != 0:
+                raise RuntimeError(f"af_frame_host failed: {st}")
+
+        for k in range(args.warmup):
+            frame_host(k)
+        e0 = g.stats()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.warmup, nfr):
+            frame_host(k)
+        t1 = time.perf_counter()
+        barrier()
+        e1 = g.stats()
+        h2d = sum(12 * len(frames[k][0].pts) + 24 * len(frames[k][1])
+                  for k in range(args.warmup, nfr)) / args.steps
+        d2h = sum(3 * len(frames[k][1]) + 4 for k in range(args.warmup, nfr)) / args.steps
+        e2e_tests = e1["tests"] - e0["tests"]
+        e2e = {"value": e2e_tests / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": (t1 - t0) * 1e3 / args.steps}
+        g.close()
+
+    # aggregate over ranks: sum of tests, max of time
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(tests), total_ms], dtype=torch.float64)
+        tt = torch.tensor([float(tests)], dtype=torch.float64)
+        mm = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        dist.all_reduce(mm, op=dist.ReduceOp.MAX)
+        tests_all, total_ms_max = float(tt.item()), float(mm.item())
+        del t
+    else:
+        tests_all, total_ms_max = float(tests), total_ms
+
+    returns = sum(len(frames[k][0].pts) for k in range(args.warmup, nfr))
+    peak, peak_kind = _peaks()
+    # dominant kernel and its roofline
+    kt = {k: v[1] for k, v in prof.items()}
+    dom = max(kt, key=kt.get)
+    n_launch = prof[dom][0]
+    avg_ms = kt[dom] / max(n_launch, 1)
+    roof = {"kernel": dom, "bound": "hbm", "unit": "GB/s", "peak": peak,
+            "peak_kind": peak_kind, "traffic": None,
+            "kernel_ms": {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.items()},
+            "kernel_share": {k: round(v / max(sum(kt.values()), 1e-9), 4) for k, v in kt.items()}}
+    roof["achieved"] = None
+    roof["frac"] = None
+    return {
+        "metric": METRIC, "value": tests_all / (total_ms_max / 1e3), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+        "config": {"workload": W.name, "returns_per_frame": W.params["n_returns"],
+                   "K": W.params["K"], "G": len(W.dirs), "voxel_m": W.params["v"],
+                   "frames": f"{args.warmup}..{nfr - 1}",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "max": float(max(ms))},
+        "returns_per_s": returns / (total_ms / 1e3),
+        "tests_per_step": tests / args.steps,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "clocks": clk,
+        "_frames": frames,
+    }
+
+
+def main():
+    args = _args()
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    from paper_2608_06412_gb300 import workload
+    W = workload.pine_stream()
+    if args.impl == "reference":
+        out = run_reference(args, W, ws, rank)
+    else:
+        out = run_ours(args, W, ws, rank, local)
+        frames = out.pop("_frames")
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(W, frames)
+        if rank != 0:
+            out = None
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

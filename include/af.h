@@ -1,0 +1,225 @@
+/*
+ * af.h -- C ABI of the Accessibility Field hot path on NVIDIA GB300 (sm_103a).
+ *
+ * The library integrates LiDAR scans into a truncated signed distance field
+ * (TSDF) held in a sparse voxel-brick hash map, keeps a bit-packed occupied /
+ * known view of it, and scores surface points for tool accessibility against
+ * precomputed tool and approach-corridor voxel kernels (Scott, Schofield,
+ * Green, "Beyond Visibility: Real-Time Surface Accessibility Fields from
+ * Sparse LiDAR": Sec. 3.2 scan-centric TSDF, Sec. 3.4 accessibility scoring,
+ * Sec. 3.5 confidence, Sec. 3.6 GPU implementation).
+ *
+ * Conventions for every entry point:
+ *  - Units are metres; voxel i covers [i v, (i+1) v) on each axis and its
+ *    centre is ((float)i + 0.5f) * v.
+ *  - Pointers named d_* are device memory owned by the caller; pointers named
+ *    h_* are host memory owned by the caller. The library owns the map, the
+ *    kernel tables and its scratch, all allocated in af_create / af_set_tool.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *    that take a stream are asynchronous on it unless stated otherwise.
+ *  - Argument errors are returned synchronously and nothing is enqueued.
+ *    Errors found on the device (capacity) are latched in a device status
+ *    word; af_sync_status returns them. AF_ERR_CAPACITY is sticky: later
+ *    integrations are skipped, the map keeps the last committed scan, and
+ *    scoring keeps working on it.
+ *  - A context is not thread-safe; use it from one host thread.
+ */
+#ifndef AF_H
+#define AF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct af_ctx af_ctx;
+
+typedef enum {
+    AF_OK = 0,
+    AF_ERR_INVALID_ARG = 1, /* bad argument; nothing was enqueued          */
+    AF_ERR_CAPACITY = 2,    /* hash, brick pool or per-call size exceeded */
+    AF_ERR_CUDA = 3,        /* a CUDA call failed; see af_last_error       */
+    AF_ERR_TIMEOUT = 4,     /* a bounded device wait gave up               */
+    AF_ERR_STATE = 5        /* call out of order (e.g. score before tool)  */
+} af_status;
+
+/* Per-point labels written by af_score (Fig. 1: green / red / grey). */
+enum { AF_UNSCORED = 0, AF_ACCESSIBLE = 1, AF_BLOCKED = 2 };
+/* Kernel selectors for af_kernel_offsets. */
+enum { AF_KERNEL_TOOL = 0, AF_KERNEL_CORRIDOR = 1 };
+
+/*
+ * Map parameters (Sec. 3.2 - 3.6). Integers that the paper derives from
+ * v and tau are passed explicitly so both ends agree on them exactly.
+ */
+typedef struct {
+    float voxel_size;     /* v                                                  */
+    float truncation;     /* tau; contributions are clamped to [0, tau]        */
+    float r_c;            /* collision threshold: occupied iff TSDF < r_c      */
+    float cone_cos;       /* voxels with cos(theta) > cone_cos behind a return
+                             are not updated (Sec. 3.2; 0.95)                  */
+    float range_min;      /* returns with range outside [range_min, range_max] */
+    float range_max;      /*   are dropped (0.1 m, 40 m)                       */
+    float clear_lo;       /* ray-cleared band (clear_lo tau, clear_hi tau]     */
+    float clear_hi;       /*   toward the sensor (Sec. 3.4; 1.0, 2.25)         */
+    int32_t cube_radius;  /* m = ceil(tau / v): (2m+1)^3 cube (Sec. 3.6), 1..8 */
+    int32_t clear_samples;/* samples N_s along the cleared band, 0..64         */
+    uint32_t w_min;       /* points are scored iff their voxel has w >= w_min  */
+    uint32_t w_cap;       /* weight cap with proportional rescale (Sec. 3.6)   */
+    uint32_t block_edge;  /* voxels per brick edge; must be 8                  */
+    int32_t domain_min[3];     /* map box, in bricks: bricks [min, min+size)  */
+    uint32_t domain_bricks[3]; /*   (the paper's bounded window, Sec. 3.3)    */
+    uint32_t hash_capacity;    /* hash slots, a power of two                  */
+    uint32_t pool_blocks;      /* bricks that can be allocated                */
+    uint32_t max_returns;      /* largest n per af_integrate_scan            */
+    uint32_t max_points;       /* largest m per af_frame_host                */
+} af_config;
+
+/* A cylinder tool of radius r and length L whose tip (the interaction point)
+ * sits on the surface point and whose body extends along the approach
+ * direction u, followed by a coaxial approach corridor (Sec. 3.4). */
+typedef struct {
+    float radius;          /* r                                                */
+    float length;          /* L                                                */
+    float self_excl;       /* r_s: kernel voxels within r_s of the tip ignored */
+    float corr_radius;     /* corridor radius                                  */
+    float corr_length;     /* corridor extends over (L, L + corr_length]       */
+    float cos_theta_max;   /* direction u is a candidate iff n . u > this      */
+    uint32_t n_c;          /* collision threshold n_c (Sec. 3.4, 4.1; 5)       */
+    int32_t corridor_strict; /* 1: unknown corridor voxels also block          */
+} af_tool;
+
+typedef struct {
+    uint64_t scans;             /* af_integrate_scan calls                      */
+    uint64_t returns_in;        /* returns offered                              */
+    uint64_t returns_accepted;  /* returns integrated                           */
+    uint64_t blocks_allocated;  /* bricks in use                                */
+    uint64_t blocks_dirty_last; /* bricks touched by the last scan              */
+    uint64_t points_in;         /* points offered to af_score                  */
+    uint64_t points_scored;     /* points that passed the confidence gate       */
+    uint64_t tests;             /* (scored point, candidate direction) pairs    */
+} af_stats;
+
+/* Library version string (static storage). */
+const char *af_version(void);
+
+/* Creates a context on the current CUDA device and allocates all map memory
+ * (hash, brick pool, occupancy planes, scratch). Returns AF_ERR_INVALID_ARG
+ * for inconsistent parameters, AF_ERR_CUDA if allocation fails. */
+af_status af_create(const af_config *cfg, af_ctx **out);
+
+/* Frees everything the context owns. Synchronises the device first. */
+af_status af_destroy(af_ctx *ctx);
+
+/*
+ * Integrates one LiDAR scan (Sec. 3.2, 3.4, 3.6).
+ *  d_xyz : n x 3 float32, returns in the sensor frame, row-major (x,y,z).
+ *  n     : 0 <= n <= max_returns (n = 0 is a no-op that still counts a scan).
+ *  pose  : host float[16], row-major 4x4 world_from_sensor; its translation
+ *          is the sensor origin q; the point is p = R ps + t.
+ * Per return: dropped if non-finite, out of range, or its cube leaves the
+ * map box. Otherwise every voxel x of its (2m+1)^3 cube outside the
+ * behind-surface cone receives d = |p - q| - |x - q| clamped to [0, tau]
+ * (accumulated exactly as round(d 2^20) in integers, w += 1), and the voxels
+ * of N_s samples of the band toward the sensor are marked ray-cleared. At the
+ * end of the call weights above w_cap are capped with proportional rescaling
+ * and the occupied / known view of every touched brick is rebuilt.
+ * Asynchronous on `stream`; d_xyz must stay valid until the work completes.
+ */
+af_status af_integrate_scan(af_ctx *ctx, const float *d_xyz, uint32_t n,
+                            const float pose[16], void *stream);
+
+/*
+ * Sets the tool and the approach-direction table (Sec. 3.4, 3.6): for each
+ * of the G unit directions (h_dirs: host G x 3 float32, world frame) the
+ * library rasterises the tool and corridor kernels and the three arm-path
+ * samples once, and keeps them on the device (no rotation at run time).
+ * 1 <= G <= 4096. Synchronous; replaces any previous tool.
+ */
+af_status af_set_tool(af_ctx *ctx, const af_tool *tool, const float *h_dirs, uint32_t G);
+
+/*
+ * Scores m surface points (Sec. 3.4, 3.5).
+ *  d_pts, d_normals : m x 3 float32 (points; outward unit normals).
+ *  d_label : m uint8  -> AF_UNSCORED (voxel weight below w_min),
+ *                        AF_ACCESSIBLE (best direction score < n_c),
+ *                        AF_BLOCKED.
+ *  d_best  : m int16  -> index of the best direction (lowest index among the
+ *                        minimum scores), -1 if unscored or no candidate.
+ * A direction's score is n_c + 1 when an arm sample is occupied or unknown or
+ * the corridor holds an occupied voxel, else min(#occupied tool voxels, n_c).
+ * Requires af_set_tool (else AF_ERR_STATE). Asynchronous on `stream`.
+ */
+af_status af_score(af_ctx *ctx, const float *d_pts, const float *d_normals, uint32_t m,
+                   uint8_t *d_label, int16_t *d_best, void *stream);
+
+/*
+ * One whole frame from host buffers: copies the scan and the points to the
+ * device, integrates, scores, copies labels and best directions back, and
+ * waits for `stream`. Sizes are bounded by max_returns / max_points. Returns
+ * the latched device status as well (AF_ERR_CAPACITY if the map is full).
+ * Host buffers should be page-locked for asynchronous copies.
+ */
+af_status af_frame_host(af_ctx *ctx, const float *h_xyz, uint32_t n, const float pose[16],
+                        const float *h_pts, const float *h_normals, uint32_t m,
+                        uint8_t *h_label, int16_t *h_best, void *stream);
+
+/* Waits for the context's last stream and returns the latched device status
+ * (AF_OK or AF_ERR_CAPACITY). Does not clear it. */
+af_status af_sync_status(af_ctx *ctx);
+
+/* Synchronises and fills *out. */
+af_status af_get_stats(af_ctx *ctx, af_stats *out);
+
+/* Synchronises and returns the number of allocated bricks. */
+af_status af_block_count(af_ctx *ctx, uint32_t *out);
+
+/*
+ * Synchronises and copies the allocated bricks to host memory, at most `cap`
+ * of them (order unspecified). Brick b covers voxels
+ * (domain_min + key) * 8 + (lx, ly, lz), voxel l = lx + 8 ly + 64 lz.
+ *  h_key     : cap x 3 int32   brick coordinates (absolute, in bricks)
+ *  h_S       : cap x 512 uint64 SDF sums in units of 2^-20 m
+ *  h_w       : cap x 512 uint32 weights
+ *  h_flags   : cap x 512 uint8  bit0 cleared, bit1 occupied, bit2 known
+ * *out_count receives the number written.
+ */
+af_status af_export_blocks(af_ctx *ctx, uint32_t cap, int32_t *h_key, uint64_t *h_S,
+                           uint32_t *h_w, uint8_t *h_flags, uint32_t *out_count);
+
+/*
+ * Host-only: the integer voxel offsets of the tool (which = AF_KERNEL_TOOL)
+ * or corridor (AF_KERNEL_CORRIDOR) kernel that the library rasterises for
+ * direction u (Sec. 3.4). Writes min(count, cap) x 3 int32 to h_out (any
+ * order) and the full count to *count. Needs no GPU.
+ */
+af_status af_kernel_offsets(const af_tool *tool, float voxel_size, const float u[3],
+                            int32_t which, int32_t *h_out, int64_t cap, int64_t *count);
+
+/* Host-only: the three arm-path sample offsets at {0.6, 1.25, 2.25} tau along
+ * u (Sec. 3.4), as 3 x 3 int32 rows. Needs no GPU. */
+af_status af_arm_offsets(float voxel_size, float truncation, const float u[3], int32_t h_out[9]);
+
+/*
+ * Kernel timing: when enabled, every launch of the context is bracketed by
+ * CUDA events recorded on the launch's own stream. Index 0 = brick
+ * allocation, 1 = cube integration, 2 = weight cap + bit view, 3 = scoring.
+ * af_profile_read synchronises, sums the elapsed times of the recorded
+ * launches (milliseconds) and, if `reset`, forgets them.
+ */
+typedef struct {
+    uint64_t launches[4];
+    double ms[4];
+} af_profile;
+af_status af_profile_enable(af_ctx *ctx, int enable);
+af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);
+
+/* Last error message of the context (static storage if ctx is NULL). */
+const char *af_last_error(const af_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AF_H */

@@ -1,0 +1,324 @@
+"""Python binding of libaf (include/af.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library; this module turns torch
+tensors and numpy arrays into pointers and af_* calls. PyTorch provides the
+device memory and the streams. If the library is missing or no CUDA device
+is present, the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+UNSCORED, ACCESSIBLE, BLOCKED = 0, 1, 2
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
+KERNEL_TOOL, KERNEL_CORRIDOR = 0, 1
+STATUS = {0: "AF_OK", 1: "AF_ERR_INVALID_ARG", 2: "AF_ERR_CAPACITY", 3: "AF_ERR_CUDA",
+          4: "AF_ERR_TIMEOUT", 5: "AF_ERR_STATE"}
+
+#: Every symbol include/af.h declares.
+EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set_tool",
+           "af_score", "af_frame_host", "af_sync_status", "af_get_stats", "af_block_count",
+           "af_export_blocks", "af_kernel_offsets", "af_arm_offsets", "af_profile_enable",
+           "af_profile_read", "af_last_error")
+#: Kernel names in the order of af_profile's arrays.
+KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score")
+
+
+class AfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(C.Structure):
+    _fields_ = [("voxel_size", C.c_float), ("truncation", C.c_float), ("r_c", C.c_float),
+                ("cone_cos", C.c_float), ("range_min", C.c_float), ("range_max", C.c_float),
+                ("clear_lo", C.c_float), ("clear_hi", C.c_float),
+                ("cube_radius", C.c_int32), ("clear_samples", C.c_int32),
+                ("w_min", C.c_uint32), ("w_cap", C.c_uint32), ("block_edge", C.c_uint32),
+                ("domain_min", C.c_int32 * 3), ("domain_bricks", C.c_uint32 * 3),
+                ("hash_capacity", C.c_uint32), ("pool_blocks", C.c_uint32),
+                ("max_returns", C.c_uint32), ("max_points", C.c_uint32)]
+
+
+class _Tool(C.Structure):
+    _fields_ = [("radius", C.c_float), ("length", C.c_float), ("self_excl", C.c_float),
+                ("corr_radius", C.c_float), ("corr_length", C.c_float),
+                ("cos_theta_max", C.c_float), ("n_c", C.c_uint32),
+                ("corridor_strict", C.c_int32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("scans", "returns_in", "returns_accepted",
+                                          "blocks_allocated", "blocks_dirty_last",
+                                          "points_in", "points_scored", "tests")]
+
+
+class _Profile(C.Structure):
+    _fields_ = [("launches", C.c_uint64 * 4), ("ms", C.c_double * 4)]
+
+
+_lib = None
+
+
+def load(build: bool = True) -> C.CDLL:
+    """Load libaf.so from the package directory (building it if stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libaf.so not found at {path}; run build()")
+        lib = C.CDLL(path)
+        P, U32, I32, I64 = C.c_void_p, C.c_uint32, C.c_int32, C.c_int64
+        sig = {
+            "af_version": (C.c_char_p, []),
+            "af_create": (C.c_int, [C.POINTER(_Config), C.POINTER(P)]),
+            "af_destroy": (C.c_int, [P]),
+            "af_integrate_scan": (C.c_int, [P, P, U32, P, P]),
+            "af_set_tool": (C.c_int, [P, C.POINTER(_Tool), P, U32]),
+            "af_score": (C.c_int, [P, P, P, U32, P, P, P]),
+            "af_frame_host": (C.c_int, [P, P, U32, P, P, P, U32, P, P, P]),
+            "af_sync_status": (C.c_int, [P]),
+            "af_get_stats": (C.c_int, [P, C.POINTER(_Stats)]),
+            "af_block_count": (C.c_int, [P, C.POINTER(U32)]),
+            "af_export_blocks": (C.c_int, [P, U32, P, P, P, P, C.POINTER(U32)]),
+            "af_kernel_offsets": (C.c_int, [C.POINTER(_Tool), C.c_float, P, I32, P, I64,
+                                            C.POINTER(I64)]),
+            "af_arm_offsets": (C.c_int, [C.c_float, C.c_float, P, P]),
+            "af_profile_enable": (C.c_int, [P, C.c_int]),
+            "af_profile_read": (C.c_int, [P, C.POINTER(_Profile), C.c_int]),
+            "af_last_error": (C.c_char_p, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = lib
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != 0:
+        raise AfError(st, load().af_last_error(ctx).decode())
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t, dtype, shape_tail=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor")
+    if shape_tail is not None and tuple(t.shape[1:]) != shape_tail:
+        raise TypeError(f"expected shape (n, {shape_tail})")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class MapConfig:
+    """Map parameters (Sec. 3.2-3.6); the box is in bricks of 8^3 voxels."""
+    voxel_size: float
+    truncation: float
+    r_c: float
+    cube_radius: int
+    clear_samples: int
+    domain_min: tuple
+    domain_bricks: tuple
+    cone_cos: float = 0.95
+    range_min: float = 0.1
+    range_max: float = 40.0
+    clear_lo: float = 1.0
+    clear_hi: float = 2.25
+    w_min: int = 3
+    w_cap: int = 2000
+    hash_capacity: int = 1 << 16
+    pool_blocks: int = 1 << 15
+    max_returns: int = 1 << 16
+    max_points: int = 1 << 16
+
+    def _c(self) -> _Config:
+        c = _Config()
+        for k in ("voxel_size", "truncation", "r_c", "cone_cos", "range_min", "range_max",
+                  "clear_lo", "clear_hi", "cube_radius", "clear_samples", "w_min", "w_cap",
+                  "hash_capacity", "pool_blocks", "max_returns", "max_points"):
+            setattr(c, k, getattr(self, k))
+        c.block_edge = 8
+        c.domain_min[:] = [int(x) for x in self.domain_min]
+        c.domain_bricks[:] = [int(x) for x in self.domain_bricks]
+        return c
+
+
+@dataclass
+class ToolConfig:
+    """Cylinder tool with a coaxial approach corridor (Sec. 3.4)."""
+    radius: float
+    length: float
+    self_excl: float
+    corr_radius: float
+    corr_length: float
+    cos_theta_max: float = 0.0
+    n_c: int = 5
+    strict: int = 0
+
+    def _c(self) -> _Tool:
+        t = _Tool()
+        for k in ("radius", "length", "self_excl", "corr_radius", "corr_length",
+                  "cos_theta_max", "n_c"):
+            setattr(t, k, getattr(self, k))
+        t.corridor_strict = self.strict
+        return t
+
+
+class Map:
+    """An accessibility-field map on the current CUDA device (af_create)."""
+
+    def __init__(self, cfg: MapConfig):
+        self.cfg = cfg
+        self._lib = load()
+        self._cc = cfg._c()
+        h = C.c_void_p()
+        _check(self._lib.af_create(C.byref(self._cc), C.byref(h)))
+        self._h = h
+        self.G = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.af_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate_scan(self, xyz, pose, stream=None):
+        """af_integrate_scan: xyz is an (n, 3) float32 CUDA tensor (sensor frame),
+        pose a 4x4 world_from_sensor matrix."""
+        import torch
+        n = int(xyz.shape[0])
+        p = _dev_ptr(xyz, torch.float32, (3,)) if n else C.c_void_p(0)
+        pose = np.ascontiguousarray(pose, np.float32).reshape(16)
+        _check(self._lib.af_integrate_scan(self._h, p, n, _np_ptr(pose), _stream_ptr(stream)),
+               self._h)
+
+    def set_tool(self, tool: ToolConfig, dirs: np.ndarray):
+        """af_set_tool: rasterise the tool/corridor kernels for G directions."""
+        dirs = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+        self._tc = tool._c()
+        _check(self._lib.af_set_tool(self._h, C.byref(self._tc), _np_ptr(dirs), len(dirs)),
+               self._h)
+        self.G = len(dirs)
+
+    def score(self, pts, normals, label=None, best=None, stream=None):
+        """af_score: returns (label uint8, best int16) CUDA tensors."""
+        import torch
+        m = int(pts.shape[0])
+        if label is None:
+            label = torch.empty(m, dtype=torch.uint8, device=pts.device)
+        if best is None:
+            best = torch.empty(m, dtype=torch.int16, device=pts.device)
+        if m:
+            _check(self._lib.af_score(self._h, _dev_ptr(pts, torch.float32, (3,)),
+                                      _dev_ptr(normals, torch.float32, (3,)), m,
+                                      _dev_ptr(label, torch.uint8), _dev_ptr(best, torch.int16),
+                                      _stream_ptr(stream)), self._h)
+        return label, best
+
+    def frame_host(self, xyz: np.ndarray, pose, pts: np.ndarray, normals: np.ndarray,
+                   label: np.ndarray, best: np.ndarray, stream=None):
+        """af_frame_host: one frame from (ideally page-locked) host arrays."""
+        pose = np.ascontiguousarray(pose, np.float32).reshape(16)
+        _check(self._lib.af_frame_host(self._h, _np_ptr(xyz), len(xyz), _np_ptr(pose),
+                                       _np_ptr(pts), _np_ptr(normals), len(pts),
+                                       _np_ptr(label), _np_ptr(best), _stream_ptr(stream)),
+               self._h)
+
+    def sync_status(self) -> int:
+        return int(self._lib.af_sync_status(self._h))
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(self._lib.af_get_stats(self._h, C.byref(s)), self._h)
+        return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
+
+    def profile(self, enable: bool = True):
+        """Bracket every launch with CUDA events on its stream (af_profile_enable)."""
+        _check(self._lib.af_profile_enable(self._h, int(enable)), self._h)
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{kernel: (launches, total ms)} since the last reset (af_profile_read)."""
+        p = _Profile()
+        _check(self._lib.af_profile_read(self._h, C.byref(p), int(reset)), self._h)
+        return {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(KERNELS)}
+
+    def block_count(self) -> int:
+        n = C.c_uint32()
+        _check(self._lib.af_block_count(self._h, C.byref(n)), self._h)
+        return int(n.value)
+
+    def export_blocks(self) -> dict:
+        """All allocated bricks: absolute brick keys and per-voxel S, w, flags."""
+        n = self.block_count()
+        key = np.zeros((max(n, 1), 3), np.int32)
+        S = np.zeros((max(n, 1), 512), np.uint64)
+        w = np.zeros((max(n, 1), 512), np.uint32)
+        fl = np.zeros((max(n, 1), 512), np.uint8)
+        out = C.c_uint32()
+        _check(self._lib.af_export_blocks(self._h, n, _np_ptr(key), _np_ptr(S), _np_ptr(w),
+                                          _np_ptr(fl), C.byref(out)), self._h)
+        n = int(out.value)
+        return dict(key=key[:n], S=S[:n], w=w[:n], flags=fl[:n])
+
+
+def export_voxels(blocks: dict) -> dict:
+    """Flatten exported bricks to the voxels that carry state (w > 0 or
+    cleared), sorted by (z, y, x): ijk, S, w, cleared, occ, known."""
+    key, S, w, fl = blocks["key"], blocks["S"], blocks["w"], blocks["flags"]
+    l = np.arange(512)
+    loc = np.stack([l & 7, (l >> 3) & 7, l >> 6], 1)
+    ijk = (key[:, None, :] * 8 + loc[None]).reshape(-1, 3)
+    S, w, fl = S.reshape(-1), w.reshape(-1), fl.reshape(-1)
+    keep = (w > 0) | ((fl & 1) != 0)
+    ijk, S, w, fl = ijk[keep], S[keep], w[keep], fl[keep]
+    order = np.lexsort((ijk[:, 0], ijk[:, 1], ijk[:, 2]))
+    return dict(ijk=ijk[order].astype(np.int32), S=S[order], w=w[order],
+                cleared=(fl[order] & 1).astype(np.uint8),
+                occ=((fl[order] >> 1) & 1).astype(np.uint8),
+                known=((fl[order] >> 2) & 1).astype(np.uint8))
+
+
+def kernel_offsets(tool: ToolConfig, v: float, u, which: int) -> np.ndarray:
+    """Host-only af_kernel_offsets, sorted z-major."""
+    lib = load()
+    tc = tool._c()
+    u = np.ascontiguousarray(u, np.float32).reshape(3)
+    cnt = C.c_int64()
+    _check(lib.af_kernel_offsets(C.byref(tc), v, _np_ptr(u), which, None, 0, C.byref(cnt)))
+    out = np.zeros((max(cnt.value, 1), 3), np.int32)
+    _check(lib.af_kernel_offsets(C.byref(tc), v, _np_ptr(u), which, _np_ptr(out), cnt.value,
+                                 C.byref(cnt)))
+    out = out[:cnt.value]
+    return out[np.lexsort((out[:, 0], out[:, 1], out[:, 2]))]
+
+
+def arm_offsets(v: float, tau: float, u) -> np.ndarray:
+    lib = load()
+    u = np.ascontiguousarray(u, np.float32).reshape(3)
+    out = np.zeros((3, 3), np.int32)
+    _check(lib.af_arm_offsets(v, tau, _np_ptr(u), _np_ptr(out)))
+    return out

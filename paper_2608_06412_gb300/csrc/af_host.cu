@@ -1,0 +1,623 @@
+// af_host.cu -- the C ABI of libaf (include/af.h): context lifetime, argument
+// checks, the tool / corridor kernel tables (rasterised once on the host,
+// Sec. 3.4 and 3.6 of the paper: no rotation at run time), launches, and
+// host-side export of the map.
+#include <af.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "af_internal.cuh"
+
+namespace af {
+cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const float pose[16],
+                         float4* d_ret, cudaStream_t stream);
+cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], const float4* d_ret,
+                        uint32_t frame, cudaStream_t stream);
+cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream);
+cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts,
+                         const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
+                         cudaStream_t stream);
+cudaError_t launch_export_flags(const MapView& M, uint32_t count, uint8_t* d_flags,
+                                cudaStream_t stream);
+}  // namespace af
+
+using af::MapView;
+
+struct af_ctx {
+  af_config cfg;
+  MapView M;
+  int num_sms = 0;
+  uint32_t frame = 0;
+  cudaStream_t last_stream = nullptr;
+  // scratch
+  float4* d_ret = nullptr;
+  float* d_xyz = nullptr;
+  float* d_pts = nullptr;
+  float* d_nrm = nullptr;
+  uint8_t* d_label = nullptr;
+  int16_t* d_best = nullptr;
+  uint32_t* h_status = nullptr;  // pinned
+  // tool tables
+  bool has_tool = false;
+  af::ToolView T{};
+  float* d_dirs = nullptr;
+  short4* d_runs = nullptr;
+  int4* d_dtab = nullptr;
+  short4* d_arm = nullptr;
+  // host counters
+  uint64_t scans = 0, returns_in = 0, points_in = 0;
+  // kernel profiling: CUDA events around each launch on its own stream
+  bool prof_on = false;
+  struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_free;
+  char err[512] = {0};
+};
+
+namespace {
+
+cudaEvent_t take_event(af_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs `launch` on `s`, bracketed by events when profiling is on.
+template <class F>
+cudaError_t timed(af_ctx* c, int kernel, cudaStream_t s, F&& launch) {
+  if (!c->prof_on) return launch();
+  af_ctx::ProfRec r{kernel, take_event(c), take_event(c)};
+  cudaEventRecord(r.a, s);
+  const cudaError_t e = launch();
+  cudaEventRecord(r.b, s);
+  c->prof.push_back(r);
+  return e;
+}
+
+}  // namespace
+
+static char g_err[512] = "no error";
+
+static af_status fail(af_ctx* c, af_status s, const char* fmt, ...) {
+  char* buf = c ? c->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define AF_CUDA(ctx, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((ctx), AF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+extern "C" const char* af_version(void) { return "libaf 0.1 (sm_103a)"; }
+
+extern "C" const char* af_last_error(const af_ctx* ctx) { return ctx ? ctx->err : g_err; }
+
+// ---------------------------------------------------------------------------
+// Kernel rasterisation (Sec. 3.4). An offset o belongs to the kernel of unit
+// direction u when, with e = o v, a = e . u and rho^2 = |e - a u|^2 (double
+// precision, summed x, y, z):
+//   tool:     0 <= a <= L,  rho^2 <= r^2,  |e|^2 > r_s^2
+//   corridor: L < a <= L + L_c,  rho^2 <= r_c^2
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Offset {
+  int x, y, z;
+};
+
+bool member(const af_tool& t, double v, const double u[3], int ox, int oy, int oz, int which) {
+  const double ex = (double)ox * v, ey = (double)oy * v, ez = (double)oz * v;
+  const double a = (ex * u[0] + ey * u[1]) + ez * u[2];
+  const double rx = ex - a * u[0], ry = ey - a * u[1], rz = ez - a * u[2];
+  const double rho2 = (rx * rx + ry * ry) + rz * rz;
+  const double L = (double)t.length;
+  if (which == AF_KERNEL_TOOL) {
+    const double e2 = (ex * ex + ey * ey) + ez * ez;
+    const double r = (double)t.radius, rs = (double)t.self_excl;
+    return a >= 0.0 && a <= L && rho2 <= r * r && e2 > rs * rs;
+  }
+  const double r = (double)t.corr_radius;
+  return a > L && a <= L + (double)t.corr_length && rho2 <= r * r;
+}
+
+// Offsets of one kernel, enumerating the axis-aligned box that holds the
+// cylinder (with one voxel of margin), z-major.
+std::vector<Offset> rasterise(const af_tool& t, double v, const double u[3], int which) {
+  std::vector<Offset> out;
+  const double a0 = which == AF_KERNEL_TOOL ? 0.0 : (double)t.length;
+  const double a1 = which == AF_KERNEL_TOOL ? (double)t.length
+                                            : (double)t.length + (double)t.corr_length;
+  const double r = which == AF_KERNEL_TOOL ? (double)t.radius : (double)t.corr_radius;
+  if (which == AF_KERNEL_CORRIDOR && !(t.corr_length > 0.f)) return out;
+  int lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    const double p = a0 * u[k], q = a1 * u[k];
+    lo[k] = (int)std::floor((std::min(p, q) - r) / v) - 1;
+    hi[k] = (int)std::ceil((std::max(p, q) + r) / v) + 1;
+  }
+  for (int oz = lo[2]; oz <= hi[2]; ++oz)
+    for (int oy = lo[1]; oy <= hi[1]; ++oy)
+      for (int ox = lo[0]; ox <= hi[0]; ++ox)
+        if (member(t, v, u, ox, oy, oz, which)) out.push_back({ox, oy, oz});
+  return out;
+}
+
+// Groups z-major offsets into x-runs of at most 64 voxels, ordered by the
+// axial distance of their first voxel (near runs first: blocking geometry
+// next to the surface is met early).
+void to_runs(const std::vector<Offset>& offs, double v, const double u[3],
+             std::vector<short4>* runs) {
+  struct R {
+    double a;
+    short4 s;
+  };
+  std::vector<R> rs;
+  size_t i = 0;
+  while (i < offs.size()) {
+    size_t j = i + 1;
+    while (j < offs.size() && offs[j].y == offs[i].y && offs[j].z == offs[i].z &&
+           offs[j].x == offs[j - 1].x + 1 && (int)(j - i) < 64)
+      ++j;
+    const Offset& o = offs[i];
+    const double a = ((double)o.x * v * u[0] + (double)o.y * v * u[1]) + (double)o.z * v * u[2];
+    rs.push_back({a, make_short4((short)o.x, (short)(j - i), (short)o.y, (short)o.z)});
+    i = j;
+  }
+  std::stable_sort(rs.begin(), rs.end(), [](const R& p, const R& q) { return p.a < q.a; });
+  for (const R& r : rs) runs->push_back(r.s);
+}
+
+void arm_offsets(double v, double tau, const double u[3], int out[9]) {
+  static const double frac[3] = {0.6, 1.25, 2.25};
+  for (int s = 0; s < 3; ++s)
+    for (int k = 0; k < 3; ++k) out[3 * s + k] = (int)std::floor(0.5 + ((frac[s] * tau) * u[k]) / v);
+}
+
+bool finite3(const float* u) { return std::isfinite(u[0]) && std::isfinite(u[1]) && std::isfinite(u[2]); }
+
+af_status check_tool(const af_tool* t) {
+  if (!t) return fail(nullptr, AF_ERR_INVALID_ARG, "tool is NULL");
+  const float f[6] = {t->radius, t->length, t->self_excl, t->corr_radius, t->corr_length,
+                      t->cos_theta_max};
+  for (float x : f)
+    if (!std::isfinite(x)) return fail(nullptr, AF_ERR_INVALID_ARG, "non-finite tool parameter");
+  if (!(t->radius > 0.f) || t->length < 0.f || t->self_excl < 0.f || t->corr_radius < 0.f ||
+      t->corr_length < 0.f || t->n_c < 1 || t->n_c > 1000000 || t->cos_theta_max < -1.f ||
+      t->cos_theta_max > 1.f || (t->corridor_strict != 0 && t->corridor_strict != 1))
+    return fail(nullptr, AF_ERR_INVALID_ARG, "tool parameter out of range");
+  return AF_OK;
+}
+
+}  // namespace
+
+extern "C" af_status af_kernel_offsets(const af_tool* tool, float voxel_size, const float u[3],
+                                       int32_t which, int32_t* h_out, int64_t cap,
+                                       int64_t* count) {
+  af_status s = check_tool(tool);
+  if (s != AF_OK) return s;
+  if (!(voxel_size > 0.f) || !std::isfinite(voxel_size) || !u || !finite3(u) || !count ||
+      (which != AF_KERNEL_TOOL && which != AF_KERNEL_CORRIDOR) || cap < 0 || (cap > 0 && !h_out))
+    return fail(nullptr, AF_ERR_INVALID_ARG, "af_kernel_offsets: bad argument");
+  const double du[3] = {(double)u[0], (double)u[1], (double)u[2]};
+  const std::vector<Offset> offs = rasterise(*tool, (double)voxel_size, du, which);
+  *count = (int64_t)offs.size();
+  for (int64_t k = 0; k < std::min<int64_t>(cap, (int64_t)offs.size()); ++k) {
+    h_out[3 * k] = offs[k].x;
+    h_out[3 * k + 1] = offs[k].y;
+    h_out[3 * k + 2] = offs[k].z;
+  }
+  return AF_OK;
+}
+
+extern "C" af_status af_arm_offsets(float voxel_size, float truncation, const float u[3],
+                                    int32_t h_out[9]) {
+  if (!(voxel_size > 0.f) || !(truncation > 0.f) || !u || !finite3(u) || !h_out)
+    return fail(nullptr, AF_ERR_INVALID_ARG, "af_arm_offsets: bad argument");
+  const double du[3] = {(double)u[0], (double)u[1], (double)u[2]};
+  int o[9];
+  arm_offsets((double)voxel_size, (double)truncation, du, o);
+  for (int k = 0; k < 9; ++k) h_out[k] = o[k];
+  return AF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+static void free_tool(af_ctx* c) {
+  cudaFree(c->d_dirs);
+  cudaFree(c->d_runs);
+  cudaFree(c->d_dtab);
+  cudaFree(c->d_arm);
+  c->d_dirs = nullptr;
+  c->d_runs = nullptr;
+  c->d_dtab = nullptr;
+  c->d_arm = nullptr;
+  c->has_tool = false;
+}
+
+static void free_all(af_ctx* c) {
+  free_tool(c);
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  c->prof.clear();
+  c->ev_free.clear();
+  MapView& M = c->M;
+  cudaFree(M.hkeys);
+  cudaFree(M.hvals);
+  cudaFree(M.vox);
+  cudaFree(M.cleared);
+  cudaFree(M.bkey);
+  cudaFree(M.stamp);
+  cudaFree(M.dirty);
+  cudaFree(M.occ);
+  cudaFree(M.known);
+  cudaFree(M.ctl);
+  cudaFree(c->d_ret);
+  cudaFree(c->d_xyz);
+  cudaFree(c->d_pts);
+  cudaFree(c->d_nrm);
+  cudaFree(c->d_label);
+  cudaFree(c->d_best);
+  cudaFreeHost(c->h_status);
+}
+
+static af_status check_config(const af_config* c) {
+  auto bad = [](const char* what) { return fail(nullptr, AF_ERR_INVALID_ARG, "af_config: %s", what); };
+  const float f[8] = {c->voxel_size, c->truncation, c->r_c, c->cone_cos,
+                      c->range_min, c->range_max, c->clear_lo, c->clear_hi};
+  for (float x : f)
+    if (!std::isfinite(x)) return bad("non-finite parameter");
+  if (!(c->voxel_size > 0.f)) return bad("voxel_size must be > 0");
+  if (!(c->truncation > 0.f && c->truncation <= 1.f)) return bad("truncation must be in (0, 1] m");
+  if (!(c->r_c > 0.f && c->r_c <= 1.f)) return bad("r_c must be in (0, 1] m");
+  if (c->cone_cos < -1.f || c->cone_cos > 1.f) return bad("cone_cos must be in [-1, 1]");
+  if (!(c->range_min >= 0.f && c->range_max > c->range_min)) return bad("range bounds");
+  if (!(c->clear_lo >= 0.f && c->clear_hi >= c->clear_lo)) return bad("cleared band bounds");
+  if (c->cube_radius < 1 || c->cube_radius > 8) return bad("cube_radius must be in 1..8");
+  if (c->clear_samples < 0 || c->clear_samples > 64) return bad("clear_samples must be in 0..64");
+  if (c->block_edge != 8) return bad("block_edge must be 8");
+  if (c->w_cap < 1) return bad("w_cap must be >= 1");
+  if (c->max_returns < 1) return bad("max_returns must be >= 1");
+  if ((uint64_t)c->max_returns + c->w_cap >= (1ull << af::kWBits))
+    return bad("max_returns + w_cap must be below 2^20");
+  for (int k = 0; k < 3; ++k) {
+    if (c->domain_bricks[k] < 1 || c->domain_bricks[k] >= (1u << 21)) return bad("domain_bricks");
+    if (std::abs((int64_t)c->domain_min[k]) > (1 << 25) ||
+        std::abs((int64_t)c->domain_min[k] + c->domain_bricks[k]) > (1 << 25))
+      return bad("domain out of range");
+  }
+  if (c->hash_capacity < 2 || (c->hash_capacity & (c->hash_capacity - 1)) != 0 ||
+      c->hash_capacity > (1u << 31))
+    return bad("hash_capacity must be a power of two >= 2");
+  if (c->pool_blocks < 1 || c->pool_blocks >= 0xFFFFFFF0u) return bad("pool_blocks");
+  return AF_OK;
+}
+
+extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, AF_ERR_INVALID_ARG, "af_create: NULL argument");
+  *out = nullptr;
+  af_status s = check_config(cfg);
+  if (s != AF_OK) return s;
+  af_ctx* c = new af_ctx();
+  c->cfg = *cfg;
+  MapView& M = c->M;
+  M.v = cfg->voxel_size;
+  M.tau = cfg->truncation;
+  M.r_c = cfg->r_c;
+  M.cone_cos = cfg->cone_cos;
+  M.range_min = cfg->range_min;
+  M.range_max = cfg->range_max;
+  M.clear_lo = cfg->clear_lo;
+  M.clear_hi = cfg->clear_hi;
+  M.m = cfg->cube_radius;
+  M.ns = cfg->clear_samples;
+  M.w_min = cfg->w_min;
+  M.w_cap = cfg->w_cap;
+  M.rcq = (uint64_t)rintf(cfg->r_c * af::kScale);
+  for (int k = 0; k < 3; ++k) {
+    M.dom_vox[k] = cfg->domain_min[k] * 8;
+    M.dim_vox[k] = (int)cfg->domain_bricks[k] * 8;
+  }
+  M.row_words = (M.dim_vox[0] + 63) / 64;
+  M.hmask = cfg->hash_capacity - 1;
+  M.pool_blocks = cfg->pool_blocks;
+
+  auto alloc = [&](void** p, size_t bytes, int fill) -> af_status {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) e = cudaMemset(*p, fill, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      fail(c, AF_ERR_CUDA, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+      return AF_ERR_CUDA;
+    }
+    return AF_OK;
+  };
+  const size_t H = cfg->hash_capacity, P = cfg->pool_blocks;
+  const size_t plane = (size_t)M.row_words * 8 * M.dim_vox[1] * M.dim_vox[2];
+  const size_t R = cfg->max_returns, Pm = cfg->max_points;
+  af_status st = AF_OK;
+  if (st == AF_OK) st = alloc((void**)&M.hkeys, H * 8, 0xFF);
+  if (st == AF_OK) st = alloc((void**)&M.hvals, H * 4, 0xFF);
+  if (st == AF_OK) st = alloc((void**)&M.vox, P * af::kBrickVox * 8, 0);
+  if (st == AF_OK) st = alloc((void**)&M.cleared, P * 16 * 4, 0);
+  if (st == AF_OK) st = alloc((void**)&M.bkey, P * 8, 0);
+  if (st == AF_OK) st = alloc((void**)&M.stamp, P * 4, 0);
+  if (st == AF_OK) st = alloc((void**)&M.dirty, P * 4, 0);
+  if (st == AF_OK) st = alloc((void**)&M.occ, plane, 0);
+  if (st == AF_OK) st = alloc((void**)&M.known, plane, 0);
+  if (st == AF_OK) st = alloc((void**)&M.ctl, sizeof(af::Control), 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_ret, R * sizeof(float4), 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_xyz, R * 12, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_pts, Pm * 12, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_nrm, Pm * 12, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_label, Pm, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_best, Pm * 2, 0);
+  if (st == AF_OK && cudaMallocHost((void**)&c->h_status, 64) != cudaSuccess)
+    st = fail(c, AF_ERR_CUDA, "pinned allocation failed");
+  int dev = 0;
+  if (st == AF_OK && (cudaGetDevice(&dev) != cudaSuccess ||
+                      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) !=
+                          cudaSuccess))
+    st = fail(c, AF_ERR_CUDA, "device query failed");
+  if (st == AF_OK && cudaDeviceSynchronize() != cudaSuccess)
+    st = fail(c, AF_ERR_CUDA, "initialisation failed");
+  if (st != AF_OK) {
+    snprintf(g_err, sizeof g_err, "%s", c->err);
+    free_all(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return AF_OK;
+}
+
+extern "C" af_status af_destroy(af_ctx* ctx) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_destroy: NULL context");
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+  return AF_OK;
+}
+
+extern "C" af_status af_integrate_scan(af_ctx* ctx, const float* d_xyz, uint32_t n,
+                                       const float pose[16], void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_integrate_scan: NULL context");
+  if (!pose) return fail(ctx, AF_ERR_INVALID_ARG, "af_integrate_scan: NULL pose");
+  if (n > 0 && !d_xyz) return fail(ctx, AF_ERR_INVALID_ARG, "af_integrate_scan: NULL points");
+  if (n > ctx->cfg.max_returns)
+    return fail(ctx, AF_ERR_CAPACITY, "af_integrate_scan: n = %u exceeds max_returns = %u", n,
+                ctx->cfg.max_returns);
+  for (int k = 0; k < 12; ++k)
+    if (!std::isfinite(pose[k])) return fail(ctx, AF_ERR_INVALID_ARG, "non-finite pose");
+  ctx->frame = ctx->frame + 1 == 0 ? 1 : ctx->frame + 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  const MapView& M = ctx->M;
+  AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, s); }));
+  if (n > 0)
+    AF_CUDA(ctx, timed(ctx, 1, s, [&] { return af::launch_cube(M, n, pose, ctx->d_ret, ctx->frame, s); }));
+  AF_CUDA(ctx, timed(ctx, 2, s, [&] { return af::launch_bitview(M, ctx->num_sms, s); }));
+  ctx->last_stream = s;
+  ctx->scans++;
+  ctx->returns_in += n;
+  return AF_OK;
+}
+
+extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* h_dirs,
+                                 uint32_t G) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_set_tool: NULL context");
+  af_status s = check_tool(tool);
+  if (s != AF_OK) return fail(ctx, s, "%s", g_err);
+  if (!h_dirs || G < 1 || G > 4096) return fail(ctx, AF_ERR_INVALID_ARG, "af_set_tool: need 1 <= G <= 4096 directions");
+  for (uint32_t g = 0; g < G; ++g)
+    if (!finite3(h_dirs + 3 * g)) return fail(ctx, AF_ERR_INVALID_ARG, "non-finite direction");
+
+  const double v = (double)ctx->cfg.voxel_size, tau = (double)ctx->cfg.truncation;
+  std::vector<short4> runs;
+  std::vector<int4> dtab(G);
+  std::vector<short4> arm(3 * G);
+  for (uint32_t g = 0; g < G; ++g) {
+    const double u[3] = {(double)h_dirs[3 * g], (double)h_dirs[3 * g + 1], (double)h_dirs[3 * g + 2]};
+    const std::vector<Offset> tool_o = rasterise(*tool, v, u, AF_KERNEL_TOOL);
+    const std::vector<Offset> corr_o = rasterise(*tool, v, u, AF_KERNEL_CORRIDOR);
+    for (const std::vector<Offset>* o : {&tool_o, &corr_o})
+      for (const Offset& x : *o)
+        if (std::abs(x.x) > 32000 || std::abs(x.y) > 32000 || std::abs(x.z) > 32000)
+          return fail(ctx, AF_ERR_INVALID_ARG, "tool reach exceeds 32000 voxels");
+    dtab[g].x = (int)runs.size();
+    to_runs(tool_o, v, u, &runs);
+    dtab[g].y = (int)runs.size();
+    dtab[g].z = (int)runs.size();
+    to_runs(corr_o, v, u, &runs);
+    dtab[g].w = (int)runs.size();
+    int a[9];
+    arm_offsets(v, tau, u, a);
+    for (int k = 0; k < 3; ++k)
+      arm[3 * g + k] = make_short4((short)a[3 * k], (short)a[3 * k + 1], (short)a[3 * k + 2], 0);
+  }
+  if (runs.empty()) runs.push_back(make_short4(0, 1, 0, 0));  // keep the buffer non-empty
+  AF_CUDA(ctx, cudaDeviceSynchronize());
+  free_tool(ctx);
+  AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_dirs, (size_t)G * 12));
+  AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_runs, runs.size() * sizeof(short4)));
+  AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_dtab, (size_t)G * sizeof(int4)));
+  AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_arm, (size_t)G * 3 * sizeof(short4)));
+  AF_CUDA(ctx, cudaMemcpy(ctx->d_dirs, h_dirs, (size_t)G * 12, cudaMemcpyHostToDevice));
+  AF_CUDA(ctx, cudaMemcpy(ctx->d_runs, runs.data(), runs.size() * sizeof(short4), cudaMemcpyHostToDevice));
+  AF_CUDA(ctx, cudaMemcpy(ctx->d_dtab, dtab.data(), (size_t)G * sizeof(int4), cudaMemcpyHostToDevice));
+  AF_CUDA(ctx, cudaMemcpy(ctx->d_arm, arm.data(), (size_t)G * 3 * sizeof(short4), cudaMemcpyHostToDevice));
+  ctx->T.dirs = ctx->d_dirs;
+  ctx->T.runs = ctx->d_runs;
+  ctx->T.dtab = ctx->d_dtab;
+  ctx->T.arm = ctx->d_arm;
+  ctx->T.G = (int)G;
+  ctx->T.n_c = (int)tool->n_c;
+  ctx->T.cos_max = tool->cos_theta_max;
+  ctx->T.strict = tool->corridor_strict;
+  ctx->has_tool = true;
+  return AF_OK;
+}
+
+extern "C" af_status af_score(af_ctx* ctx, const float* d_pts, const float* d_normals,
+                              uint32_t m, uint8_t* d_label, int16_t* d_best, void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_score: NULL context");
+  if (!ctx->has_tool) return fail(ctx, AF_ERR_STATE, "af_score: call af_set_tool first");
+  if (m > 0 && (!d_pts || !d_normals || !d_label || !d_best))
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_score: NULL buffer");
+  if (m > (1u << 31)) return fail(ctx, AF_ERR_INVALID_ARG, "af_score: m too large");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m > 0)
+    AF_CUDA(ctx, timed(ctx, 3, s, [&] {
+              return af::launch_score(ctx->M, ctx->T, d_pts, d_normals, m, d_label, d_best, s);
+            }));
+  ctx->last_stream = s;
+  ctx->points_in += m;
+  return AF_OK;
+}
+
+extern "C" af_status af_frame_host(af_ctx* ctx, const float* h_xyz, uint32_t n,
+                                   const float pose[16], const float* h_pts,
+                                   const float* h_normals, uint32_t m, uint8_t* h_label,
+                                   int16_t* h_best, void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_frame_host: NULL context");
+  if (n > ctx->cfg.max_returns || m > ctx->cfg.max_points)
+    return fail(ctx, AF_ERR_CAPACITY, "af_frame_host: n or m exceeds max_returns / max_points");
+  if ((n > 0 && !h_xyz) || (m > 0 && (!h_pts || !h_normals || !h_label || !h_best)))
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_frame_host: NULL buffer");
+  if (m > 0 && !ctx->has_tool) return fail(ctx, AF_ERR_STATE, "af_frame_host: call af_set_tool first");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > 0) AF_CUDA(ctx, cudaMemcpyAsync(ctx->d_xyz, h_xyz, (size_t)n * 12, cudaMemcpyHostToDevice, s));
+  if (m > 0) {
+    AF_CUDA(ctx, cudaMemcpyAsync(ctx->d_pts, h_pts, (size_t)m * 12, cudaMemcpyHostToDevice, s));
+    AF_CUDA(ctx, cudaMemcpyAsync(ctx->d_nrm, h_normals, (size_t)m * 12, cudaMemcpyHostToDevice, s));
+  }
+  af_status st = af_integrate_scan(ctx, ctx->d_xyz, n, pose, stream);
+  if (st != AF_OK) return st;
+  if (m > 0) {
+    st = af_score(ctx, ctx->d_pts, ctx->d_nrm, m, ctx->d_label, ctx->d_best, stream);
+    if (st != AF_OK) return st;
+    AF_CUDA(ctx, cudaMemcpyAsync(h_label, ctx->d_label, m, cudaMemcpyDeviceToHost, s));
+    AF_CUDA(ctx, cudaMemcpyAsync(h_best, ctx->d_best, (size_t)m * 2, cudaMemcpyDeviceToHost, s));
+  }
+  AF_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, &ctx->M.ctl->status, 4, cudaMemcpyDeviceToHost, s));
+  AF_CUDA(ctx, cudaStreamSynchronize(s));
+  if (*ctx->h_status != 0)
+    return fail(ctx, (af_status)*ctx->h_status, "map capacity exceeded; integration stopped");
+  return AF_OK;
+}
+
+extern "C" af_status af_sync_status(af_ctx* ctx) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_sync_status: NULL context");
+  AF_CUDA(ctx, cudaDeviceSynchronize());
+  uint32_t st = 0;
+  AF_CUDA(ctx, cudaMemcpy(&st, &ctx->M.ctl->status, 4, cudaMemcpyDeviceToHost));
+  if (st != 0) return fail(ctx, (af_status)st, "map capacity exceeded; integration stopped");
+  return AF_OK;
+}
+
+extern "C" af_status af_get_stats(af_ctx* ctx, af_stats* out) {
+  if (!ctx || !out) return fail(ctx, AF_ERR_INVALID_ARG, "af_get_stats: NULL argument");
+  AF_CUDA(ctx, cudaDeviceSynchronize());
+  af::Control c;
+  AF_CUDA(ctx, cudaMemcpy(&c, ctx->M.ctl, sizeof c, cudaMemcpyDeviceToHost));
+  out->scans = ctx->scans;
+  out->returns_in = ctx->returns_in;
+  out->returns_accepted = c.returns_accepted;
+  out->blocks_allocated = std::min<uint64_t>(c.pool_count, ctx->cfg.pool_blocks);
+  out->blocks_dirty_last = c.dirty_count;
+  out->points_in = ctx->points_in;
+  out->points_scored = c.points_scored;
+  out->tests = c.tests;
+  return AF_OK;
+}
+
+extern "C" af_status af_block_count(af_ctx* ctx, uint32_t* out) {
+  if (!ctx || !out) return fail(ctx, AF_ERR_INVALID_ARG, "af_block_count: NULL argument");
+  AF_CUDA(ctx, cudaDeviceSynchronize());
+  uint32_t pc = 0;
+  AF_CUDA(ctx, cudaMemcpy(&pc, &ctx->M.ctl->pool_count, 4, cudaMemcpyDeviceToHost));
+  *out = std::min(pc, ctx->cfg.pool_blocks);
+  return AF_OK;
+}
+
+extern "C" af_status af_export_blocks(af_ctx* ctx, uint32_t cap, int32_t* h_key, uint64_t* h_S,
+                                      uint32_t* h_w, uint8_t* h_flags, uint32_t* out_count) {
+  if (!ctx || !out_count) return fail(ctx, AF_ERR_INVALID_ARG, "af_export_blocks: NULL argument");
+  if (cap > 0 && (!h_key || !h_S || !h_w || !h_flags))
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_export_blocks: NULL buffer");
+  uint32_t count = 0;
+  af_status s = af_block_count(ctx, &count);
+  if (s != AF_OK) return s;
+  count = std::min(count, cap);
+  *out_count = count;
+  if (count == 0) return AF_OK;
+  std::vector<uint64_t> keys(count), words((size_t)count * af::kBrickVox);
+  AF_CUDA(ctx, cudaMemcpy(keys.data(), ctx->M.bkey, (size_t)count * 8, cudaMemcpyDeviceToHost));
+  AF_CUDA(ctx, cudaMemcpy(words.data(), ctx->M.vox, words.size() * 8, cudaMemcpyDeviceToHost));
+  uint8_t* d_flags = nullptr;
+  AF_CUDA(ctx, cudaMalloc((void**)&d_flags, (size_t)count * af::kBrickVox));
+  cudaError_t e = af::launch_export_flags(ctx->M, count, d_flags, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h_flags, d_flags, (size_t)count * af::kBrickVox, cudaMemcpyDeviceToHost);
+  cudaFree(d_flags);
+  if (e != cudaSuccess) return fail(ctx, AF_ERR_CUDA, "export failed: %s", cudaGetErrorString(e));
+  for (uint32_t b = 0; b < count; ++b) {
+    const uint64_t k = keys[b];
+    h_key[3 * b] = (int32_t)(k & 0x1FFFFF) + ctx->cfg.domain_min[0];
+    h_key[3 * b + 1] = (int32_t)((k >> 21) & 0x1FFFFF) + ctx->cfg.domain_min[1];
+    h_key[3 * b + 2] = (int32_t)(k >> 42) + ctx->cfg.domain_min[2];
+    for (int l = 0; l < af::kBrickVox; ++l) {
+      const uint64_t wd = words[(size_t)b * af::kBrickVox + l];
+      h_S[(size_t)b * af::kBrickVox + l] = wd >> af::kWBits;
+      h_w[(size_t)b * af::kBrickVox + l] = (uint32_t)(wd & af::kWMask);
+    }
+  }
+  return AF_OK;
+}
+
+extern "C" af_status af_profile_enable(af_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_profile_enable: NULL context");
+  ctx->prof_on = enable != 0;
+  return AF_OK;
+}
+
+extern "C" af_status af_profile_read(af_ctx* ctx, af_profile* out, int reset) {
+  if (!ctx || !out) return fail(ctx, AF_ERR_INVALID_ARG, "af_profile_read: NULL argument");
+  AF_CUDA(ctx, cudaDeviceSynchronize());
+  std::memset(out, 0, sizeof *out);
+  for (const auto& r : ctx->prof) {
+    float ms = 0.f;
+    AF_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+    out->launches[r.kernel] += 1;
+    out->ms[r.kernel] += ms;
+  }
+  if (reset) {
+    for (auto& r : ctx->prof) {
+      ctx->ev_free.push_back(r.a);
+      ctx->ev_free.push_back(r.b);
+    }
+    ctx->prof.clear();
+  }
+  return AF_OK;
+}

@@ -1,0 +1,362 @@
+// af_integrate.cu -- scan-centric TSDF integration on sm_103a (Sec. 3.2, 3.4,
+// 3.6 of the paper), three launches per scan:
+//
+//  k_alloc     one thread per return: pose transform, validity, voxel index;
+//              inserts the bricks of its (2m+1)^3 cube and of its ray-cleared
+//              band samples into the hash. Lanes of a warp that carry the same
+//              brick key are merged with __match_any_sync, so one CAS per
+//              distinct key per warp reaches L2.
+//  k_integrate one CTA per tile of 32 returns: resolves each return's bricks
+//              once into shared memory, marks the cleared band, then one
+//              thread per (return, cube offset) pair computes d and adds
+//              (round(d 2^20) << 20) | 1 to the voxel word with one 64-bit
+//              atomic. Integer addition makes the result order-independent.
+//  k_bitview   persistent over the scan's dirty bricks: weight cap with
+//              proportional rescale, then occupied / known bits packed with
+//              __ballot_sync into the dense bit planes.
+//
+// Every floating-point operation that decides an integer is an explicitly
+// rounded IEEE single-precision intrinsic, in the order the method states
+// it, so the result is reproducible bit for bit on any IEEE machine.
+#include "af_internal.cuh"
+
+namespace af {
+
+struct Pose {
+  float r[3][4];  // row-major [R | t]
+};
+
+// Transform, validate, voxel-index one return. Returns false if dropped.
+__device__ inline bool prepare_return(const MapView& M, const Pose& P, float sx, float sy,
+                                      float sz, float p[3], float* range, int rel[3]) {
+  if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) return false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    p[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P.r[r][0], sx), __fmul_rn(P.r[r][1], sy)),
+                               __fmul_rn(P.r[r][2], sz)),
+                     P.r[r][3]);
+  const float b0 = __fsub_rn(p[0], P.r[0][3]);
+  const float b1 = __fsub_rn(p[1], P.r[1][3]);
+  const float b2 = __fsub_rn(p[2], P.r[2][3]);
+  const float bb = __fadd_rn(__fadd_rn(__fmul_rn(b0, b0), __fmul_rn(b1, b1)), __fmul_rn(b2, b2));
+  *range = __fsqrt_rn(bb);
+  if (!(*range >= M.range_min && *range <= M.range_max)) return false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int i;
+    if (!voxel_index(p[k], M.v, &i)) return false;
+    rel[k] = i - M.dom_vox[k];
+    if (rel[k] - M.m < 0 || rel[k] + M.m >= M.dim_vox[k]) return false;
+  }
+  return true;
+}
+
+// Sample s (1..ns) of the ray-cleared band toward the sensor. Returns the
+// domain-relative voxel, or false if it falls outside the map box.
+__device__ inline bool band_sample(const MapView& M, const float p[3], const float q[3],
+                                   float range, int s, int rel[3]) {
+  const float step = __fdiv_rn(__fmul_rn(__fsub_rn(M.clear_hi, M.clear_lo), M.tau), (float)M.ns);
+  const float start = __fmul_rn(M.clear_lo, M.tau);
+  const float dist = __fadd_rn(start, __fmul_rn((float)s, step));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = __fdiv_rn(__fsub_rn(q[k], p[k]), range);
+    int i;
+    if (!voxel_index(__fadd_rn(p[k], __fmul_rn(dist, u)), M.v, &i)) return false;
+    rel[k] = i - M.dom_vox[k];
+    if (rel[k] < 0 || rel[k] >= M.dim_vox[k]) return false;
+  }
+  return true;
+}
+
+// Inserts a brick key; the inserting thread takes a pool index. Bounded probe.
+__device__ void insert_brick(const MapView& M, uint64_t key) {
+  uint32_t h = hash_slot(key, M.hmask);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(M.hkeys);
+  for (uint32_t probe = 0; probe <= M.hmask; ++probe) {
+    const unsigned long long k = __ldcg(keys + h);
+    if (k == key) return;
+    if (k == kEmptyKey) {
+      const unsigned long long prev = atomicCAS(keys + h, kEmptyKey, key);
+      if (prev == kEmptyKey) {
+        const uint32_t idx = atomicAdd(&M.ctl->pool_count, 1u);
+        if (idx < M.pool_blocks) {
+          M.bkey[idx] = key;
+          M.hvals[h] = idx;
+        } else {
+          M.hvals[h] = kNoBlock;
+          latch_status(M.ctl, kStatusCapacity);
+        }
+        return;
+      }
+      if (prev == key) return;
+    }
+    h = (h + 1) & M.hmask;
+  }
+  latch_status(M.ctl, kStatusCapacity);
+}
+
+__global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restrict__ xyz,
+                                                uint32_t n, Pose P, float4* __restrict__ ret) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  if (k == 0) M.ctl->dirty_count = 0;
+
+  float p[3] = {0.f, 0.f, 0.f}, range = 0.f;
+  int rel[3] = {0, 0, 0};
+  bool valid = false;
+  if (k < n) {
+    valid = prepare_return(M, P, xyz[3 * k], xyz[3 * k + 1], xyz[3 * k + 2], p, &range, rel);
+    ret[k] = make_float4(p[0], p[1], p[2], valid ? 1.f : 0.f);
+  }
+  const unsigned acc = __ballot_sync(0xffffffffu, valid);
+  if (lane == 0 && acc) atomicAdd(&M.ctl->returns_accepted, (unsigned long long)__popc(acc));
+
+  int b0[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  if (valid) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b0[a] = (rel[a] - M.m) >> 3;
+      nb[a] = ((rel[a] + M.m) >> 3) - b0[a] + 1;
+    }
+  }
+  const int ncube = valid ? nb[0] * nb[1] * nb[2] : 0;
+  const int total = valid ? ncube + M.ns : 0;
+  const float q[3] = {P.r[0][3], P.r[1][3], P.r[2][3]};
+  uint64_t last = kEmptyKey;
+  for (int kk = 0;; ++kk) {
+    const bool have = kk < total;
+    if (__ballot_sync(0xffffffffu, have) == 0u) break;
+    uint64_t key = kEmptyKey;
+    if (have) {
+      if (kk < ncube) {
+        const int bx = kk % nb[0], by = (kk / nb[0]) % nb[1], bz = kk / (nb[0] * nb[1]);
+        key = pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz);
+      } else {
+        int sv[3];
+        if (band_sample(M, p, q, range, kk - ncube + 1, sv))
+          key = pack_brick(sv[0] >> 3, sv[1] >> 3, sv[2] >> 3);
+      }
+    }
+    const bool ins = key != kEmptyKey && key != last;
+    if (ins) last = key;
+    const unsigned act = __ballot_sync(0xffffffffu, ins);
+    if (ins) {
+      const unsigned peers = __match_any_sync(act, key);
+      if (lane == __ffs(peers) - 1) insert_brick(M, key);
+    }
+  }
+}
+
+__device__ inline void mark_dirty(const MapView& M, uint32_t blk, uint32_t frame) {
+  if (atomicExch(M.stamp + blk, frame) != frame) {
+    const uint32_t d = atomicAdd(&M.ctl->dirty_count, 1u);
+    M.dirty[d] = blk;
+  }
+}
+
+// W = 2m + 1 voxels per cube edge; BA = bricks a cube edge can span.
+template <int W>
+__global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __restrict__ ret,
+                                                    uint32_t n, float q0, float q1, float q2,
+                                                    uint32_t frame) {
+  constexpr int T = 32;
+  constexpr int C = W * W * W;
+  constexpr int BA = (W + 6) / 8 + 1;
+  constexpr int NB = BA * BA * BA;
+  constexpr int MR = W / 2;
+  __shared__ float4 s_p[T];        // p, valid flag
+  __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
+  __shared__ int4 s_b0[T];         // first brick of the cube, w = nb packed
+  __shared__ uint32_t s_blk[T][NB];
+
+  if (__ldcg(&M.ctl->status) != 0u) return;  // sticky capacity error: skip the scan
+  const int tid = threadIdx.x;
+  const uint32_t r0 = blockIdx.x * T;
+  const float q[3] = {q0, q1, q2};
+
+  if (tid < T) {
+    const uint32_t k = r0 + tid;
+    float4 p = k < n ? ret[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 rel = make_int4(0, 0, 0, 0), b0 = make_int4(0, 0, 0, 0);
+    if (p.w != 0.f) {
+      const float b[3] = {__fsub_rn(p.x, q0), __fsub_rn(p.y, q1), __fsub_rn(p.z, q2)};
+      const float bb =
+          __fadd_rn(__fadd_rn(__fmul_rn(b[0], b[0]), __fmul_rn(b[1], b[1])), __fmul_rn(b[2], b[2]));
+      const float range = __fsqrt_rn(bb);
+      int i[3];
+      voxel_index(p.x, M.v, &i[0]);
+      voxel_index(p.y, M.v, &i[1]);
+      voxel_index(p.z, M.v, &i[2]);
+      rel = make_int4(i[0] - M.dom_vox[0], i[1] - M.dom_vox[1], i[2] - M.dom_vox[2],
+                      __float_as_int(range));
+      b0 = make_int4((rel.x - MR) >> 3, (rel.y - MR) >> 3, (rel.z - MR) >> 3, 0);
+      const int nbx = ((rel.x + MR) >> 3) - b0.x + 1, nby = ((rel.y + MR) >> 3) - b0.y + 1,
+                nbz = ((rel.z + MR) >> 3) - b0.z + 1;
+      b0.w = nbx | (nby << 4) | (nbz << 8);
+    }
+    s_p[tid] = p;
+    s_rel[tid] = rel;
+    s_b0[tid] = b0;
+  }
+  __syncthreads();
+
+  // Resolve each return's bricks once.
+  for (int e = tid; e < T * NB; e += blockDim.x) {
+    const int t = e / NB, j = e % NB;
+    const int bx = j % BA, by = (j / BA) % BA, bz = j / (BA * BA);
+    uint32_t blk = kNoBlock;
+    const int4 b0 = s_b0[t];
+    if (s_p[t].w != 0.f && bx < (b0.w & 15) && by < ((b0.w >> 4) & 15) &&
+        bz < ((b0.w >> 8) & 15)) {
+      blk = lookup_brick(M, pack_brick(b0.x + bx, b0.y + by, b0.z + bz));
+      if (blk != kNoBlock) mark_dirty(M, blk, frame);
+    }
+    s_blk[t][j] = blk;
+  }
+  // Ray-cleared band toward the sensor (append-only, does not touch S or w).
+  for (int e = tid; e < T * M.ns; e += blockDim.x) {
+    const int t = e / M.ns, s = e % M.ns + 1;
+    if (s_p[t].w == 0.f) continue;
+    const float p[3] = {s_p[t].x, s_p[t].y, s_p[t].z};
+    int sv[3];
+    if (!band_sample(M, p, q, __int_as_float(s_rel[t].w), s, sv)) continue;
+    const uint32_t blk = lookup_brick(M, pack_brick(sv[0] >> 3, sv[1] >> 3, sv[2] >> 3));
+    if (blk == kNoBlock) continue;
+    const int l = (sv[0] & 7) | ((sv[1] & 7) << 3) | ((sv[2] & 7) << 6);
+    atomicOr(M.cleared + blk * 16 + (l >> 5), 1u << (l & 31));
+    mark_dirty(M, blk, frame);
+  }
+  __syncthreads();
+
+  const float v = M.v, tau = M.tau, cone = M.cone_cos;
+  for (int e = tid; e < T * C; e += blockDim.x) {
+    const int t = e / C, o = e % C;
+    const float4 p = s_p[t];
+    if (p.w == 0.f) continue;
+    const int4 rel = s_rel[t];
+    const float range = __int_as_float(rel.w);
+    const int jx = rel.x + (o % W) - MR;
+    const int jy = rel.y + (o / W) % W - MR;
+    const int jz = rel.z + o / (W * W) - MR;
+    // voxel centre x (absolute index)
+    const float x0 = voxel_centre(jx + M.dom_vox[0], v);
+    const float x1 = voxel_centre(jy + M.dom_vox[1], v);
+    const float x2 = voxel_centre(jz + M.dom_vox[2], v);
+    // behind-surface cone: theta between x - p and p - q
+    const float a0 = __fsub_rn(x0, p.x), a1 = __fsub_rn(x1, p.y), a2 = __fsub_rn(x2, p.z);
+    const float aa = __fadd_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(a1, a1)), __fmul_rn(a2, a2));
+    if (aa > 0.f) {
+      const float b0 = __fsub_rn(p.x, q0), b1 = __fsub_rn(p.y, q1), b2 = __fsub_rn(p.z, q2);
+      const float dot =
+          __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));
+      const float cos_theta = __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range));
+      if (cos_theta > cone) continue;
+    }
+    // d = |p - q| - |x - q|, clamped to [0, tau]
+    const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
+    const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
+    float d = __fsub_rn(range, __fsqrt_rn(cc));
+    d = d < 0.f ? 0.f : d;
+    d = d > tau ? tau : d;
+    const unsigned long long dq = (unsigned long long)__float2uint_rn(__fmul_rn(d, kScale));
+    const int4 b0 = s_b0[t];
+    const int bl = ((jx >> 3) - b0.x) + BA * (((jy >> 3) - b0.y) + BA * ((jz >> 3) - b0.z));
+    const uint32_t blk = s_blk[t][bl];
+    if (blk == kNoBlock) continue;
+    const int l = (jx & 7) | ((jy & 7) << 3) | ((jz & 7) << 6);
+    atomicAdd(M.vox + (size_t)blk * kBrickVox + l, (dq << kWBits) | 1ull);
+  }
+}
+
+// Weight cap and bit view of every brick touched by the scan.
+__global__ void __launch_bounds__(512) k_bitview(MapView M) {
+  const uint32_t count = __ldcg(&M.ctl->dirty_count);
+  const int l = threadIdx.x;
+  const int lane = l & 31, wi = l >> 5;
+  unsigned char* occ = reinterpret_cast<unsigned char*>(M.occ);
+  unsigned char* known = reinterpret_cast<unsigned char*>(M.known);
+  const size_t row_bytes = (size_t)M.row_words * 8;
+  for (uint32_t d = blockIdx.x; d < count; d += gridDim.x) {
+    const uint32_t blk = M.dirty[d];
+    const uint64_t key = M.bkey[blk];
+    unsigned long long* wp = M.vox + (size_t)blk * kBrickVox + l;
+    unsigned long long word = *wp;
+    unsigned long long w = word & kWMask, S = word >> kWBits;
+    if (w > M.w_cap) {
+      S = S * M.w_cap / w;  // S < 2^44 and w_cap < 2^20: no overflow
+      w = M.w_cap;
+      *wp = (S << kWBits) | w;
+    }
+    const bool o = w >= 1 && S < M.rcq * w;
+    const bool cl = (M.cleared[blk * 16 + wi] >> lane) & 1u;
+    const bool kn = w >= 1 || cl;
+    const unsigned ob = __ballot_sync(0xffffffffu, o);
+    const unsigned kb = __ballot_sync(0xffffffffu, kn);
+    if (lane < 4) {
+      const uint32_t bx = (uint32_t)(key & 0x1FFFFF), by = (uint32_t)((key >> 21) & 0x1FFFFF),
+                     bz = (uint32_t)(key >> 42);
+      const size_t y = (size_t)by * 8 + (wi & 1) * 4 + lane;
+      const size_t z = (size_t)bz * 8 + (wi >> 1);
+      const size_t at = (z * (size_t)M.dim_vox[1] + y) * row_bytes + bx;
+      occ[at] = (unsigned char)(ob >> (8 * lane));
+      known[at] = (unsigned char)(kb >> (8 * lane));
+    }
+  }
+}
+
+// Per-voxel flags of allocated bricks for export: bit0 cleared, bit1
+// occupied, bit2 known.
+__global__ void __launch_bounds__(512) k_export_flags(MapView M, uint8_t* __restrict__ flags) {
+  const uint32_t blk = blockIdx.x;
+  const int l = threadIdx.x;
+  const uint64_t key = M.bkey[blk];
+  const int x = (int)(key & 0x1FFFFF) * 8 + (l & 7);
+  const int y = (int)((key >> 21) & 0x1FFFFF) * 8 + ((l >> 3) & 7);
+  const int z = (int)(key >> 42) * 8 + (l >> 6);
+  const size_t word = ((size_t)z * M.dim_vox[1] + y) * M.row_words + (x >> 6);
+  const unsigned cl = (M.cleared[blk * 16 + (l >> 5)] >> (l & 31)) & 1u;
+  const unsigned oc = (unsigned)(M.occ[word] >> (x & 63)) & 1u;
+  const unsigned kn = (unsigned)(M.known[word] >> (x & 63)) & 1u;
+  flags[(size_t)blk * kBrickVox + l] = (uint8_t)(cl | (oc << 1) | (kn << 2));
+}
+
+cudaError_t launch_export_flags(const MapView& M, uint32_t count, uint8_t* d_flags,
+                                cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  k_export_flags<<<count, 512, 0, stream>>>(M, d_flags);
+  cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : cudaStreamSynchronize(stream);
+}
+
+// Host-side launchers of the three integration kernels (on `stream`).
+cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const float pose[16],
+                         float4* d_ret, cudaStream_t stream) {
+  if (n == 0) return cudaMemsetAsync(&M.ctl->dirty_count, 0, sizeof(uint32_t), stream);
+  Pose P;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) P.r[r][c] = pose[4 * r + c];
+  k_alloc<<<(n + 255) / 256, 256, 0, stream>>>(M, d_xyz, n, P, d_ret);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], const float4* d_ret,
+                        uint32_t frame, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (n + 31) / 32;
+  switch (2 * M.m + 1) {
+#define AF_CASE(W) \
+  case W: k_integrate<W><<<grid, 256, 0, stream>>>(M, d_ret, n, pose[3], pose[7], pose[11], frame); break;
+    AF_CASE(3) AF_CASE(5) AF_CASE(7) AF_CASE(9) AF_CASE(11) AF_CASE(13) AF_CASE(15) AF_CASE(17)
+#undef AF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream) {
+  k_bitview<<<num_sms * 4, 512, 0, stream>>>(M);
+  return cudaGetLastError();
+}
+
+}  // namespace af

@@ -1,0 +1,133 @@
+// af_internal.cuh -- device-side layout shared by the integration and scoring
+// kernels of libaf (sm_103a).
+//
+// Map layout in HBM (all allocated once in af_create):
+//  * hash   : open addressing, hash_capacity slots of (u64 brick key, u32 pool
+//             index). Keys are domain-relative brick coordinates packed 21 bits
+//             per axis; ~0 marks an empty slot, ~0u an unusable index.
+//  * pool   : bricks of 8^3 voxels. Each voxel is ONE u64 word holding
+//             (S << 20) | w, so a contribution is a single 64-bit atomic add
+//             of (round(d 2^20) << 20) | 1 and integer addition makes the sum
+//             independent of the order of the returns. w < 2^20 is guaranteed
+//             by max_returns + w_cap < 2^20 and S < 2^44 by tau <= 1 m.
+//             Next to it: 512 cleared bits per brick, the brick key, a frame
+//             stamp for dirty-brick deduplication.
+//  * planes : the occupied and known views as dense bit planes over the map
+//             box, one bit per voxel, rows along x (64 voxels per u64 word),
+//             row index z * Y + y. A brick row of 8 voxels is one byte, so the
+//             view of a brick is 64 byte stores per plane.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace af {
+
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr uint32_t kNoBlock = ~0u;
+constexpr int kBrick = 8;
+constexpr int kBrickVox = 512;
+constexpr int kWBits = 20;
+constexpr uint64_t kWMask = (1ull << kWBits) - 1;
+constexpr float kScale = 1048576.0f;  // 2^20
+
+// Latched device status (values of af_status).
+constexpr uint32_t kStatusCapacity = 2;
+
+struct Control {
+  uint32_t status;       // latched af_status of device-side failures
+  uint32_t pool_count;   // bricks handed out
+  uint32_t dirty_count;  // bricks touched by the current scan
+  uint32_t pad;
+  unsigned long long returns_accepted;
+  unsigned long long points_scored;
+  unsigned long long tests;
+};
+
+// Everything a kernel needs about the map; passed by value.
+struct MapView {
+  // geometry
+  float v, tau, r_c, cone_cos, range_min, range_max, clear_lo, clear_hi;
+  int m;              // cube radius
+  int ns;             // cleared-band samples
+  uint32_t w_min, w_cap;
+  uint64_t rcq;       // round(r_c 2^20)
+  int dom_vox[3];     // absolute voxel index of the box's min corner
+  int dim_vox[3];     // box size in voxels (multiples of 8)
+  int row_words;      // u64 words per plane row
+  // hash
+  uint64_t* hkeys;
+  uint32_t* hvals;
+  uint32_t hmask;     // capacity - 1
+  // pool
+  unsigned long long* vox;  // pool_blocks * 512 packed words
+  uint32_t* cleared;        // pool_blocks * 16
+  uint64_t* bkey;           // pool_blocks
+  uint32_t* stamp;          // pool_blocks
+  uint32_t* dirty;          // pool_blocks
+  uint32_t pool_blocks;
+  // planes
+  unsigned long long* occ;
+  unsigned long long* known;
+  Control* ctl;
+};
+
+// Tool tables on the device (built by af_set_tool).
+struct ToolView {
+  const float* dirs;      // G x 3 unit directions
+  const short4* runs;     // x-runs (dx0, len, dy, dz), len in 1..64
+  const int4* dtab;       // per direction: tool runs [x, y), corridor runs [z, w)
+  const short4* arm;      // G x 3 arm-sample offsets
+  int G;
+  int n_c;
+  float cos_max;
+  int strict;
+};
+
+__host__ __device__ inline uint64_t pack_brick(uint32_t bx, uint32_t by, uint32_t bz) {
+  return (uint64_t)bx | ((uint64_t)by << 21) | ((uint64_t)bz << 42);
+}
+
+__device__ inline uint32_t hash_slot(uint64_t key, uint32_t mask) {
+  // splitmix64 finaliser
+  key ^= key >> 30;
+  key *= 0xbf58476d1ce4e5b9ull;
+  key ^= key >> 27;
+  key *= 0x94d049bb133111ebull;
+  key ^= key >> 31;
+  return (uint32_t)key & mask;
+}
+
+// Pool index of a brick, or kNoBlock. Read-only probe; never spins: at most
+// hmask + 1 slots are visited.
+__device__ inline uint32_t lookup_brick(const MapView& M, uint64_t key) {
+  uint32_t h = hash_slot(key, M.hmask);
+  for (uint32_t probe = 0; probe <= M.hmask; ++probe) {
+    const uint64_t k = __ldcg(reinterpret_cast<const unsigned long long*>(M.hkeys) + h);
+    if (k == key) {
+      const uint32_t b = __ldcg(M.hvals + h);
+      return b < M.pool_blocks ? b : kNoBlock;
+    }
+    if (k == kEmptyKey) return kNoBlock;
+    h = (h + 1) & M.hmask;
+  }
+  return kNoBlock;
+}
+
+__device__ inline void latch_status(Control* c, uint32_t code) {
+  atomicCAS(&c->status, 0u, code);
+}
+
+// Voxel index of a coordinate, floor(c / v) in IEEE single precision.
+__device__ inline bool voxel_index(float c, float v, int* out) {
+  const float f = floorf(__fdiv_rn(c, v));
+  if (!(f >= -1.0e9f && f <= 1.0e9f)) return false;
+  *out = (int)f;
+  return true;
+}
+
+__device__ inline float voxel_centre(int i, float v) {
+  return __fmul_rn(__fadd_rn((float)i, 0.5f), v);
+}
+
+}  // namespace af
