@@ -130,4 +130,54 @@ __device__ inline float voxel_centre(int i, float v) {
   return __fmul_rn(__fadd_rn((float)i, 0.5f), v);
 }
 
+
+// ---- per-return steps shared by the integration kernels (Sec. 3.2, 3.4) ----
+
+struct Pose {
+  float r[3][4];  // row-major [R | t]
+};
+
+// Transform, validate, voxel-index one return. Returns false if dropped.
+__device__ inline bool prepare_return(const MapView& M, const Pose& P, float sx, float sy,
+                                      float sz, float p[3], float* range, int rel[3]) {
+  if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) return false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    p[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P.r[r][0], sx), __fmul_rn(P.r[r][1], sy)),
+                               __fmul_rn(P.r[r][2], sz)),
+                     P.r[r][3]);
+  const float b0 = __fsub_rn(p[0], P.r[0][3]);
+  const float b1 = __fsub_rn(p[1], P.r[1][3]);
+  const float b2 = __fsub_rn(p[2], P.r[2][3]);
+  const float bb = __fadd_rn(__fadd_rn(__fmul_rn(b0, b0), __fmul_rn(b1, b1)), __fmul_rn(b2, b2));
+  *range = __fsqrt_rn(bb);
+  if (!(*range >= M.range_min && *range <= M.range_max)) return false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int i;
+    if (!voxel_index(p[k], M.v, &i)) return false;
+    rel[k] = i - M.dom_vox[k];
+    if (rel[k] - M.m < 0 || rel[k] + M.m >= M.dim_vox[k]) return false;
+  }
+  return true;
+}
+
+// Sample s (1..ns) of the ray-cleared band toward the sensor. Returns the
+// domain-relative voxel, or false if it falls outside the map box.
+__device__ inline bool band_sample(const MapView& M, const float p[3], const float q[3],
+                                   float range, int s, int rel[3]) {
+  const float step = __fdiv_rn(__fmul_rn(__fsub_rn(M.clear_hi, M.clear_lo), M.tau), (float)M.ns);
+  const float start = __fmul_rn(M.clear_lo, M.tau);
+  const float dist = __fadd_rn(start, __fmul_rn((float)s, step));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = __fdiv_rn(__fsub_rn(q[k], p[k]), range);
+    int i;
+    if (!voxel_index(__fadd_rn(p[k], __fmul_rn(dist, u)), M.v, &i)) return false;
+    rel[k] = i - M.dom_vox[k];
+    if (rel[k] < 0 || rel[k] >= M.dim_vox[k]) return false;
+  }
+  return true;
+}
+
 }  // namespace af
