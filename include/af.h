@@ -216,6 +216,41 @@ typedef struct {
 af_status af_profile_enable(af_ctx *ctx, int enable);
 af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);
 
+/*
+ * Allocation-free scan integration. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- a real-time
+ * loop whose memory is budgeted once at start-up, a host framework that owns
+ * every device buffer through its own arena, code that must not enter the
+ * CUDA allocator while other work runs. af_create allocates the hashed map,
+ * so those callers integrate into a dense voxel box that they own instead.
+ *
+ * The call integrates one scan exactly as af_integrate_scan does (same drop
+ * rules, same arithmetic, same weight cap and occupied / known rule; `cfg`'s
+ * geometry and map box are used, its capacities are ignored) and ADDS it to
+ * the box's current contents, so consecutive calls accumulate scans like a
+ * map. The caller clears the box once before the first scan.
+ *  box_min, box_dim : the output box in absolute voxel indices; voxel
+ *                     (x, y, z) is element ((z - z0) * dy + (y - y0)) * dx +
+ *                     (x - x0). Contributions outside the box are not kept.
+ *  d_vox   : per voxel, (S << 20) | w: S the SDF sum in units of 2^-20 m,
+ *            w the weight (device memory, caller-owned, in/out).
+ *  d_flags : per voxel, bit0 ray-cleared, bit1 occupied, bit2 known
+ *            (device memory, caller-owned, in/out).
+ * The library allocates nothing: its per-return scratch is a fixed device
+ * array of AF_NOALLOC_MAX_RETURNS float4 (1 MiB) that every GPU loading the
+ * library holds until the process exits. n > AF_NOALLOC_MAX_RETURNS returns
+ * AF_ERR_CAPACITY (split the scan). The first call on a device looks up the
+ * array's device address once; make that first call before any stream
+ * capture. All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller. Asynchronous on `stream`; errors are
+ * reported through af_last_error(NULL).
+ */
+#define AF_NOALLOC_MAX_RETURNS 65536
+af_status af_integrate_scan_noalloc(const af_config *cfg, const float *d_xyz, uint32_t n,
+                                    const float pose[16], const int32_t box_min[3],
+                                    const uint32_t box_dim[3], uint64_t *d_vox,
+                                    uint8_t *d_flags, void *stream);
+
 /* Last error message of the context (static storage if ctx is NULL). */
 const char *af_last_error(const af_ctx *ctx);
 

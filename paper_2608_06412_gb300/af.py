@@ -25,7 +25,8 @@ STATUS = {0: "AF_OK", 1: "AF_ERR_INVALID_ARG", 2: "AF_ERR_CAPACITY", 3: "AF_ERR_
 EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set_tool",
            "af_score", "af_frame_host", "af_sync_status", "af_get_stats", "af_block_count",
            "af_export_blocks", "af_kernel_offsets", "af_arm_offsets", "af_profile_enable",
-           "af_profile_read", "af_last_error")
+           "af_profile_read", "af_integrate_scan_noalloc", "af_last_error")
+NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score")
 
@@ -93,6 +94,8 @@ def load(build: bool = True) -> C.CDLL:
             "af_arm_offsets": (C.c_int, [C.c_float, C.c_float, P, P]),
             "af_profile_enable": (C.c_int, [P, C.c_int]),
             "af_profile_read": (C.c_int, [P, C.POINTER(_Profile), C.c_int]),
+            "af_integrate_scan_noalloc": (C.c_int, [C.POINTER(_Config), P, U32, P, P, P, P, P,
+                                                    P]),
             "af_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -322,3 +325,25 @@ def arm_offsets(v: float, tau: float, u) -> np.ndarray:
     out = np.zeros((3, 3), np.int32)
     _check(lib.af_arm_offsets(v, tau, _np_ptr(u), _np_ptr(out)))
     return out
+
+
+def integrate_scan_noalloc(cfg: MapConfig, xyz, pose, box_min, box_dim, vox, flags,
+                           stream=None):
+    """af_integrate_scan_noalloc: add one scan to a caller-owned dense voxel box
+    (vox: int64 CUDA tensor of (S << 20) | w words, flags: uint8 CUDA tensor;
+    both box_dim[0] * box_dim[1] * box_dim[2] long). The library allocates
+    nothing for this call, for callers that cannot allocate device memory."""
+    import torch
+    lib = load()
+    cc = cfg._c()
+    n = int(xyz.shape[0])
+    p = _dev_ptr(xyz, torch.float32, (3,)) if n else C.c_void_p(0)
+    pose = np.ascontiguousarray(pose, np.float32).reshape(16)
+    bmin = np.ascontiguousarray(box_min, np.int32).reshape(3)
+    bdim = np.ascontiguousarray(box_dim, np.uint32).reshape(3)
+    count = int(np.prod(bdim.astype(np.int64)))
+    if vox.numel() != count or flags.numel() != count:
+        raise ValueError("vox and flags must hold box_dim[0] * box_dim[1] * box_dim[2] voxels")
+    _check(lib.af_integrate_scan_noalloc(C.byref(cc), p, n, _np_ptr(pose), _np_ptr(bmin),
+                                         _np_ptr(bdim), _dev_ptr(vox, torch.int64),
+                                         _dev_ptr(flags, torch.uint8), _stream_ptr(stream)))

@@ -111,6 +111,10 @@ extern "C" const char* af_version(void) { return "libaf 0.1 (sm_103a)"; }
 
 extern "C" const char* af_last_error(const af_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
+namespace af {
+void set_global_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace af
+
 // ---------------------------------------------------------------------------
 // Kernel rasterisation (Sec. 3.4). An offset o belongs to the kernel of unit
 // direction u when, with e = o v, a = e . u and rho^2 = |e - a u|^2 (double
