@@ -228,12 +228,39 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def integrate_bytes(stats_delta_vox, n_ret, dirty):
-    """Algorithmic bytes of one scan's integration: 12 B per return in,
-    read + write of the 8-byte voxel word of every voxel the scan updates,
-    and per touched brick the 4 KB word read of the bit view plus its
-    128 B of bit-plane writes."""
-    return 12 * n_ret + 16 * stats_delta_vox + (4096 + 128) * dirty
+def score_bytes_per_test(W) -> float:
+    """Algorithmic bytes of one point x orientation test: the occupied and
+    known bits (2 bits per voxel) of every voxel the test's tool kernel,
+    corridor kernel and three arm samples cover, with no early exit; the
+    mean over the direction table."""
+    from paper_2608_06412_gb300 import af
+    t = W.af_tool()
+    v = W.params["v"]
+    vox = [len(af.kernel_offsets(t, v, u, af.KERNEL_TOOL)) +
+           len(af.kernel_offsets(t, v, u, af.KERNEL_CORRIDOR)) + 3 for u in W.dirs]
+    return 2.0 * float(np.mean(vox)) / 8.0
+
+# per scored point: 24 B of point + normal in, 3 B of label + best out
+SCORE_BYTES_PER_POINT = 27.0
+
+# DRAM bytes (read + write) per launch from one ncu capture of the benchmark
+# (profiles/), valid only while the kernel's sources hash as recorded.
+TRAFFIC = {
+    "k_score": (4826368 + 0, {"paper_2608_06412_gb300/csrc/af_score.cu": "c18ce5ebbff973a3",
+                              "paper_2608_06412_gb300/csrc/af_internal.cuh": "d16abb1faa3844a0"}),
+}
+
+
+def _traffic(kernel: str):
+    import hashlib
+    if kernel not in TRAFFIC:
+        return None
+    nbytes, files = TRAFFIC[kernel]
+    for path, digest in files.items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != digest:
+                return None
+    return nbytes
 
 
 # ---------------------------------------------------------------------------
@@ -374,11 +401,21 @@ def run_ours(args, W, ws, rank, local):
     n_launch = prof[dom][0]
     avg_ms = kt[dom] / max(n_launch, 1)
     roof = {"kernel": dom, "bound": "hbm", "unit": "GB/s", "peak": peak,
-            "peak_kind": peak_kind, "traffic": None,
+            "peak_kind": peak_kind, "traffic": _traffic(dom),
             "kernel_ms": {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.items()},
             "kernel_share": {k: round(v / max(sum(kt.values()), 1e-9), 4) for k, v in kt.items()}}
-    roof["achieved"] = None
-    roof["frac"] = None
+    if dom == "k_score":
+        bpt = score_bytes_per_test(W)
+        tests_l = (sB1["tests"] - sB0["tests"]) / max(n_launch, 1)
+        pts_l = (sB1["points_scored"] - sB0["points_scored"]) / max(n_launch, 1)
+        alg = bpt * tests_l + SCORE_BYTES_PER_POINT * pts_l
+        roof["algorithmic_bytes_per_launch"] = alg
+        roof["bytes_per_test"] = bpt
+        roof["achieved"] = alg / (avg_ms * 1e-3) / 1e9
+        roof["frac"] = roof["achieved"] / peak
+    else:
+        roof["achieved"] = None
+        roof["frac"] = None
     return {
         "metric": METRIC, "value": tests_all / (total_ms_max / 1e3), "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
