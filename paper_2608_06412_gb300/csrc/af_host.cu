@@ -47,6 +47,7 @@ struct af_ctx {
   af::ToolView T{};
   float* d_dirs = nullptr;
   short4* d_runs = nullptr;
+  int2* d_fruns = nullptr;
   int4* d_dtab = nullptr;
   short4* d_arm = nullptr;
   // host counters
@@ -250,10 +251,12 @@ extern "C" af_status af_arm_offsets(float voxel_size, float truncation, const fl
 static void free_tool(af_ctx* c) {
   cudaFree(c->d_dirs);
   cudaFree(c->d_runs);
+  cudaFree(c->d_fruns);
   cudaFree(c->d_dtab);
   cudaFree(c->d_arm);
   c->d_dirs = nullptr;
   c->d_runs = nullptr;
+  c->d_fruns = nullptr;
   c->d_dtab = nullptr;
   c->d_arm = nullptr;
   c->has_tool = false;
@@ -461,10 +464,36 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
       arm[3 * g + k] = make_short4((short)a[3 * k], (short)a[3 * k + 1], (short)a[3 * k + 2], 0);
   }
   if (runs.empty()) runs.push_back(make_short4(0, 1, 0, 0));  // keep the buffer non-empty
+  // Fast-path form of the runs: the plane-word offset of the run's row relative to
+  // the point's row, valid while every plane index fits in 31 bits. `reach` bounds
+  // every offset, so a point at least `reach` voxels inside the box needs no checks.
+  const MapView& M = ctx->M;
+  const int64_t plane_words = (int64_t)M.row_words * M.dim_vox[1] * M.dim_vox[2];
+  const bool fast_ok = plane_words < (1ll << 31);
+  std::vector<int2> fruns(runs.size());
+  int reach[3] = {0, 0, 0};
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const short4 s = runs[r];
+    const int64_t delta = ((int64_t)s.w * M.dim_vox[1] + s.z) * M.row_words;
+    fruns[r] = make_int2((int)delta, (int)(uint16_t)s.x | ((int)s.y << 16));
+    reach[0] = std::max({reach[0], std::abs((int)s.x), std::abs((int)s.x + (int)s.y - 1)});
+    reach[1] = std::max(reach[1], std::abs((int)s.z));
+    reach[2] = std::max(reach[2], std::abs((int)s.w));
+  }
+  for (const short4& a : arm) {
+    reach[0] = std::max(reach[0], std::abs((int)a.x));
+    reach[1] = std::max(reach[1], std::abs((int)a.y));
+    reach[2] = std::max(reach[2], std::abs((int)a.z));
+  }
+  if (!fast_ok) reach[0] = reach[1] = reach[2] = 1 << 30;  // never take the fast path
   AF_CUDA(ctx, cudaDeviceSynchronize());
   free_tool(ctx);
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_dirs, (size_t)G * 12));
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_runs, runs.size() * sizeof(short4)));
+  AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_fruns, fruns.size() * sizeof(int2)));
+  AF_CUDA(ctx, cudaMemcpy(ctx->d_fruns, fruns.data(), fruns.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  for (int k = 0; k < 3; ++k) ctx->T.reach[k] = reach[k];
+  ctx->T.fruns = ctx->d_fruns;
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_dtab, (size_t)G * sizeof(int4)));
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_arm, (size_t)G * 3 * sizeof(short4)));
   AF_CUDA(ctx, cudaMemcpy(ctx->d_dirs, h_dirs, (size_t)G * 12, cudaMemcpyHostToDevice));

@@ -102,18 +102,27 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
 }
 
 __device__ inline void mark_dirty(const MapView& M, uint32_t blk, uint32_t frame) {
-  if (atomicExch(M.stamp + blk, frame) != frame) {
+  // read first: most returns touch bricks already marked by another return
+  if (__ldcg(M.stamp + blk) != frame && atomicExch(M.stamp + blk, frame) != frame) {
     const uint32_t d = atomicAdd(&M.ctl->dirty_count, 1u);
     M.dirty[d] = blk;
   }
 }
+
+// Approximate square root (MUFU reciprocal square root), relative error well
+// below 2^-20 for the normal arguments it is used on. Only ever used to take
+// a decision that the exact result is certain to agree with (margins of
+// 2^-16 relative); near any threshold the exact IEEE operation decides.
+__device__ inline float sqrt_approx(float x) { return x * rsqrtf(x); }
+
+constexpr float kMargin = 1.52587890625e-05f;  // 2^-16
 
 // W = 2m + 1 voxels per cube edge; BA = bricks a cube edge can span.
 template <int W>
 __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __restrict__ ret,
                                                     uint32_t n, float q0, float q1, float q2,
                                                     uint32_t frame) {
-  constexpr int T = 32;
+  constexpr int T = 16;
   constexpr int C = W * W * W;
   constexpr int BA = (W + 6) / 8 + 1;
   constexpr int NB = BA * BA * BA;
@@ -121,6 +130,7 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
   __shared__ float4 s_p[T];        // p, valid flag
   __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
   __shared__ int4 s_b0[T];         // first brick of the cube, w = nb packed
+  __shared__ float s_bb[T];        // |p - q|^2 as rounded in single precision
   __shared__ uint32_t s_blk[T][NB];
 
   if (__ldcg(&M.ctl->status) != 0u) return;  // sticky capacity error: skip the scan
@@ -132,10 +142,10 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
     const uint32_t k = r0 + tid;
     float4 p = k < n ? ret[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     int4 rel = make_int4(0, 0, 0, 0), b0 = make_int4(0, 0, 0, 0);
+    float bb = 0.f;
     if (p.w != 0.f) {
       const float b[3] = {__fsub_rn(p.x, q0), __fsub_rn(p.y, q1), __fsub_rn(p.z, q2)};
-      const float bb =
-          __fadd_rn(__fadd_rn(__fmul_rn(b[0], b[0]), __fmul_rn(b[1], b[1])), __fmul_rn(b[2], b[2]));
+      bb = __fadd_rn(__fadd_rn(__fmul_rn(b[0], b[0]), __fmul_rn(b[1], b[1])), __fmul_rn(b[2], b[2]));
       const float range = __fsqrt_rn(bb);
       int i[3];
       voxel_index(p.x, M.v, &i[0]);
@@ -151,6 +161,7 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
     s_p[tid] = p;
     s_rel[tid] = rel;
     s_b0[tid] = b0;
+    s_bb[tid] = bb;
   }
   __syncthreads();
 
@@ -196,22 +207,40 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
     const float x0 = voxel_centre(jx + M.dom_vox[0], v);
     const float x1 = voxel_centre(jy + M.dom_vox[1], v);
     const float x2 = voxel_centre(jz + M.dom_vox[2], v);
-    // behind-surface cone: theta between x - p and p - q
+    // behind-surface cone: theta between x - p and p - q; excluded iff
+    // RN(dot / RN(RN(sqrt(aa)) * range)) > cone
     const float a0 = __fsub_rn(x0, p.x), a1 = __fsub_rn(x1, p.y), a2 = __fsub_rn(x2, p.z);
     const float aa = __fadd_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(a1, a1)), __fmul_rn(a2, a2));
     if (aa > 0.f) {
       const float b0 = __fsub_rn(p.x, q0), b1 = __fsub_rn(p.y, q1), b2 = __fsub_rn(p.z, q2);
       const float dot =
           __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));
-      const float cos_theta = __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range));
-      if (cos_theta > cone) continue;
+      // dot <= 0 makes the rounded cosine <= 0, so with cone >= 0 it is kept
+      if (dot > 0.f || cone < 0.f) {
+        bool decided = false;
+        if (aa > 1e-20f) {
+          const float ca = __fdividef(dot, sqrt_approx(aa) * range);
+          if (ca > cone + kMargin) continue;        // certainly excluded
+          decided = ca < cone - kMargin;            // certainly kept
+        }
+        if (!decided &&
+            __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range)) > cone)
+          continue;
+      }
     }
     // d = |p - q| - |x - q|, clamped to [0, tau]
     const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
     const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
-    float d = __fsub_rn(range, __fsqrt_rn(cc));
-    d = d < 0.f ? 0.f : d;
-    d = d > tau ? tau : d;
+    float d;
+    if (cc >= s_bb[t]) {
+      d = 0.f;  // |x - q| >= |p - q|: the rounded difference is <= 0
+    } else if (cc > 1e-20f && range - sqrt_approx(cc) > tau + range * kMargin) {
+      d = tau;  // the exact difference exceeds tau
+    } else {
+      d = __fsub_rn(range, __fsqrt_rn(cc));
+      d = d < 0.f ? 0.f : d;
+      d = d > tau ? tau : d;
+    }
     const unsigned long long dq = (unsigned long long)__float2uint_rn(__fmul_rn(d, kScale));
     const int4 b0 = s_b0[t];
     const int bl = ((jx >> 3) - b0.x) + BA * (((jy >> 3) - b0.y) + BA * ((jz >> 3) - b0.z));
@@ -221,6 +250,7 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
     atomicAdd(M.vox + (size_t)blk * kBrickVox + l, (dq << kWBits) | 1ull);
   }
 }
+
 
 // Weight cap and bit view of every brick touched by the scan.
 __global__ void __launch_bounds__(512) k_bitview(MapView M) {
@@ -296,7 +326,7 @@ cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const
 cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], const float4* d_ret,
                         uint32_t frame, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
-  const unsigned grid = (n + 31) / 32;
+  const unsigned grid = (n + 15) / 16;  // k_integrate tiles of 16 returns
   switch (2 * M.m + 1) {
 #define AF_CASE(W) \
   case W: k_integrate<W><<<grid, 256, 0, stream>>>(M, d_ret, n, pose[3], pose[7], pose[11], frame); break;

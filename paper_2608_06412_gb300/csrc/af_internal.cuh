@@ -76,12 +76,14 @@ struct MapView {
 struct ToolView {
   const float* dirs;      // G x 3 unit directions
   const short4* runs;     // x-runs (dx0, len, dy, dz), len in 1..64
+  const int2* fruns;      // the same runs as (row delta in plane words, dx0 | len << 16)
   const int4* dtab;       // per direction: tool runs [x, y), corridor runs [z, w)
   const short4* arm;      // G x 3 arm-sample offsets
   int G;
   int n_c;
   float cos_max;
   int strict;
+  int reach[3];           // largest |offset| per axis over every kernel and arm sample
 };
 
 __host__ __device__ inline uint64_t pack_brick(uint32_t bx, uint32_t by, uint32_t bz) {

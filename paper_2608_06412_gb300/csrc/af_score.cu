@@ -17,10 +17,18 @@
 //
 // Kernels are x-runs rather than voxel lists: a cylinder meets every x-row
 // in one interval (two at most next to the self-exclusion ball), so a run
-// of up to 64 voxels costs one or two loads of the bit plane.
+// of up to 64 voxels costs one or two loads of the bit plane. A point whose
+// whole kernel reach lies inside the map box takes the FAST path: the run
+// table then holds each run's row as a plane-word offset from the point's
+// row, and no bound is checked.
 #include "af_internal.cuh"
 
 namespace af {
+
+struct Pt {
+  int px, py, pz;  // box-relative voxel of the point
+  int row;         // plane-word index of the point's row (FAST path only)
+};
 
 // Bits x0 .. x0+len-1 of plane row (y, z), bit i = voxel x0 + i; voxels
 // outside the map box read 0 and set *outside.
@@ -47,28 +55,53 @@ __device__ inline unsigned long long row_bits(const unsigned long long* __restri
   return win << (xa - x0);
 }
 
-__device__ inline bool bit_at(const unsigned long long* __restrict__ plane, const MapView& M,
-                              int x, int y, int z) {
-  if ((unsigned)x >= (unsigned)M.dim_vox[0] || (unsigned)y >= (unsigned)M.dim_vox[1] ||
-      (unsigned)z >= (unsigned)M.dim_vox[2])
-    return false;
-  const unsigned long long wd =
-      __ldg(plane + ((size_t)z * M.dim_vox[1] + y) * M.row_words + (x >> 6));
-  return (wd >> (x & 63)) & 1ull;
+// Bits of run r of the tables for point P; *len receives the run length.
+template <bool FAST>
+__device__ inline unsigned long long run_bits(const unsigned long long* __restrict__ plane,
+                                              const MapView& M, const ToolView& T, int r,
+                                              const Pt& P, int* len, bool* outside) {
+  if (FAST) {
+    const int2 fr = __ldg(T.fruns + r);
+    const int n = fr.y >> 16;
+    const int xa = P.px + (int)(short)(fr.y & 0xffff);
+    const int row = P.row + fr.x;
+    const int wa = xa >> 6, wb = (xa + n - 1) >> 6, sh = xa & 63;
+    unsigned long long win = __ldg(plane + row + wa) >> sh;
+    if (wb != wa) win |= __ldg(plane + row + wb) << (64 - sh);
+    if (n < 64) win &= (1ull << n) - 1ull;
+    *len = n;
+    return win;
+  }
+  const short4 run = __ldg(T.runs + r);
+  *len = run.y;
+  return row_bits(plane, M, P.px + run.x, P.py + run.z, P.pz + run.w, run.y, outside);
 }
 
-// Occupied tool voxels of direction g at voxel (px,py,pz), saturated at `sat`.
-__device__ inline int tool_count(const MapView& M, const ToolView& T, int g, int px, int py,
-                                 int pz, int sat, int lane) {
+template <bool FAST>
+__device__ inline bool bit_at(const unsigned long long* __restrict__ plane, const MapView& M,
+                              const Pt& P, short4 a) {
+  const int x = P.px + a.x, y = P.py + a.y, z = P.pz + a.z;
+  if (!FAST && ((unsigned)x >= (unsigned)M.dim_vox[0] || (unsigned)y >= (unsigned)M.dim_vox[1] ||
+                (unsigned)z >= (unsigned)M.dim_vox[2]))
+    return false;
+  const size_t w = FAST ? (size_t)(P.row + (a.z * M.dim_vox[1] + a.y) * M.row_words + (x >> 6))
+                        : ((size_t)z * M.dim_vox[1] + y) * M.row_words + (x >> 6);
+  return (__ldg(plane + w) >> (x & 63)) & 1ull;
+}
+
+// Occupied tool voxels of direction g at point P, saturated at `sat`.
+template <bool FAST>
+__device__ inline int tool_count(const MapView& M, const ToolView& T, int g, const Pt& P, int sat,
+                                 int lane) {
   const int4 dt = __ldg(T.dtab + g);
   int total = 0;
   for (int r0 = dt.x; r0 < dt.y; r0 += 32) {
     const int r = r0 + lane;
     int c = 0;
     if (r < dt.y) {
-      const short4 run = __ldg(T.runs + r);
+      int len;
       bool out = false;
-      c = __popcll(row_bits(M.occ, M, px + run.x, py + run.z, pz + run.w, run.y, &out));
+      c = __popcll(run_bits<FAST>(M.occ, M, T, r, P, &len, &out));
     }
     total += __reduce_add_sync(0xffffffffu, c);
     if (total >= sat) return sat;
@@ -77,13 +110,13 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, int
 }
 
 // Arm samples (occupied or unknown) or corridor (occupied; strict: or unknown).
-__device__ inline bool path_blocked(const MapView& M, const ToolView& T, int g, int px, int py,
-                                    int pz, int lane) {
+template <bool FAST>
+__device__ inline bool path_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
+                                    int lane) {
   bool hit = false;
   if (lane < 3) {
     const short4 a = __ldg(T.arm + 3 * g + lane);
-    const int x = px + a.x, y = py + a.y, z = pz + a.z;
-    hit = bit_at(M.occ, M, x, y, z) || !bit_at(M.known, M, x, y, z);
+    hit = bit_at<FAST>(M.occ, M, P, a) || !bit_at<FAST>(M.known, M, P, a);
   }
   if (__any_sync(0xffffffffu, hit)) return true;
   const int4 dt = __ldg(T.dtab + g);
@@ -91,15 +124,12 @@ __device__ inline bool path_blocked(const MapView& M, const ToolView& T, int g, 
     const int r = r0 + lane;
     bool h = false;
     if (r < dt.w) {
-      const short4 run = __ldg(T.runs + r);
+      int len;
       bool out = false;
-      const unsigned long long o =
-          row_bits(M.occ, M, px + run.x, py + run.z, pz + run.w, run.y, &out);
-      h = o != 0ull;
+      h = run_bits<FAST>(M.occ, M, T, r, P, &len, &out) != 0ull;
       if (T.strict && !h) {
-        const unsigned long long k =
-            row_bits(M.known, M, px + run.x, py + run.z, pz + run.w, run.y, &out);
-        const unsigned long long full = run.y == 64 ? ~0ull : ((1ull << run.y) - 1ull);
+        const unsigned long long k = run_bits<FAST>(M.known, M, T, r, P, &len, &out);
+        const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
         h = out || (k != full);
       }
     }
@@ -108,12 +138,55 @@ __device__ inline bool path_blocked(const MapView& M, const ToolView& T, int g, 
   return false;
 }
 
+__device__ inline bool candidate(const ToolView& T, int g, float n0, float n1, float n2) {
+  if (g >= T.G) return false;
+  const float u0 = __ldg(T.dirs + 3 * g), u1 = __ldg(T.dirs + 3 * g + 1),
+              u2 = __ldg(T.dirs + 3 * g + 2);
+  const float nu = __fadd_rn(__fadd_rn(__fmul_rn(n0, u0), __fmul_rn(n1, u1)), __fmul_rn(n2, u2));
+  return nu > T.cos_max;
+}
+
+// The candidate loop of one point: lowest-index minimum of the direction
+// scores, with exact early exits. Returns (best score, best index).
+template <bool FAST>
+__device__ inline int2 best_direction(const MapView& M, const ToolView& T, const Pt& P, float n0,
+                                      float n1, float n2, int lane) {
+  const int nc = T.n_c;
+  int bscore = nc + 2, best = -1;
+  for (int gb = 0; gb < T.G && bscore != 0; gb += 32) {
+    unsigned mask = __ballot_sync(0xffffffffu, candidate(T, gb + lane, n0, n1, n2));
+    while (mask) {
+      const int g = gb + __ffs(mask) - 1;
+      mask &= mask - 1u;
+      if (bscore <= nc) {
+        // improves only if not blocked and strictly fewer collisions
+        const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
+        if (cnt >= bscore) continue;
+        if (path_blocked<FAST>(M, T, g, P, lane)) continue;
+        bscore = cnt;
+        best = g;
+      } else {
+        // nothing unblocked yet: any unblocked direction improves
+        if (path_blocked<FAST>(M, T, g, P, lane)) {
+          if (best < 0) {
+            bscore = nc + 1;
+            best = g;
+          }
+          continue;
+        }
+        bscore = tool_count<FAST>(M, T, g, P, nc, lane);
+        best = g;
+      }
+      if (bscore == 0) break;
+    }
+  }
+  return make_int2(bscore, best);
+}
+
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_score(MapView M, ToolView T,
-                                                       const float* __restrict__ pts,
-                                                       const float* __restrict__ nrm, uint32_t m,
-                                                       uint8_t* __restrict__ label,
-                                                       int16_t* __restrict__ best_out) {
+__global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
+    k_score(MapView M, ToolView T, const float* __restrict__ pts, const float* __restrict__ nrm,
+            uint32_t m, uint8_t* __restrict__ label, int16_t* __restrict__ best_out) {
   const int lane = threadIdx.x & 31;
   const uint32_t pi = blockIdx.x * WARPS + (threadIdx.x >> 5);
   if (pi >= m) return;  // whole warp
@@ -123,16 +196,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_score(MapView M, ToolView T,
 
   // the point's voxel and its weight (confidence gate, Sec. 3.5)
   int i0, i1, i2;
-  bool ok = voxel_index(s0, M.v, &i0) && voxel_index(s1, M.v, &i1) && voxel_index(s2, M.v, &i2);
-  const int px = i0 - M.dom_vox[0], py = i1 - M.dom_vox[1], pz = i2 - M.dom_vox[2];
+  const bool ok =
+      voxel_index(s0, M.v, &i0) && voxel_index(s1, M.v, &i1) && voxel_index(s2, M.v, &i2);
+  Pt P;
+  P.px = i0 - M.dom_vox[0];
+  P.py = i1 - M.dom_vox[1];
+  P.pz = i2 - M.dom_vox[2];
   uint32_t w = 0;
-  if (ok && (unsigned)px < (unsigned)M.dim_vox[0] && (unsigned)py < (unsigned)M.dim_vox[1] &&
-      (unsigned)pz < (unsigned)M.dim_vox[2]) {
+  if (ok && (unsigned)P.px < (unsigned)M.dim_vox[0] && (unsigned)P.py < (unsigned)M.dim_vox[1] &&
+      (unsigned)P.pz < (unsigned)M.dim_vox[2]) {
     uint32_t blk = kNoBlock;
-    if (lane == 0) blk = lookup_brick(M, pack_brick(px >> 3, py >> 3, pz >> 3));
+    if (lane == 0) blk = lookup_brick(M, pack_brick(P.px >> 3, P.py >> 3, P.pz >> 3));
     blk = __shfl_sync(0xffffffffu, blk, 0);
     if (blk != kNoBlock) {
-      const int l = (px & 7) | ((py & 7) << 3) | ((pz & 7) << 6);
+      const int l = (P.px & 7) | ((P.py & 7) << 3) | ((P.pz & 7) << 6);
       w = (uint32_t)(__ldcg(M.vox + (size_t)blk * kBrickVox + l) & kWMask);
     }
   }
@@ -146,59 +223,24 @@ __global__ void __launch_bounds__(WARPS * 32) k_score(MapView M, ToolView T,
 
   // nominal tests: every candidate direction of this point
   int ncand = 0;
-  for (int gb = 0; gb < T.G; gb += 32) {
-    const int g = gb + lane;
-    bool cand = false;
-    if (g < T.G) {
-      const float u0 = __ldg(T.dirs + 3 * g), u1 = __ldg(T.dirs + 3 * g + 1),
-                  u2 = __ldg(T.dirs + 3 * g + 2);
-      const float nu = __fadd_rn(__fadd_rn(__fmul_rn(n0, u0), __fmul_rn(n1, u1)), __fmul_rn(n2, u2));
-      cand = nu > T.cos_max;
-    }
-    ncand += __popc(__ballot_sync(0xffffffffu, cand));
-  }
+  for (int gb = 0; gb < T.G; gb += 32)
+    ncand += __popc(__ballot_sync(0xffffffffu, candidate(T, gb + lane, n0, n1, n2)));
 
-  const int nc = T.n_c;
-  int bscore = nc + 2, best = -1;
-  for (int gb = 0; gb < T.G && bscore != 0; gb += 32) {
-    const int g = gb + lane;
-    bool cand = false;
-    if (g < T.G) {
-      const float u0 = __ldg(T.dirs + 3 * g), u1 = __ldg(T.dirs + 3 * g + 1),
-                  u2 = __ldg(T.dirs + 3 * g + 2);
-      const float nu = __fadd_rn(__fadd_rn(__fmul_rn(n0, u0), __fmul_rn(n1, u1)), __fmul_rn(n2, u2));
-      cand = nu > T.cos_max;
-    }
-    unsigned mask = __ballot_sync(0xffffffffu, cand);
-    while (mask) {
-      const int gg = gb + __ffs(mask) - 1;
-      mask &= mask - 1u;
-      if (bscore <= nc) {
-        // improves only if not blocked and strictly fewer collisions
-        const int cnt = tool_count(M, T, gg, px, py, pz, bscore, lane);
-        if (cnt >= bscore) continue;
-        if (path_blocked(M, T, gg, px, py, pz, lane)) continue;
-        bscore = cnt;
-        best = gg;
-      } else {
-        // nothing unblocked yet: any unblocked direction improves
-        if (path_blocked(M, T, gg, px, py, pz, lane)) {
-          if (best < 0) {
-            bscore = nc + 1;
-            best = gg;
-          }
-          continue;
-        }
-        bscore = tool_count(M, T, gg, px, py, pz, nc, lane);
-        best = gg;
-      }
-      if (bscore == 0) break;
-    }
+  const bool fast = P.px >= T.reach[0] && P.px + T.reach[0] < M.dim_vox[0] &&
+                    P.py >= T.reach[1] && P.py + T.reach[1] < M.dim_vox[1] &&
+                    P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
+  int2 res;
+  if (fast) {
+    P.row = (P.pz * M.dim_vox[1] + P.py) * M.row_words;
+    res = best_direction<true>(M, T, P, n0, n1, n2, lane);
+  } else {
+    P.row = 0;
+    res = best_direction<false>(M, T, P, n0, n1, n2, lane);
   }
 
   if (lane == 0) {
-    label[pi] = (best >= 0 && bscore < nc) ? 1 : 2;
-    best_out[pi] = (int16_t)best;
+    label[pi] = (res.y >= 0 && res.x < T.n_c) ? 1 : 2;
+    best_out[pi] = (int16_t)res.y;
     atomicAdd(&M.ctl->points_scored, 1ull);
     atomicAdd(&M.ctl->tests, (unsigned long long)ncand);
   }
