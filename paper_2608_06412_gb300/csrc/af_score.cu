@@ -25,6 +25,10 @@
 
 namespace af {
 
+// Runs each lane evaluates per warp step: more loads in flight per step,
+// at the price of a little wasted work when a step decides early.
+constexpr int kRunsPerLane = 1;
+
 struct Pt {
   int px, py, pz;  // box-relative voxel of the point
   int row;         // plane-word index of the point's row (FAST path only)
@@ -95,13 +99,16 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, con
                                  int lane) {
   const int4 dt = __ldg(T.dtab + g);
   int total = 0;
-  for (int r0 = dt.x; r0 < dt.y; r0 += 32) {
-    const int r = r0 + lane;
+  for (int r0 = dt.x; r0 < dt.y; r0 += 32 * kRunsPerLane) {
     int c = 0;
-    if (r < dt.y) {
-      int len;
-      bool out = false;
-      c = __popcll(run_bits<FAST>(M.occ, M, T, r, P, &len, &out));
+#pragma unroll
+    for (int k = 0; k < kRunsPerLane; ++k) {
+      const int r = r0 + 32 * k + lane;
+      if (r < dt.y) {
+        int len;
+        bool out = false;
+        c += __popcll(run_bits<FAST>(M.occ, M, T, r, P, &len, &out));
+      }
     }
     total += __reduce_add_sync(0xffffffffu, c);
     if (total >= sat) return sat;
@@ -109,28 +116,38 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, con
   return total;
 }
 
-// Arm samples (occupied or unknown) or corridor (occupied; strict: or unknown).
+// The three arm samples of direction g (one lane): clear iff none is
+// occupied or unknown.
 template <bool FAST>
-__device__ inline bool path_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
-                                    int lane) {
-  bool hit = false;
-  if (lane < 3) {
-    const short4 a = __ldg(T.arm + 3 * g + lane);
-    hit = bit_at<FAST>(M.occ, M, P, a) || !bit_at<FAST>(M.known, M, P, a);
+__device__ inline bool arm_clear(const MapView& M, const ToolView& T, int g, const Pt& P) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const short4 a = __ldg(T.arm + 3 * g + s);
+    if (bit_at<FAST>(M.occ, M, P, a) || !bit_at<FAST>(M.known, M, P, a)) return false;
   }
-  if (__any_sync(0xffffffffu, hit)) return true;
+  return true;
+}
+
+// Corridor of direction g: any occupied voxel (strict: or unknown) blocks.
+template <bool FAST>
+__device__ inline bool corridor_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
+                                        int lane) {
   const int4 dt = __ldg(T.dtab + g);
-  for (int r0 = dt.z; r0 < dt.w; r0 += 32) {
-    const int r = r0 + lane;
+  for (int r0 = dt.z; r0 < dt.w; r0 += 32 * kRunsPerLane) {
     bool h = false;
-    if (r < dt.w) {
-      int len;
-      bool out = false;
-      h = run_bits<FAST>(M.occ, M, T, r, P, &len, &out) != 0ull;
-      if (T.strict && !h) {
-        const unsigned long long k = run_bits<FAST>(M.known, M, T, r, P, &len, &out);
-        const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
-        h = out || (k != full);
+#pragma unroll
+    for (int k = 0; k < kRunsPerLane; ++k) {
+      const int r = r0 + 32 * k + lane;
+      if (r < dt.w) {
+        int len;
+        bool out = false;
+        bool hk = run_bits<FAST>(M.occ, M, T, r, P, &len, &out) != 0ull;
+        if (T.strict && !hk) {
+          const unsigned long long kb = run_bits<FAST>(M.known, M, T, r, P, &len, &out);
+          const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
+          hk = out || (kb != full);
+        }
+        h = h || hk;
       }
     }
     if (__any_sync(0xffffffffu, h)) return true;
@@ -154,20 +171,32 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
   const int nc = T.n_c;
   int bscore = nc + 2, best = -1;
   for (int gb = 0; gb < T.G && bscore != 0; gb += 32) {
-    unsigned mask = __ballot_sync(0xffffffffu, candidate(T, gb + lane, n0, n1, n2));
+    // lane-parallel screen: candidates, and the arm samples of each candidate
+    const bool cand = candidate(T, gb + lane, n0, n1, n2);
+    unsigned mask = __ballot_sync(0xffffffffu, cand);
+    const unsigned arm_ok = __ballot_sync(0xffffffffu, cand && arm_clear<FAST>(M, T, gb + lane, P));
     while (mask) {
-      const int g = gb + __ffs(mask) - 1;
+      const int bit = __ffs(mask) - 1;
+      const int g = gb + bit;
       mask &= mask - 1u;
+      if (!((arm_ok >> bit) & 1u)) {
+        // blocked (n_c + 1): improves only the first candidate's empty best
+        if (best < 0) {
+          bscore = nc + 1;
+          best = g;
+        }
+        continue;
+      }
       if (bscore <= nc) {
         // improves only if not blocked and strictly fewer collisions
         const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
         if (cnt >= bscore) continue;
-        if (path_blocked<FAST>(M, T, g, P, lane)) continue;
+        if (corridor_blocked<FAST>(M, T, g, P, lane)) continue;
         bscore = cnt;
         best = g;
       } else {
         // nothing unblocked yet: any unblocked direction improves
-        if (path_blocked<FAST>(M, T, g, P, lane)) {
+        if (corridor_blocked<FAST>(M, T, g, P, lane)) {
           if (best < 0) {
             bscore = nc + 1;
             best = g;
