@@ -49,55 +49,61 @@ __device__ void insert_brick(const MapView& M, uint64_t key) {
   latch_status(M.ctl, kStatusCapacity);
 }
 
+// One thread per (return, brick key): key slots [0, nbmax) are the bricks of
+// the return's cube, slots [nbmax, nbmax + N_s) its cleared-band samples. The
+// pose transform is recomputed by every thread of a return (cheap next to an
+// L2 probe); slot 0 also writes the return's world position for k_integrate.
 __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restrict__ xyz,
-                                                uint32_t n, Pose P, float4* __restrict__ ret) {
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+                                                uint32_t n, Pose P, float4* __restrict__ ret,
+                                                int nbmax) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = nbmax + M.ns;
+  const uint32_t k = e / per;
+  const int j = (int)(e % per);
   const int lane = threadIdx.x & 31;
-  if (k == 0) M.ctl->dirty_count = 0;
+  if (e == 0) M.ctl->dirty_count = 0;
 
   float p[3] = {0.f, 0.f, 0.f}, range = 0.f;
   int rel[3] = {0, 0, 0};
   bool valid = false;
   if (k < n) {
     valid = prepare_return(M, P, xyz[3 * k], xyz[3 * k + 1], xyz[3 * k + 2], p, &range, rel);
-    ret[k] = make_float4(p[0], p[1], p[2], valid ? 1.f : 0.f);
+    if (j == 0) ret[k] = make_float4(p[0], p[1], p[2], valid ? 1.f : 0.f);
   }
-  const unsigned acc = __ballot_sync(0xffffffffu, valid);
+  const unsigned acc = __ballot_sync(0xffffffffu, valid && j == 0);
   if (lane == 0 && acc) atomicAdd(&M.ctl->returns_accepted, (unsigned long long)__popc(acc));
 
-  int b0[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  uint64_t key = kEmptyKey;
   if (valid) {
+    int b0[3], nb[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       b0[a] = (rel[a] - M.m) >> 3;
       nb[a] = ((rel[a] + M.m) >> 3) - b0[a] + 1;
     }
-  }
-  const int ncube = valid ? nb[0] * nb[1] * nb[2] : 0;
-  const int total = valid ? ncube + M.ns : 0;
-  const float q[3] = {P.r[0][3], P.r[1][3], P.r[2][3]};
-  uint64_t last = kEmptyKey;
-  for (int kk = 0;; ++kk) {
-    const bool have = kk < total;
-    if (__ballot_sync(0xffffffffu, have) == 0u) break;
-    uint64_t key = kEmptyKey;
-    if (have) {
-      if (kk < ncube) {
-        const int bx = kk % nb[0], by = (kk / nb[0]) % nb[1], bz = kk / (nb[0] * nb[1]);
+    if (j < nbmax) {
+      if (j < nb[0] * nb[1] * nb[2]) {
+        const int bx = j % nb[0], by = (j / nb[0]) % nb[1], bz = j / (nb[0] * nb[1]);
         key = pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz);
-      } else {
-        int sv[3];
-        if (band_sample(M, p, q, range, kk - ncube + 1, sv))
-          key = pack_brick(sv[0] >> 3, sv[1] >> 3, sv[2] >> 3);
+      }
+    } else {
+      const float q[3] = {P.r[0][3], P.r[1][3], P.r[2][3]};
+      int sv[3];
+      if (band_sample(M, p, q, range, j - nbmax + 1, sv)) {
+        const int sb[3] = {sv[0] >> 3, sv[1] >> 3, sv[2] >> 3};
+        // bricks of the cube are inserted by the cube slots
+        const bool in_cube = sb[0] - b0[0] < nb[0] && sb[1] - b0[1] < nb[1] &&
+                             sb[2] - b0[2] < nb[2] && sb[0] >= b0[0] && sb[1] >= b0[1] &&
+                             sb[2] >= b0[2];
+        if (!in_cube) key = pack_brick(sb[0], sb[1], sb[2]);
       }
     }
-    const bool ins = key != kEmptyKey && key != last;
-    if (ins) last = key;
-    const unsigned act = __ballot_sync(0xffffffffu, ins);
-    if (ins) {
-      const unsigned peers = __match_any_sync(act, key);
-      if (lane == __ffs(peers) - 1) insert_brick(M, key);
-    }
+  }
+  const bool ins = key != kEmptyKey;
+  const unsigned act = __ballot_sync(0xffffffffu, ins);
+  if (ins) {
+    const unsigned peers = __match_any_sync(act, key);
+    if (lane == __ffs(peers) - 1) insert_brick(M, key);
   }
 }
 
@@ -319,7 +325,10 @@ cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const
   Pose P;
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 4; ++c) P.r[r][c] = pose[4 * r + c];
-  k_alloc<<<(n + 255) / 256, 256, 0, stream>>>(M, d_xyz, n, P, d_ret);
+  const int ba = (2 * M.m + 1 + 6) / 8 + 1;  // bricks a cube edge can span
+  const int nbmax = ba * ba * ba;
+  const uint64_t threads = (uint64_t)n * (nbmax + M.ns);
+  k_alloc<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(M, d_xyz, n, P, d_ret, nbmax);
   return cudaGetLastError();
 }
 
