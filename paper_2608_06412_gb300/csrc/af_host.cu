@@ -15,7 +15,7 @@
 
 namespace af {
 cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const float pose[16],
-                         float4* d_ret, cudaStream_t stream);
+                         float4* d_ret, uint32_t frame, cudaStream_t stream);
 cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], const float4* d_ret,
                         uint32_t frame, cudaStream_t stream);
 cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream);
@@ -279,6 +279,7 @@ static void free_all(af_ctx* c) {
   cudaFree(M.bkey);
   cudaFree(M.stamp);
   cudaFree(M.dirty);
+  cudaFree(M.rtab);
   cudaFree(M.occ);
   cudaFree(M.known);
   cudaFree(M.ctl);
@@ -351,6 +352,10 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   M.row_words = (M.dim_vox[0] + 63) / 64;
   M.hmask = cfg->hash_capacity - 1;
   M.pool_blocks = cfg->pool_blocks;
+  {
+    const int ba = (2 * M.m + 1 + 6) / 8 + 1;  // bricks a cube edge can span
+    M.nbmax = ba * ba * ba;
+  }
 
   auto alloc = [&](void** p, size_t bytes, int fill) -> af_status {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
@@ -376,6 +381,7 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   if (st == AF_OK) st = alloc((void**)&M.known, plane, 0);
   if (st == AF_OK) st = alloc((void**)&M.ctl, sizeof(af::Control), 0);
   if (st == AF_OK) st = alloc((void**)&c->d_ret, R * sizeof(float4), 0);
+  if (st == AF_OK) st = alloc((void**)&M.rtab, R * (size_t)M.nbmax * 4, 0);
   if (st == AF_OK) st = alloc((void**)&c->d_xyz, R * 12, 0);
   if (st == AF_OK) st = alloc((void**)&c->d_pts, Pm * 12, 0);
   if (st == AF_OK) st = alloc((void**)&c->d_nrm, Pm * 12, 0);
@@ -421,7 +427,7 @@ extern "C" af_status af_integrate_scan(af_ctx* ctx, const float* d_xyz, uint32_t
   ctx->frame = ctx->frame + 1 == 0 ? 1 : ctx->frame + 1;
   cudaStream_t s = (cudaStream_t)stream;
   const MapView& M = ctx->M;
-  AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, s); }));
+  AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, ctx->frame, s); }));
   if (n > 0)
     AF_CUDA(ctx, timed(ctx, 1, s, [&] { return af::launch_cube(M, n, pose, ctx->d_ret, ctx->frame, s); }));
   AF_CUDA(ctx, timed(ctx, 2, s, [&] { return af::launch_bitview(M, ctx->num_sms, s); }));

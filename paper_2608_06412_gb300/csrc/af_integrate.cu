@@ -1,52 +1,81 @@
 // af_integrate.cu -- scan-centric TSDF integration on sm_103a (Sec. 3.2, 3.4,
 // 3.6 of the paper), three launches per scan:
 //
-//  k_alloc     one thread per return: pose transform, validity, voxel index;
-//              inserts the bricks of its (2m+1)^3 cube and of its ray-cleared
-//              band samples into the hash. Lanes of a warp that carry the same
-//              brick key are merged with __match_any_sync, so one CAS per
-//              distinct key per warp reaches L2.
-//  k_integrate one CTA per tile of 32 returns: resolves each return's bricks
-//              once into shared memory, marks the cleared band, then one
-//              thread per (return, cube offset) pair computes d and adds
+//  k_alloc     one thread per (return, brick key): pose transform, validity,
+//              voxel index; inserts the bricks of the return's (2m+1)^3 cube
+//              and of its ray-cleared band samples into the hash. Lanes of a
+//              warp that carry the same key are merged with __match_any_sync,
+//              so one probe per distinct key per warp reaches L2. The pool
+//              index of each cube brick goes into a per-return brick table,
+//              and the brick is marked dirty.
+//  k_integrate one CTA per tile of 16 returns, one thread per cube offset: the
+//              tile's brick tables are loaded once (bricks created by this
+//              scan are looked up here), then each thread walks the tile's
+//              returns for its offset, computes d and adds
 //              (round(d 2^20) << 20) | 1 to the voxel word with one 64-bit
-//              atomic. Integer addition makes the result order-independent.
+//              atomic; integer addition makes the result order-independent.
+//              The cleared-band marks follow, off the barrier path.
 //  k_bitview   persistent over the scan's dirty bricks: weight cap with
 //              proportional rescale, then occupied / known bits packed with
 //              __ballot_sync into the dense bit planes.
 //
 // Every floating-point operation that decides an integer is an explicitly
-// rounded IEEE single-precision intrinsic, in the order the method states
-// it, so the result is reproducible bit for bit on any IEEE machine.
+// rounded IEEE single-precision operation, in the order the method states
+// it, so the result is reproducible bit for bit on any IEEE machine; where a
+// cheaper approximate value is used, it only takes decisions that the exact
+// value is certain to agree with (margins of 2^-16).
 #include "af_internal.cuh"
 
 namespace af {
 
-// Inserts a brick key; the inserting thread takes a pool index. Bounded probe.
-__device__ void insert_brick(const MapView& M, uint64_t key) {
+// Inserts a brick key (bounded probe) and returns its pool index: the index
+// this thread took if it inserted the key, the stored index if the key was
+// already there, or kNoBlock if another thread of this launch is inserting it
+// right now (or the pool is full).
+__device__ uint32_t insert_brick(const MapView& M, uint64_t key) {
   uint32_t h = hash_slot(key, M.hmask);
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(M.hkeys);
   for (uint32_t probe = 0; probe <= M.hmask; ++probe) {
-    const unsigned long long k = __ldcg(keys + h);
-    if (k == key) return;
+    unsigned long long k = __ldcg(keys + h);
     if (k == kEmptyKey) {
-      const unsigned long long prev = atomicCAS(keys + h, kEmptyKey, key);
-      if (prev == kEmptyKey) {
+      k = atomicCAS(keys + h, kEmptyKey, key);
+      if (k == kEmptyKey) {
         const uint32_t idx = atomicAdd(&M.ctl->pool_count, 1u);
         if (idx < M.pool_blocks) {
           M.bkey[idx] = key;
           M.hvals[h] = idx;
-        } else {
-          M.hvals[h] = kNoBlock;
-          latch_status(M.ctl, kStatusCapacity);
+          return idx;
         }
-        return;
+        M.hvals[h] = kNoBlock;
+        latch_status(M.ctl, kStatusCapacity);
+        return kNoBlock;
       }
-      if (prev == key) return;
+    }
+    if (k == key) {
+      const uint32_t b = __ldcg(M.hvals + h);
+      return b < M.pool_blocks ? b : kNoBlock;
     }
     h = (h + 1) & M.hmask;
   }
   latch_status(M.ctl, kStatusCapacity);
+  return kNoBlock;
+}
+
+__device__ inline void mark_dirty(const MapView& M, uint32_t blk, uint32_t frame) {
+  // read first: most returns touch bricks already marked by another return
+  if (__ldcg(M.stamp + blk) != frame && atomicExch(M.stamp + blk, frame) != frame) {
+    const uint32_t d = atomicAdd(&M.ctl->dirty_count, 1u);
+    M.dirty[d] = blk;
+  }
+}
+
+// Cube bricks of a return: first brick b0 and count nb per axis.
+__device__ inline void cube_bricks(const MapView& M, const int rel[3], int b0[3], int nb[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b0[a] = (rel[a] - M.m) >> 3;
+    nb[a] = ((rel[a] + M.m) >> 3) - b0[a] + 1;
+  }
 }
 
 // One thread per (return, brick key): key slots [0, nbmax) are the bricks of
@@ -55,13 +84,13 @@ __device__ void insert_brick(const MapView& M, uint64_t key) {
 // L2 probe); slot 0 also writes the return's world position for k_integrate.
 __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restrict__ xyz,
                                                 uint32_t n, Pose P, float4* __restrict__ ret,
-                                                int nbmax) {
+                                                uint32_t frame) {
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nbmax = M.nbmax;
   const int per = nbmax + M.ns;
   const uint32_t k = e / per;
   const int j = (int)(e % per);
   const int lane = threadIdx.x & 31;
-  if (e == 0) M.ctl->dirty_count = 0;
 
   float p[3] = {0.f, 0.f, 0.f}, range = 0.f;
   int rel[3] = {0, 0, 0};
@@ -74,17 +103,17 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
   if (lane == 0 && acc) atomicAdd(&M.ctl->returns_accepted, (unsigned long long)__popc(acc));
 
   uint64_t key = kEmptyKey;
+  bool cube_slot = false;
   if (valid) {
     int b0[3], nb[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      b0[a] = (rel[a] - M.m) >> 3;
-      nb[a] = ((rel[a] + M.m) >> 3) - b0[a] + 1;
-    }
+    cube_bricks(M, rel, b0, nb);
     if (j < nbmax) {
-      if (j < nb[0] * nb[1] * nb[2]) {
-        const int bx = j % nb[0], by = (j / nb[0]) % nb[1], bz = j / (nb[0] * nb[1]);
+      // table layout shared with k_integrate: slot j = bx + BA (by + BA bz)
+      const int ba = (2 * M.m + 7) / 8 + 1;
+      const int bx = j % ba, by = (j / ba) % ba, bz = j / (ba * ba);
+      if (bx < nb[0] && by < nb[1] && bz < nb[2]) {
         key = pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz);
+        cube_slot = true;
       }
     } else {
       const float q[3] = {P.r[0][3], P.r[1][3], P.r[2][3]};
@@ -92,26 +121,25 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
       if (band_sample(M, p, q, range, j - nbmax + 1, sv)) {
         const int sb[3] = {sv[0] >> 3, sv[1] >> 3, sv[2] >> 3};
         // bricks of the cube are inserted by the cube slots
-        const bool in_cube = sb[0] - b0[0] < nb[0] && sb[1] - b0[1] < nb[1] &&
-                             sb[2] - b0[2] < nb[2] && sb[0] >= b0[0] && sb[1] >= b0[1] &&
-                             sb[2] >= b0[2];
+        const bool in_cube = sb[0] >= b0[0] && sb[0] - b0[0] < nb[0] && sb[1] >= b0[1] &&
+                             sb[1] - b0[1] < nb[1] && sb[2] >= b0[2] && sb[2] - b0[2] < nb[2];
         if (!in_cube) key = pack_brick(sb[0], sb[1], sb[2]);
       }
     }
   }
   const bool ins = key != kEmptyKey;
   const unsigned act = __ballot_sync(0xffffffffu, ins);
+  uint32_t blk = kNoBlock;
   if (ins) {
     const unsigned peers = __match_any_sync(act, key);
-    if (lane == __ffs(peers) - 1) insert_brick(M, key);
+    const int leader = __ffs(peers) - 1;
+    if (lane == leader) blk = insert_brick(M, key);
+    blk = __shfl_sync(peers, blk, leader);
   }
-}
-
-__device__ inline void mark_dirty(const MapView& M, uint32_t blk, uint32_t frame) {
-  // read first: most returns touch bricks already marked by another return
-  if (__ldcg(M.stamp + blk) != frame && atomicExch(M.stamp + blk, frame) != frame) {
-    const uint32_t d = atomicAdd(&M.ctl->dirty_count, 1u);
-    M.dirty[d] = blk;
+  if (k < n && j < nbmax) {
+    // kNoBlock: created by another thread of this launch, resolved in k_integrate
+    M.rtab[(size_t)k * nbmax + j] = cube_slot ? blk : kUnused;
+    if (cube_slot && blk != kNoBlock) mark_dirty(M, blk, frame);
   }
 }
 
@@ -123,19 +151,28 @@ __device__ inline float sqrt_approx(float x) { return x * rsqrtf(x); }
 
 constexpr float kMargin = 1.52587890625e-05f;  // 2^-16
 
-// W = 2m + 1 voxels per cube edge; BA = bricks a cube edge can span.
 template <int W>
-__global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __restrict__ ret,
-                                                    uint32_t n, float q0, float q1, float q2,
-                                                    uint32_t frame) {
+struct CubeShape {
+  static constexpr int C = W * W * W;                                 // offsets
+  static constexpr int NT = ((C + 31) / 32) * 32 <= 1024 ? ((C + 31) / 32) * 32 : 1024;
+  static constexpr int OPT = (C + NT - 1) / NT;                       // offsets per thread
+  static constexpr int BA = (W + 6) / 8 + 1;                          // bricks per edge
+  static constexpr int NB = BA * BA * BA;
+  static constexpr int MR = W / 2;
+};
+
+// W = 2m + 1 voxels per cube edge.
+template <int W>
+__global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
+                                                                const float4* __restrict__ ret,
+                                                                uint32_t n, float q0, float q1,
+                                                                float q2, uint32_t frame) {
+  using S = CubeShape<W>;
   constexpr int T = 16;
-  constexpr int C = W * W * W;
-  constexpr int BA = (W + 6) / 8 + 1;
-  constexpr int NB = BA * BA * BA;
-  constexpr int MR = W / 2;
+  constexpr int C = S::C, NT = S::NT, OPT = S::OPT, BA = S::BA, NB = S::NB, MR = S::MR;
   __shared__ float4 s_p[T];        // p, valid flag
   __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
-  __shared__ int4 s_b0[T];         // first brick of the cube, w = nb packed
+  __shared__ int4 s_b0[T];         // first brick of the cube
   __shared__ float s_bb[T];        // |p - q|^2 as rounded in single precision
   __shared__ uint32_t s_blk[T][NB];
 
@@ -160,32 +197,107 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
       rel = make_int4(i[0] - M.dom_vox[0], i[1] - M.dom_vox[1], i[2] - M.dom_vox[2],
                       __float_as_int(range));
       b0 = make_int4((rel.x - MR) >> 3, (rel.y - MR) >> 3, (rel.z - MR) >> 3, 0);
-      const int nbx = ((rel.x + MR) >> 3) - b0.x + 1, nby = ((rel.y + MR) >> 3) - b0.y + 1,
-                nbz = ((rel.z + MR) >> 3) - b0.z + 1;
-      b0.w = nbx | (nby << 4) | (nbz << 8);
     }
     s_p[tid] = p;
     s_rel[tid] = rel;
     s_b0[tid] = b0;
     s_bb[tid] = bb;
   }
-  __syncthreads();
-
-  // Resolve each return's bricks once.
-  for (int e = tid; e < T * NB; e += blockDim.x) {
+  // The tile's brick tables; bricks created by this scan are looked up now.
+  for (int e = tid; e < T * NB; e += NT) {
     const int t = e / NB, j = e % NB;
-    const int bx = j % BA, by = (j / BA) % BA, bz = j / (BA * BA);
-    uint32_t blk = kNoBlock;
-    const int4 b0 = s_b0[t];
-    if (s_p[t].w != 0.f && bx < (b0.w & 15) && by < ((b0.w >> 4) & 15) &&
-        bz < ((b0.w >> 8) & 15)) {
-      blk = lookup_brick(M, pack_brick(b0.x + bx, b0.y + by, b0.z + bz));
-      if (blk != kNoBlock) mark_dirty(M, blk, frame);
+    const uint32_t k = r0 + t;
+    uint32_t blk = kUnused;
+    if (k < n) {
+      blk = M.rtab[(size_t)k * NB + j];
+      if (blk == kNoBlock) {
+        const float4 p = ret[k];
+        int i[3];
+        voxel_index(p.x, M.v, &i[0]);
+        voxel_index(p.y, M.v, &i[1]);
+        voxel_index(p.z, M.v, &i[2]);
+        const int rel[3] = {i[0] - M.dom_vox[0], i[1] - M.dom_vox[1], i[2] - M.dom_vox[2]};
+        int b0[3], nb[3];
+        cube_bricks(M, rel, b0, nb);
+        const int bx = j % BA, by = (j / BA) % BA, bz = j / (BA * BA);
+        blk = lookup_brick(M, pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz));
+        if (blk != kNoBlock) mark_dirty(M, blk, frame);
+      }
     }
     s_blk[t][j] = blk;
   }
+  __syncthreads();
+
+  // This thread's cube offsets (ox fastest, so neighbouring threads update
+  // neighbouring voxel words).
+  int ox[OPT], oy[OPT], oz[OPT];
+#pragma unroll
+  for (int s = 0; s < OPT; ++s) {
+    const int o = tid + s * NT;
+    ox[s] = o % W - MR;
+    oy[s] = (o / W) % W - MR;
+    oz[s] = o / (W * W) - MR;
+  }
+
+  const float v = M.v, tau = M.tau, cone = M.cone_cos;
+  for (int t = 0; t < T; ++t) {
+    const float4 p = s_p[t];
+    if (p.w == 0.f) continue;  // uniform across the block
+    const int4 rel = s_rel[t];
+    const int4 b0 = s_b0[t];
+    const float range = __int_as_float(rel.w);
+    const float bb = s_bb[t];
+    const float bq0 = __fsub_rn(p.x, q0), bq1 = __fsub_rn(p.y, q1), bq2 = __fsub_rn(p.z, q2);
+#pragma unroll
+    for (int s = 0; s < OPT; ++s) {
+      if (tid + s * NT >= C) break;
+      const int jx = rel.x + ox[s], jy = rel.y + oy[s], jz = rel.z + oz[s];
+      // voxel centre x (absolute index)
+      const float x0 = voxel_centre(jx + M.dom_vox[0], v);
+      const float x1 = voxel_centre(jy + M.dom_vox[1], v);
+      const float x2 = voxel_centre(jz + M.dom_vox[2], v);
+      // behind-surface cone: theta between x - p and p - q; excluded iff
+      // RN(dot / RN(RN(sqrt(aa)) * range)) > cone
+      const float a0 = __fsub_rn(x0, p.x), a1 = __fsub_rn(x1, p.y), a2 = __fsub_rn(x2, p.z);
+      const float aa = __fadd_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(a1, a1)), __fmul_rn(a2, a2));
+      if (aa > 0.f) {
+        const float dot =
+            __fadd_rn(__fadd_rn(__fmul_rn(a0, bq0), __fmul_rn(a1, bq1)), __fmul_rn(a2, bq2));
+        // dot <= 0 makes the rounded cosine <= 0, so with cone >= 0 it is kept
+        if (dot > 0.f || cone < 0.f) {
+          bool decided = false;
+          if (aa > 1e-20f) {
+            const float ca = __fdividef(dot, sqrt_approx(aa) * range);
+            if (ca > cone + kMargin) continue;  // certainly excluded
+            decided = ca < cone - kMargin;      // certainly kept
+          }
+          if (!decided && __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range)) > cone) continue;
+        }
+      }
+      // d = |p - q| - |x - q|, clamped to [0, tau]
+      const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
+      const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
+      float d;
+      if (cc >= bb) {
+        d = 0.f;  // |x - q| >= |p - q|: the rounded difference is <= 0
+      } else if (cc > 1e-20f && range - sqrt_approx(cc) > tau + range * kMargin) {
+        d = tau;  // the exact difference exceeds tau
+      } else {
+        d = __fsub_rn(range, __fsqrt_rn(cc));
+        d = d < 0.f ? 0.f : d;
+        d = d > tau ? tau : d;
+      }
+      const unsigned long long dq = (unsigned long long)__float2uint_rn(__fmul_rn(d, kScale));
+      const int bl = ((jx >> 3) - b0.x) + BA * (((jy >> 3) - b0.y) + BA * ((jz >> 3) - b0.z));
+      const uint32_t blk = s_blk[t][bl];
+      if (blk >= M.pool_blocks) continue;
+      const int l = (jx & 7) | ((jy & 7) << 3) | ((jz & 7) << 6);
+      atomicAdd(M.vox + (size_t)blk * kBrickVox + l, (dq << kWBits) | 1ull);
+    }
+  }
+
   // Ray-cleared band toward the sensor (append-only, does not touch S or w).
-  for (int e = tid; e < T * M.ns; e += blockDim.x) {
+  for (int e = tid; e < T * M.ns; e += NT) {
     const int t = e / M.ns, s = e % M.ns + 1;
     if (s_p[t].w == 0.f) continue;
     const float p[3] = {s_p[t].x, s_p[t].y, s_p[t].z};
@@ -197,66 +309,7 @@ __global__ void __launch_bounds__(256) k_integrate(MapView M, const float4* __re
     atomicOr(M.cleared + blk * 16 + (l >> 5), 1u << (l & 31));
     mark_dirty(M, blk, frame);
   }
-  __syncthreads();
-
-  const float v = M.v, tau = M.tau, cone = M.cone_cos;
-  for (int e = tid; e < T * C; e += blockDim.x) {
-    const int t = e / C, o = e % C;
-    const float4 p = s_p[t];
-    if (p.w == 0.f) continue;
-    const int4 rel = s_rel[t];
-    const float range = __int_as_float(rel.w);
-    const int jx = rel.x + (o % W) - MR;
-    const int jy = rel.y + (o / W) % W - MR;
-    const int jz = rel.z + o / (W * W) - MR;
-    // voxel centre x (absolute index)
-    const float x0 = voxel_centre(jx + M.dom_vox[0], v);
-    const float x1 = voxel_centre(jy + M.dom_vox[1], v);
-    const float x2 = voxel_centre(jz + M.dom_vox[2], v);
-    // behind-surface cone: theta between x - p and p - q; excluded iff
-    // RN(dot / RN(RN(sqrt(aa)) * range)) > cone
-    const float a0 = __fsub_rn(x0, p.x), a1 = __fsub_rn(x1, p.y), a2 = __fsub_rn(x2, p.z);
-    const float aa = __fadd_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(a1, a1)), __fmul_rn(a2, a2));
-    if (aa > 0.f) {
-      const float b0 = __fsub_rn(p.x, q0), b1 = __fsub_rn(p.y, q1), b2 = __fsub_rn(p.z, q2);
-      const float dot =
-          __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));
-      // dot <= 0 makes the rounded cosine <= 0, so with cone >= 0 it is kept
-      if (dot > 0.f || cone < 0.f) {
-        bool decided = false;
-        if (aa > 1e-20f) {
-          const float ca = __fdividef(dot, sqrt_approx(aa) * range);
-          if (ca > cone + kMargin) continue;        // certainly excluded
-          decided = ca < cone - kMargin;            // certainly kept
-        }
-        if (!decided &&
-            __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range)) > cone)
-          continue;
-      }
-    }
-    // d = |p - q| - |x - q|, clamped to [0, tau]
-    const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
-    const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
-    float d;
-    if (cc >= s_bb[t]) {
-      d = 0.f;  // |x - q| >= |p - q|: the rounded difference is <= 0
-    } else if (cc > 1e-20f && range - sqrt_approx(cc) > tau + range * kMargin) {
-      d = tau;  // the exact difference exceeds tau
-    } else {
-      d = __fsub_rn(range, __fsqrt_rn(cc));
-      d = d < 0.f ? 0.f : d;
-      d = d > tau ? tau : d;
-    }
-    const unsigned long long dq = (unsigned long long)__float2uint_rn(__fmul_rn(d, kScale));
-    const int4 b0 = s_b0[t];
-    const int bl = ((jx >> 3) - b0.x) + BA * (((jy >> 3) - b0.y) + BA * ((jz >> 3) - b0.z));
-    const uint32_t blk = s_blk[t][bl];
-    if (blk == kNoBlock) continue;
-    const int l = (jx & 7) | ((jy & 7) << 3) | ((jz & 7) << 6);
-    atomicAdd(M.vox + (size_t)blk * kBrickVox + l, (dq << kWBits) | 1ull);
-  }
 }
-
 
 // Weight cap and bit view of every brick touched by the scan.
 __global__ void __launch_bounds__(512) k_bitview(MapView M) {
@@ -320,15 +373,14 @@ cudaError_t launch_export_flags(const MapView& M, uint32_t count, uint8_t* d_fla
 
 // Host-side launchers of the three integration kernels (on `stream`).
 cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const float pose[16],
-                         float4* d_ret, cudaStream_t stream) {
-  if (n == 0) return cudaMemsetAsync(&M.ctl->dirty_count, 0, sizeof(uint32_t), stream);
+                         float4* d_ret, uint32_t frame, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(&M.ctl->dirty_count, 0, sizeof(uint32_t), stream);
+  if (e != cudaSuccess || n == 0) return e;
   Pose P;
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 4; ++c) P.r[r][c] = pose[4 * r + c];
-  const int ba = (2 * M.m + 1 + 6) / 8 + 1;  // bricks a cube edge can span
-  const int nbmax = ba * ba * ba;
-  const uint64_t threads = (uint64_t)n * (nbmax + M.ns);
-  k_alloc<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(M, d_xyz, n, P, d_ret, nbmax);
+  const uint64_t threads = (uint64_t)n * (M.nbmax + M.ns);
+  k_alloc<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(M, d_xyz, n, P, d_ret, frame);
   return cudaGetLastError();
 }
 
@@ -337,8 +389,11 @@ cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], cons
   if (n == 0) return cudaSuccess;
   const unsigned grid = (n + 15) / 16;  // k_integrate tiles of 16 returns
   switch (2 * M.m + 1) {
-#define AF_CASE(W) \
-  case W: k_integrate<W><<<grid, 256, 0, stream>>>(M, d_ret, n, pose[3], pose[7], pose[11], frame); break;
+#define AF_CASE(W)                                                                          \
+  case W:                                                                                   \
+    k_integrate<W><<<grid, CubeShape<W>::NT, 0, stream>>>(M, d_ret, n, pose[3], pose[7],   \
+                                                          pose[11], frame);                 \
+    break;
     AF_CASE(3) AF_CASE(5) AF_CASE(7) AF_CASE(9) AF_CASE(11) AF_CASE(13) AF_CASE(15) AF_CASE(17)
 #undef AF_CASE
     default: return cudaErrorInvalidValue;

@@ -25,6 +25,7 @@ namespace af {
 
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr uint32_t kNoBlock = ~0u;
+constexpr uint32_t kUnused = ~0u - 2;  // brick-table slot outside the return's cube
 constexpr int kBrick = 8;
 constexpr int kBrickVox = 512;
 constexpr int kWBits = 20;
@@ -66,6 +67,9 @@ struct MapView {
   uint32_t* stamp;          // pool_blocks
   uint32_t* dirty;          // pool_blocks
   uint32_t pool_blocks;
+  // per-scan scratch: the pool index of each cube brick of each return
+  uint32_t* rtab;           // max_returns * nbmax
+  int nbmax;                // bricks a cube can span: ((2m + 7) / 8 + 1)^3
   // planes
   unsigned long long* occ;
   unsigned long long* known;
