@@ -272,12 +272,10 @@ static void free_all(af_ctx* c) {
   c->prof.clear();
   c->ev_free.clear();
   MapView& M = c->M;
-  cudaFree(M.hkeys);
-  cudaFree(M.hvals);
+  cudaFree(M.slots);
   cudaFree(M.vox);
   cudaFree(M.cleared);
   cudaFree(M.bkey);
-  cudaFree(M.stamp);
   cudaFree(M.dirty);
   cudaFree(M.rtab);
   cudaFree(M.occ);
@@ -333,6 +331,7 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   c->cfg = *cfg;
   MapView& M = c->M;
   M.v = cfg->voxel_size;
+  M.inv_v = 1.0f / cfg->voxel_size;
   M.tau = cfg->truncation;
   M.r_c = cfg->r_c;
   M.cone_cos = cfg->cone_cos;
@@ -370,12 +369,10 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   const size_t plane = (size_t)M.row_words * 8 * M.dim_vox[1] * M.dim_vox[2];
   const size_t R = cfg->max_returns, Pm = cfg->max_points;
   af_status st = AF_OK;
-  if (st == AF_OK) st = alloc((void**)&M.hkeys, H * 8, 0xFF);
-  if (st == AF_OK) st = alloc((void**)&M.hvals, H * 4, 0xFF);
+  if (st == AF_OK) st = alloc((void**)&M.slots, H * sizeof(af::HashSlot), 0xFF);
   if (st == AF_OK) st = alloc((void**)&M.vox, P * af::kBrickVox * 8, 0);
   if (st == AF_OK) st = alloc((void**)&M.cleared, P * 16 * 4, 0);
   if (st == AF_OK) st = alloc((void**)&M.bkey, P * 8, 0);
-  if (st == AF_OK) st = alloc((void**)&M.stamp, P * 4, 0);
   if (st == AF_OK) st = alloc((void**)&M.dirty, P * 4, 0);
   if (st == AF_OK) st = alloc((void**)&M.occ, plane, 0);
   if (st == AF_OK) st = alloc((void**)&M.known, plane, 0);
@@ -424,7 +421,8 @@ extern "C" af_status af_integrate_scan(af_ctx* ctx, const float* d_xyz, uint32_t
                 ctx->cfg.max_returns);
   for (int k = 0; k < 12; ++k)
     if (!std::isfinite(pose[k])) return fail(ctx, AF_ERR_INVALID_ARG, "non-finite pose");
-  ctx->frame = ctx->frame + 1 == 0 ? 1 : ctx->frame + 1;
+  // scan stamps: 1 .. 2^32 - 2 (all ones marks a slot that no scan touched)
+  ctx->frame = ctx->frame + 1 >= 0xFFFFFFFFu ? 1 : ctx->frame + 1;
   cudaStream_t s = (cudaStream_t)stream;
   const MapView& M = ctx->M;
   AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, ctx->frame, s); }));

@@ -24,6 +24,8 @@
 // it, so the result is reproducible bit for bit on any IEEE machine; where a
 // cheaper approximate value is used, it only takes decisions that the exact
 // value is certain to agree with (margins of 2^-16).
+#include <cooperative_groups.h>
+
 #include "af_internal.cuh"
 
 namespace af {
@@ -32,28 +34,32 @@ namespace af {
 // this thread took if it inserted the key, the stored index if the key was
 // already there, or kNoBlock if another thread of this launch is inserting it
 // right now (or the pool is full).
-__device__ uint32_t insert_brick(const MapView& M, uint64_t key) {
+// *slot receives the slot index and *stamp the slot's scan stamp as read.
+__device__ uint32_t insert_brick(const MapView& M, uint64_t key, uint32_t* slot,
+                                 uint32_t* stamp) {
   uint32_t h = hash_slot(key, M.hmask);
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(M.hkeys);
   for (uint32_t probe = 0; probe <= M.hmask; ++probe) {
-    unsigned long long k = __ldcg(keys + h);
+    unsigned long long k;
+    uint32_t val;
+    load_slot(M, h, &k, &val, stamp);
     if (k == kEmptyKey) {
-      k = atomicCAS(keys + h, kEmptyKey, key);
+      k = atomicCAS(&M.slots[h].key, kEmptyKey, key);
       if (k == kEmptyKey) {
+        *slot = h;
         const uint32_t idx = atomicAdd(&M.ctl->pool_count, 1u);
         if (idx < M.pool_blocks) {
           M.bkey[idx] = key;
-          M.hvals[h] = idx;
+          M.slots[h].val = idx;
           return idx;
         }
-        M.hvals[h] = kNoBlock;
         latch_status(M.ctl, kStatusCapacity);
         return kNoBlock;
       }
+      val = kNoBlock;  // another thread is filling this slot right now
     }
     if (k == key) {
-      const uint32_t b = __ldcg(M.hvals + h);
-      return b < M.pool_blocks ? b : kNoBlock;
+      *slot = h;
+      return val < M.pool_blocks ? val : kNoBlock;
     }
     h = (h + 1) & M.hmask;
   }
@@ -61,12 +67,22 @@ __device__ uint32_t insert_brick(const MapView& M, uint64_t key) {
   return kNoBlock;
 }
 
-__device__ inline void mark_dirty(const MapView& M, uint32_t blk, uint32_t frame) {
-  // read first: most returns touch bricks already marked by another return
-  if (__ldcg(M.stamp + blk) != frame && atomicExch(M.stamp + blk, frame) != frame) {
-    const uint32_t d = atomicAdd(&M.ctl->dirty_count, 1u);
-    M.dirty[d] = blk;
-  }
+// Appends blk (hash slot h, whose stamp was read as `seen`) to the scan's
+// dirty list once per scan: the stamp decides which thread appends. Appends
+// are aggregated over the threads that call together: one counter atomic per
+// group instead of one per brick.
+__device__ inline void mark_dirty(const MapView& M, uint32_t h, uint32_t blk, uint32_t frame,
+                                  uint32_t seen) {
+  namespace cg = cooperative_groups;
+  const cg::coalesced_group g = cg::coalesced_threads();
+  const bool need = seen != frame && atomicExch(&M.slots[h].stamp, frame) != frame;
+  const unsigned nm = g.ballot(need);
+  if (nm == 0u) return;
+  const int first = __ffs(nm) - 1;
+  uint32_t base = 0;
+  if ((int)g.thread_rank() == first) base = atomicAdd(&M.ctl->dirty_count, (unsigned)__popc(nm));
+  base = g.shfl(base, first);
+  if (need) M.dirty[base + __popc(nm & ((1u << g.thread_rank()) - 1u))] = blk;
 }
 
 // Cube bricks of a return: first brick b0 and count nb per axis.
@@ -133,14 +149,16 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
   if (ins) {
     const unsigned peers = __match_any_sync(act, key);
     const int leader = __ffs(peers) - 1;
-    if (lane == leader) blk = insert_brick(M, key);
+    if (lane == leader) {
+      uint32_t h, seen;
+      blk = insert_brick(M, key, &h, &seen);
+      if (blk != kNoBlock) mark_dirty(M, h, blk, frame, seen);
+    }
     blk = __shfl_sync(peers, blk, leader);
   }
-  if (k < n && j < nbmax) {
-    // kNoBlock: created by another thread of this launch, resolved in k_integrate
-    M.rtab[(size_t)k * nbmax + j] = cube_slot ? blk : kUnused;
-    if (cube_slot && blk != kNoBlock) mark_dirty(M, blk, frame);
-  }
+  // kNoBlock: created by another thread of this launch, resolved (and marked
+  // dirty) in k_integrate
+  if (k < n && j < nbmax) M.rtab[(size_t)k * nbmax + j] = cube_slot ? blk : kUnused;
 }
 
 // Approximate square root (MUFU reciprocal square root), relative error well
@@ -191,9 +209,9 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
       bb = __fadd_rn(__fadd_rn(__fmul_rn(b[0], b[0]), __fmul_rn(b[1], b[1])), __fmul_rn(b[2], b[2]));
       const float range = __fsqrt_rn(bb);
       int i[3];
-      voxel_index(p.x, M.v, &i[0]);
-      voxel_index(p.y, M.v, &i[1]);
-      voxel_index(p.z, M.v, &i[2]);
+      voxel_index(p.x, M, &i[0]);
+      voxel_index(p.y, M, &i[1]);
+      voxel_index(p.z, M, &i[2]);
       rel = make_int4(i[0] - M.dom_vox[0], i[1] - M.dom_vox[1], i[2] - M.dom_vox[2],
                       __float_as_int(range));
       b0 = make_int4((rel.x - MR) >> 3, (rel.y - MR) >> 3, (rel.z - MR) >> 3, 0);
@@ -213,15 +231,17 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
       if (blk == kNoBlock) {
         const float4 p = ret[k];
         int i[3];
-        voxel_index(p.x, M.v, &i[0]);
-        voxel_index(p.y, M.v, &i[1]);
-        voxel_index(p.z, M.v, &i[2]);
+        voxel_index(p.x, M, &i[0]);
+        voxel_index(p.y, M, &i[1]);
+        voxel_index(p.z, M, &i[2]);
         const int rel[3] = {i[0] - M.dom_vox[0], i[1] - M.dom_vox[1], i[2] - M.dom_vox[2]};
         int b0[3], nb[3];
         cube_bricks(M, rel, b0, nb);
         const int bx = j % BA, by = (j / BA) % BA, bz = j / (BA * BA);
-        blk = lookup_brick(M, pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz));
-        if (blk != kNoBlock) mark_dirty(M, blk, frame);
+        uint32_t val, seen;
+        const int h = find_slot(M, pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz), &val, &seen);
+        blk = (h >= 0 && val < M.pool_blocks) ? val : kNoBlock;
+        if (blk != kNoBlock) mark_dirty(M, (uint32_t)h, blk, frame, seen);
       }
     }
     s_blk[t][j] = blk;
@@ -303,11 +323,12 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
     const float p[3] = {s_p[t].x, s_p[t].y, s_p[t].z};
     int sv[3];
     if (!band_sample(M, p, q, __int_as_float(s_rel[t].w), s, sv)) continue;
-    const uint32_t blk = lookup_brick(M, pack_brick(sv[0] >> 3, sv[1] >> 3, sv[2] >> 3));
-    if (blk == kNoBlock) continue;
+    uint32_t blk, seen;
+    const int h = find_slot(M, pack_brick(sv[0] >> 3, sv[1] >> 3, sv[2] >> 3), &blk, &seen);
+    if (h < 0 || blk >= M.pool_blocks) continue;
     const int l = (sv[0] & 7) | ((sv[1] & 7) << 3) | ((sv[2] & 7) << 6);
     atomicOr(M.cleared + blk * 16 + (l >> 5), 1u << (l & 31));
-    mark_dirty(M, blk, frame);
+    mark_dirty(M, (uint32_t)h, blk, frame, seen);
   }
 }
 

@@ -45,10 +45,20 @@ struct Control {
   unsigned long long tests;
 };
 
+// One hash slot, 16 bytes, so that one load returns the brick key, its pool
+// index and the scan stamp that deduplicates dirty-brick marks. All ones =
+// empty slot (key ~0, pool index kNoBlock, stamp never equal to a scan).
+struct alignas(16) HashSlot {
+  unsigned long long key;
+  uint32_t val;
+  uint32_t stamp;
+};
+
 // Everything a kernel needs about the map; passed by value.
 struct MapView {
   // geometry
   float v, tau, r_c, cone_cos, range_min, range_max, clear_lo, clear_hi;
+  float inv_v;        // 1 / v rounded to single precision
   int m;              // cube radius
   int ns;             // cleared-band samples
   uint32_t w_min, w_cap;
@@ -57,14 +67,12 @@ struct MapView {
   int dim_vox[3];     // box size in voxels (multiples of 8)
   int row_words;      // u64 words per plane row
   // hash
-  uint64_t* hkeys;
-  uint32_t* hvals;
+  struct HashSlot* slots;
   uint32_t hmask;     // capacity - 1
   // pool
   unsigned long long* vox;  // pool_blocks * 512 packed words
   uint32_t* cleared;        // pool_blocks * 16
   uint64_t* bkey;           // pool_blocks
-  uint32_t* stamp;          // pool_blocks
   uint32_t* dirty;          // pool_blocks
   uint32_t pool_blocks;
   // per-scan scratch: the pool index of each cube brick of each return
@@ -104,29 +112,53 @@ __device__ inline uint32_t hash_slot(uint64_t key, uint32_t mask) {
   return (uint32_t)key & mask;
 }
 
-// Pool index of a brick, or kNoBlock. Read-only probe; never spins: at most
-// hmask + 1 slots are visited.
-__device__ inline uint32_t lookup_brick(const MapView& M, uint64_t key) {
+// One 16-byte slot read: key, pool index, stamp.
+__device__ inline void load_slot(const MapView& M, uint32_t h, unsigned long long* key,
+                                 uint32_t* val, uint32_t* stamp) {
+  const uint4 s = __ldcg(reinterpret_cast<const uint4*>(M.slots) + h);
+  *key = (unsigned long long)s.x | ((unsigned long long)s.y << 32);
+  *val = s.z;
+  *stamp = s.w;
+}
+
+// Slot holding `key` (or -1) with its pool index and stamp. Read-only probe;
+// never spins: at most hmask + 1 slots are visited.
+__device__ inline int find_slot(const MapView& M, uint64_t key, uint32_t* val, uint32_t* stamp) {
   uint32_t h = hash_slot(key, M.hmask);
   for (uint32_t probe = 0; probe <= M.hmask; ++probe) {
-    const uint64_t k = __ldcg(reinterpret_cast<const unsigned long long*>(M.hkeys) + h);
-    if (k == key) {
-      const uint32_t b = __ldcg(M.hvals + h);
-      return b < M.pool_blocks ? b : kNoBlock;
-    }
-    if (k == kEmptyKey) return kNoBlock;
+    unsigned long long k;
+    load_slot(M, h, &k, val, stamp);
+    if (k == key) return (int)h;
+    if (k == kEmptyKey) return -1;
     h = (h + 1) & M.hmask;
   }
-  return kNoBlock;
+  return -1;
+}
+
+// Pool index of a brick, or kNoBlock.
+__device__ inline uint32_t lookup_brick(const MapView& M, uint64_t key) {
+  uint32_t val, stamp;
+  if (find_slot(M, key, &val, &stamp) < 0) return kNoBlock;
+  return val < M.pool_blocks ? val : kNoBlock;
 }
 
 __device__ inline void latch_status(Control* c, uint32_t code) {
   atomicCAS(&c->status, 0u, code);
 }
 
-// Voxel index of a coordinate, floor(c / v) in IEEE single precision.
-__device__ inline bool voxel_index(float c, float v, int* out) {
-  const float f = floorf(__fdiv_rn(c, v));
+// Voxel index of a coordinate, floor(c / v) with c / v rounded in IEEE single
+// precision. The product with the rounded reciprocal 1/v lies within
+// |c / v| 2^-22 of the rounded quotient; when no integer lies within
+// |c / v| 2^-20 of the product the floor is already decided by it, and
+// otherwise the correctly rounded division decides. Same result either way.
+__device__ inline bool voxel_index(float c, const MapView& M, int* out) {
+  const float qa = c * M.inv_v;
+  const float e = fabsf(qa) * 9.5367431640625e-07f;  // 2^-20
+  float f;
+  if (fabsf(qa) > 1e-30f && floorf(qa - e) == floorf(qa + e))
+    f = floorf(qa);
+  else
+    f = floorf(__fdiv_rn(c, M.v));
   if (!(f >= -1.0e9f && f <= 1.0e9f)) return false;
   *out = (int)f;
   return true;
@@ -161,7 +193,7 @@ __device__ inline bool prepare_return(const MapView& M, const Pose& P, float sx,
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     int i;
-    if (!voxel_index(p[k], M.v, &i)) return false;
+    if (!voxel_index(p[k], M, &i)) return false;
     rel[k] = i - M.dom_vox[k];
     if (rel[k] - M.m < 0 || rel[k] + M.m >= M.dim_vox[k]) return false;
   }
@@ -179,7 +211,7 @@ __device__ inline bool band_sample(const MapView& M, const float p[3], const flo
   for (int k = 0; k < 3; ++k) {
     const float u = __fdiv_rn(__fsub_rn(q[k], p[k]), range);
     int i;
-    if (!voxel_index(__fadd_rn(p[k], __fmul_rn(dist, u)), M.v, &i)) return false;
+    if (!voxel_index(__fadd_rn(p[k], __fmul_rn(dist, u)), M, &i)) return false;
     rel[k] = i - M.dom_vox[k];
     if (rel[k] < 0 || rel[k] >= M.dim_vox[k]) return false;
   }

@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(256) k_na_integrate(MapView M, const float4* _
     const float range =
         __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(b0, b0), __fmul_rn(b1, b1)), __fmul_rn(b2, b2)));
     int i[3];
-    voxel_index(p.x, M.v, &i[0]);
-    voxel_index(p.y, M.v, &i[1]);
-    voxel_index(p.z, M.v, &i[2]);
+    voxel_index(p.x, M, &i[0]);
+    voxel_index(p.y, M, &i[1]);
+    voxel_index(p.z, M, &i[2]);
     const int jx = i[0] - M.dom_vox[0] + o % W - M.m;
     const int jy = i[1] - M.dom_vox[1] + (o / W) % W - M.m;
     const int jz = i[2] - M.dom_vox[2] + o / (W * W) - M.m;
@@ -218,6 +218,7 @@ extern "C" af_status af_integrate_scan_noalloc(const af_config* cfg, const float
 
   MapView M{};
   M.v = cfg->voxel_size;
+  M.inv_v = 1.0f / cfg->voxel_size;
   M.tau = cfg->truncation;
   M.r_c = cfg->r_c;
   M.cone_cos = cfg->cone_cos;

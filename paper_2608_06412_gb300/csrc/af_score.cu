@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
   // the point's voxel and its weight (confidence gate, Sec. 3.5)
   int i0, i1, i2;
   const bool ok =
-      voxel_index(s0, M.v, &i0) && voxel_index(s1, M.v, &i1) && voxel_index(s2, M.v, &i2);
+      voxel_index(s0, M, &i0) && voxel_index(s1, M, &i1) && voxel_index(s2, M, &i2);
   Pt P;
   P.px = i0 - M.dom_vox[0];
   P.py = i1 - M.dom_vox[1];
@@ -279,7 +279,7 @@ cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts
                          const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
                          cudaStream_t stream) {
   if (m == 0) return cudaSuccess;
-  constexpr int WARPS = 4;
+  constexpr int WARPS = 2;
   k_score<WARPS><<<(m + WARPS - 1) / WARPS, WARPS * 32, 0, stream>>>(M, T, d_pts, d_nrm, m,
                                                                       d_label, d_best);
   return cudaGetLastError();
