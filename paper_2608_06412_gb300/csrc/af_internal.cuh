@@ -2,16 +2,16 @@
 // kernels of libaf (sm_103a).
 //
 // Map layout in HBM (all allocated once in af_create):
-//  * hash   : open addressing, hash_capacity slots of (u64 brick key, u32 pool
-//             index). Keys are domain-relative brick coordinates packed 21 bits
-//             per axis; ~0 marks an empty slot, ~0u an unusable index.
+//  * hash   : open addressing, hash_capacity 16-byte slots of (u64 brick key,
+//             u32 pool index, u32 scan stamp for dirty-brick deduplication).
+//             Keys are domain-relative brick coordinates packed 21 bits per
+//             axis; all ones marks an empty slot.
 //  * pool   : bricks of 8^3 voxels. Each voxel is ONE u64 word holding
 //             (S << 20) | w, so a contribution is a single 64-bit atomic add
 //             of (round(d 2^20) << 20) | 1 and integer addition makes the sum
 //             independent of the order of the returns. w < 2^20 is guaranteed
 //             by max_returns + w_cap < 2^20 and S < 2^44 by tau <= 1 m.
-//             Next to it: 512 cleared bits per brick, the brick key, a frame
-//             stamp for dirty-brick deduplication.
+//             Next to it: 512 cleared bits per brick and the brick key.
 //  * planes : the occupied and known views as dense bit planes over the map
 //             box, one bit per voxel, rows along x (64 voxels per u64 word),
 //             row index z * Y + y. A brick row of 8 voxels is one byte, so the
