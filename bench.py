@@ -263,6 +263,20 @@ def _traffic(kernel: str):
     return nbytes
 
 
+def reduce_over_ranks(tests: float, total_ms: float, ws: int, device=None):
+    """Whole-job totals of independent replicas: the tests of all ranks, and
+    the slowest rank's timed milliseconds."""
+    if ws <= 1:
+        return tests, total_ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([tests], dtype=torch.float64, device=device)
+    mm = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    dist.all_reduce(mm, op=dist.ReduceOp.MAX)
+    return float(tt.item()), float(mm.item())
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -275,8 +289,8 @@ def run_ours(args, W, ws, rank, local):
     dev = torch.device("cuda", local)
     nfr = args.warmup + args.steps
     frames = _frames(W, 0, nfr)
-    caps = dict(hash_capacity=1 << 19, pool_blocks=1 << 18, max_returns=1 << 16,
-                max_points=1 << 16)
+    from paper_2608_06412_gb300.workload import BENCH_CAPS
+    caps = dict(BENCH_CAPS)
 
     d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
     d_pts = [torch.from_numpy(f[1]).to(dev) for f in frames]
@@ -380,18 +394,7 @@ def run_ours(args, W, ws, rank, local):
                "ms_per_step": (t1 - t0) * 1e3 / args.steps}
         g.close()
 
-    # aggregate over ranks: sum of tests, max of time
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([float(tests), total_ms], dtype=torch.float64)
-        tt = torch.tensor([float(tests)], dtype=torch.float64)
-        mm = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        dist.all_reduce(mm, op=dist.ReduceOp.MAX)
-        tests_all, total_ms_max = float(tt.item()), float(mm.item())
-        del t
-    else:
-        tests_all, total_ms_max = float(tests), total_ms
+    tests_all, total_ms_max = reduce_over_ranks(float(tests), total_ms, ws, dev)
 
     returns = sum(len(frames[k][0].pts) for k in range(args.warmup, nfr))
     peak, peak_kind = _peaks()

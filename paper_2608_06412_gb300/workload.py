@@ -86,3 +86,10 @@ def pine_frame(W: Workload, f: int):
                              frames_per_orbit=p["frames_per_orbit"])
     pts, nrm = synth.surface_points(fr.world, fr.normal, p["v"])
     return fr, pts, nrm
+
+
+#: Map capacities the benchmark uses for the pine stream (and the full-size
+#: parity test runs with): 512k hash slots, 256k bricks (1.1 GB), 64k returns
+#: and points per call.
+BENCH_CAPS = dict(hash_capacity=1 << 19, pool_blocks=1 << 18, max_returns=1 << 16,
+                  max_points=1 << 16)
