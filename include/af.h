@@ -203,6 +203,56 @@ af_status af_kernel_offsets(const af_tool *tool, float voxel_size, const float u
 af_status af_arm_offsets(float voxel_size, float truncation, const float u[3], int32_t h_out[9]);
 
 /*
+ * Batched ticks: many maps (scenes), each with its own scan, tool and
+ * direction table, integrated and scored together -- one CUDA graph launch
+ * per tick whose persistent kernels share the GPU across scenes of uneven
+ * size. The result of a tick is exactly that of af_integrate_scan followed
+ * by af_score on every scene (Sec. 3.2 - 3.5; the batching itself is the
+ * implementation's, not the paper's).
+ *
+ * af_batch_create groups existing contexts (same device, same cube_radius,
+ * each at most once); they must outlive the batch and must not be used on
+ * another stream while a tick is in flight. Each tick reads the scenes' tools
+ * as set at that time.
+ */
+typedef struct af_batch af_batch;
+
+typedef struct {
+    const float *d_xyz;      /* n x 3 returns, sensor frame (as af_integrate_scan) */
+    uint32_t n;              /* 0 <= n <= the scene's max_returns                  */
+    float pose[16];          /* world_from_sensor, row-major                       */
+    const float *d_pts;      /* m x 3 points to score after integration            */
+    const float *d_normals;  /* m x 3 normals                                      */
+    uint32_t m;              /* 0 = score nothing for this scene                   */
+    uint8_t *d_label;        /* m labels (as af_score)                             */
+    int16_t *d_best;         /* m best-direction indices                           */
+} af_batch_item;
+
+/* Launch shape of a batch: integration tile and scoring CTA size. */
+typedef struct {
+    uint32_t returns_per_tile;  /* returns per integration CTA: 8, 16 or 32      */
+    uint32_t warps_per_cta;     /* warps per scoring CTA: 2, 4 or 8              */
+    uint32_t explored;          /* candidate shapes timed so far (of 9)         */
+    uint32_t done;              /* 1 once the shape is final                     */
+    float ms[9];                /* mean tick time per candidate (tile-major), 0 if untimed */
+} af_batch_tuning;
+
+af_status af_batch_create(af_ctx *const *scenes, uint32_t count, af_batch **out);
+af_status af_batch_destroy(af_batch *batch);
+
+/* One tick: items[s] is scene s's scan and points (count items). Asynchronous
+ * on `stream`; the item buffers must stay valid until the tick completes. The
+ * first 18 ticks time the 9 candidate launch shapes twice each (the online
+ * autotuner), later ticks use the fastest; results never depend on the shape. */
+af_status af_batch_tick(af_batch *batch, const af_batch_item *items, void *stream);
+
+/* Fixes the launch shape (tile 8/16/32, warps 2/4/8); (0, 0) returns to tuning. */
+af_status af_batch_set_tuning(af_batch *batch, uint32_t returns_per_tile, uint32_t warps_per_cta);
+
+/* Synchronises and reports the tuner's state and the chosen shape. */
+af_status af_batch_get_tuning(af_batch *batch, af_batch_tuning *out);
+
+/*
  * Kernel timing: when enabled, every launch of the context is bracketed by
  * CUDA events recorded on the launch's own stream. Index 0 = brick
  * allocation, 1 = cube integration, 2 = weight cap + bit view, 3 = scoring.

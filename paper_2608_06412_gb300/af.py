@@ -25,7 +25,8 @@ STATUS = {0: "AF_OK", 1: "AF_ERR_INVALID_ARG", 2: "AF_ERR_CAPACITY", 3: "AF_ERR_
 EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set_tool",
            "af_score", "af_frame_host", "af_sync_status", "af_get_stats", "af_block_count",
            "af_export_blocks", "af_kernel_offsets", "af_arm_offsets", "af_profile_enable",
-           "af_profile_read", "af_integrate_scan_noalloc", "af_last_error")
+           "af_profile_read", "af_integrate_scan_noalloc", "af_batch_create", "af_batch_destroy",
+           "af_batch_tick", "af_batch_set_tuning", "af_batch_get_tuning", "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score")
@@ -65,6 +66,17 @@ class _Profile(C.Structure):
     _fields_ = [("launches", C.c_uint64 * 4), ("ms", C.c_double * 4)]
 
 
+class _BatchItem(C.Structure):
+    _fields_ = [("d_xyz", C.c_void_p), ("n", C.c_uint32), ("pose", C.c_float * 16),
+                ("d_pts", C.c_void_p), ("d_normals", C.c_void_p), ("m", C.c_uint32),
+                ("d_label", C.c_void_p), ("d_best", C.c_void_p)]
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("returns_per_tile", C.c_uint32), ("warps_per_cta", C.c_uint32),
+                ("explored", C.c_uint32), ("done", C.c_uint32), ("ms", C.c_float * 9)]
+
+
 _lib = None
 
 
@@ -96,6 +108,11 @@ def load(build: bool = True) -> C.CDLL:
             "af_profile_read": (C.c_int, [P, C.POINTER(_Profile), C.c_int]),
             "af_integrate_scan_noalloc": (C.c_int, [C.POINTER(_Config), P, U32, P, P, P, P, P,
                                                     P]),
+            "af_batch_create": (C.c_int, [P, U32, C.POINTER(P)]),
+            "af_batch_destroy": (C.c_int, [P]),
+            "af_batch_tick": (C.c_int, [P, P, P]),
+            "af_batch_set_tuning": (C.c_int, [P, U32, U32]),
+            "af_batch_get_tuning": (C.c_int, [P, C.POINTER(_Tuning)]),
             "af_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -347,3 +364,55 @@ def integrate_scan_noalloc(cfg: MapConfig, xyz, pose, box_min, box_dim, vox, fla
     _check(lib.af_integrate_scan_noalloc(C.byref(cc), p, n, _np_ptr(pose), _np_ptr(bmin),
                                          _np_ptr(bdim), _dev_ptr(vox, torch.int64),
                                          _dev_ptr(flags, torch.uint8), _stream_ptr(stream)))
+
+
+class Batch:
+    """Many maps ticked together (af_batch_*): each tick integrates every
+    scene's scan and scores its points, as one CUDA graph launch."""
+
+    def __init__(self, maps):
+        self.maps = list(maps)
+        self._lib = load()
+        arr = (C.c_void_p * len(self.maps))(*[m._h.value for m in self.maps])
+        h = C.c_void_p()
+        _check(self._lib.af_batch_create(arr, len(self.maps), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.af_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tick(self, items, stream=None):
+        """items[s] = (xyz, pose, pts, normals, label, best) for scene s: CUDA
+        tensors as for Map.integrate_scan / Map.score (pts may hold 0 rows).
+        The tensors must stay alive until the tick has run."""
+        import torch
+        arr = (_BatchItem * len(self.maps))()
+        for s, (xyz, pose, pts, nrm, lab, best) in enumerate(items):
+            it = arr[s]
+            it.n = int(xyz.shape[0])
+            it.d_xyz = _dev_ptr(xyz, torch.float32, (3,)).value if it.n else None
+            it.pose[:] = [float(x) for x in np.asarray(pose, np.float32).reshape(16)]
+            it.m = int(pts.shape[0])
+            if it.m:
+                it.d_pts = _dev_ptr(pts, torch.float32, (3,)).value
+                it.d_normals = _dev_ptr(nrm, torch.float32, (3,)).value
+                it.d_label = _dev_ptr(lab, torch.uint8).value
+                it.d_best = _dev_ptr(best, torch.int16).value
+        _check(self._lib.af_batch_tick(self._h, arr, _stream_ptr(stream)))
+
+    def set_tuning(self, returns_per_tile: int, warps_per_cta: int):
+        _check(self._lib.af_batch_set_tuning(self._h, returns_per_tile, warps_per_cta))
+
+    def tuning(self) -> dict:
+        t = _Tuning()
+        _check(self._lib.af_batch_get_tuning(self._h, C.byref(t)))
+        return dict(returns_per_tile=t.returns_per_tile, warps_per_cta=t.warps_per_cta,
+                    explored=t.explored, done=bool(t.done), ms=list(t.ms))

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <vector>
 
+#include "af_ctx.cuh"
 #include "af_internal.cuh"
 
 namespace af {
@@ -28,40 +29,6 @@ cudaError_t launch_export_flags(const MapView& M, uint32_t count, uint8_t* d_fla
 
 using af::MapView;
 
-struct af_ctx {
-  af_config cfg;
-  MapView M;
-  int num_sms = 0;
-  uint32_t frame = 0;
-  cudaStream_t last_stream = nullptr;
-  // scratch
-  float4* d_ret = nullptr;
-  float* d_xyz = nullptr;
-  float* d_pts = nullptr;
-  float* d_nrm = nullptr;
-  uint8_t* d_label = nullptr;
-  int16_t* d_best = nullptr;
-  uint32_t* h_status = nullptr;  // pinned
-  // tool tables
-  bool has_tool = false;
-  af::ToolView T{};
-  float* d_dirs = nullptr;
-  short4* d_runs = nullptr;
-  int2* d_fruns = nullptr;
-  int4* d_dtab = nullptr;
-  short4* d_arm = nullptr;
-  // host counters
-  uint64_t scans = 0, returns_in = 0, points_in = 0;
-  // kernel profiling: CUDA events around each launch on its own stream
-  bool prof_on = false;
-  struct ProfRec {
-    int kernel;
-    cudaEvent_t a, b;
-  };
-  std::vector<ProfRec> prof;
-  std::vector<cudaEvent_t> ev_free;
-  char err[512] = {0};
-};
 
 namespace {
 

@@ -98,10 +98,12 @@ __device__ inline void cube_bricks(const MapView& M, const int rel[3], int b0[3]
 // the return's cube, slots [nbmax, nbmax + N_s) its cleared-band samples. The
 // pose transform is recomputed by every thread of a return (cheap next to an
 // L2 probe); slot 0 also writes the return's world position for k_integrate.
-__global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restrict__ xyz,
-                                                uint32_t n, Pose P, float4* __restrict__ ret,
-                                                uint32_t frame) {
-  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+// All 32 lanes of the warp call this together; `group` tells lanes of
+// different maps apart (0 for a single map), `e` is the thread's slot index
+// within its map's scan (slots past the scan are inactive).
+__device__ void alloc_slot(const MapView& M, const float* __restrict__ xyz, uint32_t n,
+                           const Pose& P, float4* __restrict__ ret, uint32_t frame, uint32_t e,
+                           uint32_t group) {
   const int nbmax = M.nbmax;
   const int per = nbmax + M.ns;
   const uint32_t k = e / per;
@@ -115,8 +117,10 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
     valid = prepare_return(M, P, xyz[3 * k], xyz[3 * k + 1], xyz[3 * k + 2], p, &range, rel);
     if (j == 0) ret[k] = make_float4(p[0], p[1], p[2], valid ? 1.f : 0.f);
   }
-  const unsigned acc = __ballot_sync(0xffffffffu, valid && j == 0);
-  if (lane == 0 && acc) atomicAdd(&M.ctl->returns_accepted, (unsigned long long)__popc(acc));
+  const unsigned same_map = __match_any_sync(0xffffffffu, group);
+  const unsigned acc = __ballot_sync(0xffffffffu, valid && j == 0) & same_map;
+  if (lane == __ffs(same_map) - 1 && acc)
+    atomicAdd(&M.ctl->returns_accepted, (unsigned long long)__popc(acc));
 
   uint64_t key = kEmptyKey;
   bool cube_slot = false;
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
   const unsigned act = __ballot_sync(0xffffffffu, ins);
   uint32_t blk = kNoBlock;
   if (ins) {
-    const unsigned peers = __match_any_sync(act, key);
+    const unsigned peers = __match_any_sync(act, key) & __match_any_sync(act, group);
     const int leader = __ffs(peers) - 1;
     if (lane == leader) {
       uint32_t h, seen;
@@ -159,6 +163,12 @@ __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restric
   // kNoBlock: created by another thread of this launch, resolved (and marked
   // dirty) in k_integrate
   if (k < n && j < nbmax) M.rtab[(size_t)k * nbmax + j] = cube_slot ? blk : kUnused;
+}
+
+__global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restrict__ xyz,
+                                                uint32_t n, Pose P, float4* __restrict__ ret,
+                                                uint32_t frame) {
+  alloc_slot(M, xyz, n, P, ret, frame, blockIdx.x * blockDim.x + threadIdx.x, 0u);
 }
 
 // Approximate square root (MUFU reciprocal square root), relative error well
@@ -179,14 +189,12 @@ struct CubeShape {
   static constexpr int MR = W / 2;
 };
 
-// W = 2m + 1 voxels per cube edge.
-template <int W>
-__global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
-                                                                const float4* __restrict__ ret,
-                                                                uint32_t n, float q0, float q1,
-                                                                float q2, uint32_t frame) {
+// Tile `tile` (returns tile*T .. tile*T + T - 1) of one scan; called by the
+// whole CTA of CubeShape<W>::NT threads. W = 2m + 1 voxels per cube edge.
+template <int W, int T>
+__device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret, uint32_t n,
+                               float q0, float q1, float q2, uint32_t frame, uint32_t tile) {
   using S = CubeShape<W>;
-  constexpr int T = 16;
   constexpr int C = S::C, NT = S::NT, OPT = S::OPT, BA = S::BA, NB = S::NB, MR = S::MR;
   __shared__ float4 s_p[T];        // p, valid flag
   __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
@@ -195,8 +203,9 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
   __shared__ uint32_t s_blk[T][NB];
 
   if (__ldcg(&M.ctl->status) != 0u) return;  // sticky capacity error: skip the scan
+  __syncthreads();  // a previous tile of this CTA may still read the tables
   const int tid = threadIdx.x;
-  const uint32_t r0 = blockIdx.x * T;
+  const uint32_t r0 = tile * T;
   const float q[3] = {q0, q1, q2};
 
   if (tid < T) {
@@ -332,16 +341,26 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
   }
 }
 
-// Weight cap and bit view of every brick touched by the scan.
-__global__ void __launch_bounds__(512) k_bitview(MapView M) {
-  const uint32_t count = __ldcg(&M.ctl->dirty_count);
+// Tiles of 16 returns for the single-map path.
+constexpr int kTile = 16;
+
+template <int W>
+__global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
+                                                                const float4* __restrict__ ret,
+                                                                uint32_t n, float q0, float q1,
+                                                                float q2, uint32_t frame) {
+  integrate_tile<W, kTile>(M, ret, n, q0, q1, q2, frame, blockIdx.x);
+}
+
+// Weight cap and bit view of one dirty brick; called by a CTA of 512 threads
+// (one voxel each).
+__device__ void bitview_brick(const MapView& M, uint32_t blk) {
   const int l = threadIdx.x;
   const int lane = l & 31, wi = l >> 5;
   unsigned char* occ = reinterpret_cast<unsigned char*>(M.occ);
   unsigned char* known = reinterpret_cast<unsigned char*>(M.known);
   const size_t row_bytes = (size_t)M.row_words * 8;
-  for (uint32_t d = blockIdx.x; d < count; d += gridDim.x) {
-    const uint32_t blk = M.dirty[d];
+  {
     const uint64_t key = M.bkey[blk];
     unsigned long long* wp = M.vox + (size_t)blk * kBrickVox + l;
     unsigned long long word = *wp;
@@ -366,6 +385,12 @@ __global__ void __launch_bounds__(512) k_bitview(MapView M) {
       known[at] = (unsigned char)(kb >> (8 * lane));
     }
   }
+}
+
+// Weight cap and bit view of every brick touched by the scan.
+__global__ void __launch_bounds__(512) k_bitview(MapView M) {
+  const uint32_t count = __ldcg(&M.ctl->dirty_count);
+  for (uint32_t d = blockIdx.x; d < count; d += gridDim.x) bitview_brick(M, M.dirty[d]);
 }
 
 // Per-voxel flags of allocated bricks for export: bit0 cleared, bit1
@@ -408,7 +433,7 @@ cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const
 cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], const float4* d_ret,
                         uint32_t frame, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
-  const unsigned grid = (n + 15) / 16;  // k_integrate tiles of 16 returns
+  const unsigned grid = (n + kTile - 1) / kTile;
   switch (2 * M.m + 1) {
 #define AF_CASE(W)                                                                          \
   case W:                                                                                   \
@@ -424,6 +449,93 @@ cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], cons
 
 cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream) {
   k_bitview<<<num_sms * 4, 512, 0, stream>>>(M);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched ticks: the same per-map bodies, driven by persistent grids over
+// the work of every map of the batch (see af_batch.cu).
+// ---------------------------------------------------------------------------
+
+__global__ void k_batch_begin(const BatchHdr* __restrict__ B, const SceneDesc* __restrict__ D) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < B->count;
+       s += gridDim.x * blockDim.x)
+    D[s].M.ctl->dirty_count = 0;
+}
+
+__global__ void __launch_bounds__(256) k_alloc_batch(const BatchHdr* __restrict__ B,
+                                                      const SceneDesc* __restrict__ D) {
+  const uint32_t total = B->total_alloc;
+  const int count = (int)B->count;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // warp-uniform trip count: alloc_slot is a warp-wide call
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
+       base += stride) {
+    const uint32_t e = base + (threadIdx.x & 31u);
+    const bool act = e < total;
+    const int s = act ? scene_of<0>(D, count, e) : 0;
+    const SceneDesc& d = D[s];
+    alloc_slot(d.M, d.xyz, act ? d.n : 0u, d.P, d.ret, d.frame, act ? e - d.alloc_off : 0u,
+               act ? (uint32_t)s : 0xFFFFFFFFu);
+  }
+}
+
+template <int W, int T>
+__global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate_batch(
+    const BatchHdr* __restrict__ B, const SceneDesc* __restrict__ D) {
+  const uint32_t total = B->total_tiles;
+  const int count = (int)B->count;
+  for (uint32_t tg = blockIdx.x; tg < total; tg += gridDim.x) {
+    const int s = scene_of<1>(D, count, tg);
+    const SceneDesc& d = D[s];
+    integrate_tile<W, T>(d.M, d.ret, d.n, d.P.r[0][3], d.P.r[1][3], d.P.r[2][3], d.frame,
+                         tg - d.tile_off);
+  }
+}
+
+// Dirty bricks of all maps as one concatenated list, strided over the CTAs.
+__global__ void __launch_bounds__(512) k_bitview_batch(const BatchHdr* __restrict__ B,
+                                                        const SceneDesc* __restrict__ D) {
+  const uint32_t count = B->count, grid = gridDim.x;
+  uint32_t acc = 0;
+  for (uint32_t s = 0; s < count; ++s) {
+    const MapView& M = D[s].M;
+    const uint32_t cnt = __ldcg(&M.ctl->dirty_count);
+    // this CTA takes the global indices acc + r with (acc + r) % grid == blockIdx.x
+    for (uint32_t r = (blockIdx.x + grid - acc % grid) % grid; r < cnt; r += grid)
+      bitview_brick(M, M.dirty[r]);
+    acc += cnt;
+  }
+}
+
+template <int W, int T>
+int blocks_per_sm_integrate() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_integrate_batch<W, T>, CubeShape<W>::NT, 0);
+  return b > 0 ? b : 1;
+}
+
+cudaError_t launch_batch_integrate(const BatchHdr* B, const SceneDesc* D, uint32_t count, int m,
+                                   int tile, int num_sms, cudaStream_t stream) {
+  k_batch_begin<<<(count + 127) / 128, 128, 0, stream>>>(B, D);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_alloc_batch, 256, 0);
+  k_alloc_batch<<<num_sms * (per > 0 ? per : 1), 256, 0, stream>>>(B, D);
+  switch ((2 * m + 1) * 100 + tile) {
+#define AF_BCASE(W, TT)                                                                \
+  case W * 100 + TT:                                                                   \
+    k_integrate_batch<W, TT><<<num_sms * blocks_per_sm_integrate<W, TT>(),             \
+                               CubeShape<W>::NT, 0, stream>>>(B, D);                   \
+    break;
+#define AF_BW(W) AF_BCASE(W, 8) AF_BCASE(W, 16) AF_BCASE(W, 32)
+    AF_BW(3) AF_BW(5) AF_BW(7) AF_BW(9) AF_BW(11) AF_BW(13) AF_BW(15) AF_BW(17)
+#undef AF_BW
+#undef AF_BCASE
+    default: return cudaErrorInvalidValue;
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bitview_batch, 512, 0);
+  k_bitview_batch<<<num_sms * (per > 0 ? per : 1), 512, 0, stream>>>(B, D);
   return cudaGetLastError();
 }
 

@@ -175,6 +175,48 @@ struct Pose {
   float r[3][4];  // row-major [R | t]
 };
 
+// ---- batched ticks: many maps in one set of persistent launches ----
+
+// One map's share of a batched tick, rewritten every tick. The offsets are
+// exclusive prefix sums over the batch, so a global work index maps to its
+// map by a binary search.
+struct SceneDesc {
+  MapView M;
+  ToolView T;
+  Pose P;
+  const float* xyz;     // n returns, sensor frame
+  float4* ret;          // per-return scratch of the map's context
+  const float* pts;     // m points and normals
+  const float* nrm;
+  uint8_t* label;
+  int16_t* best;
+  uint32_t n, m, frame;
+  uint32_t alloc_off;   // allocation threads: n * (nbmax + N_s)
+  uint32_t tile_off;    // integration tiles: ceil(n / returns per tile)
+  uint32_t pt_off;      // scored points: m
+};
+
+struct BatchHdr {
+  uint32_t count;
+  uint32_t total_alloc, total_tiles, total_points;
+};
+
+// Largest s with off_F(s) <= x (F: 0 allocation, 1 tiles, 2 points). Maps
+// with no work share their successor's offset, so the one found owns x.
+template <int F>
+__device__ inline int scene_of(const SceneDesc* __restrict__ D, int count, uint32_t x) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const uint32_t off = F == 0 ? D[mid].alloc_off : (F == 1 ? D[mid].tile_off : D[mid].pt_off);
+    if (off <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // Transform, validate, voxel-index one return. Returns false if dropped.
 __device__ inline bool prepare_return(const MapView& M, const Pose& P, float sx, float sy,
                                       float sz, float p[3], float* range, int rel[3]) {

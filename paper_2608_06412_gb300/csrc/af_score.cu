@@ -212,14 +212,11 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
   return make_int2(bscore, best);
 }
 
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
-    k_score(MapView M, ToolView T, const float* __restrict__ pts, const float* __restrict__ nrm,
-            uint32_t m, uint8_t* __restrict__ label, int16_t* __restrict__ best_out) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t pi = blockIdx.x * WARPS + (threadIdx.x >> 5);
-  if (pi >= m) return;  // whole warp
-
+// Scores point pi with the whole warp (all 32 lanes call this together).
+__device__ void score_point(const MapView& M, const ToolView& T, const float* __restrict__ pts,
+                            const float* __restrict__ nrm, uint32_t pi,
+                            uint8_t* __restrict__ label, int16_t* __restrict__ best_out,
+                            int lane) {
   const float s0 = pts[3 * pi], s1 = pts[3 * pi + 1], s2 = pts[3 * pi + 2];
   const float n0 = nrm[3 * pi], n1 = nrm[3 * pi + 1], n2 = nrm[3 * pi + 2];
 
@@ -275,6 +272,15 @@ __global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
   }
 }
 
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
+    k_score(MapView M, ToolView T, const float* __restrict__ pts, const float* __restrict__ nrm,
+            uint32_t m, uint8_t* __restrict__ label, int16_t* __restrict__ best_out) {
+  const uint32_t pi = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  if (pi >= m) return;  // whole warp
+  score_point(M, T, pts, nrm, pi, label, best_out, threadIdx.x & 31);
+}
+
 cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts,
                          const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
                          cudaStream_t stream) {
@@ -283,6 +289,41 @@ cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts
   k_score<WARPS><<<(m + WARPS - 1) / WARPS, WARPS * 32, 0, stream>>>(M, T, d_pts, d_nrm, m,
                                                                       d_label, d_best);
   return cudaGetLastError();
+}
+
+
+// Batched ticks: every point of every map of the batch, one warp per point,
+// persistent grid (see af_batch.cu).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
+    k_score_batch(const BatchHdr* __restrict__ B, const SceneDesc* __restrict__ D) {
+  const uint32_t total = B->total_points;
+  const int count = (int)B->count;
+  const uint32_t nw = gridDim.x * WARPS;
+  for (uint32_t pg = blockIdx.x * WARPS + (threadIdx.x >> 5); pg < total; pg += nw) {
+    const int s = scene_of<2>(D, count, pg);
+    const SceneDesc& d = D[s];
+    score_point(d.M, d.T, d.pts, d.nrm, pg - d.pt_off, d.label, d.best, threadIdx.x & 31);
+  }
+}
+
+template <int WARPS>
+static cudaError_t launch_score_batch_w(const BatchHdr* B, const SceneDesc* D, int num_sms,
+                                        cudaStream_t stream) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score_batch<WARPS>, WARPS * 32, 0);
+  k_score_batch<WARPS><<<num_sms * (per > 0 ? per : 1), WARPS * 32, 0, stream>>>(B, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_score_batch(const BatchHdr* B, const SceneDesc* D, int warps, int num_sms,
+                               cudaStream_t stream) {
+  switch (warps) {
+    case 2: return launch_score_batch_w<2>(B, D, num_sms, stream);
+    case 4: return launch_score_batch_w<4>(B, D, num_sms, stream);
+    case 8: return launch_score_batch_w<8>(B, D, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace af

@@ -93,3 +93,75 @@ def pine_frame(W: Workload, f: int):
 #: and points per call.
 BENCH_CAPS = dict(hash_capacity=1 << 19, pool_blocks=1 << 18, max_returns=1 << 16,
                   max_points=1 << 16)
+
+
+#: The three tools of the batched workload: cylinder radius r and length L,
+#: corridor length; the corridor radius is r + 1 cm and r_s = r, as for the
+#: 4 cm tool of the single-scene workloads.
+BATCH_TOOLS = [dict(radius=0.03, length=0.15, self_excl=0.03, corr_radius=0.04,
+                    corr_length=0.5, cos_theta_max=0.0, n_c=5, strict=0),
+               dict(radius=0.04, length=0.25, self_excl=0.04, corr_radius=0.05,
+                    corr_length=1.0, cos_theta_max=0.0, n_c=5, strict=0),
+               dict(radius=0.06, length=0.40, self_excl=0.06, corr_radius=0.07,
+                    corr_length=1.5, cos_theta_max=0.0, n_c=5, strict=0)]
+
+
+def clutter_scene(seed: int) -> synth.Scene:
+    """Boxes (5-40 cm) and spheres (r 5-25 cm) scattered over 3 x 3 x 2 m."""
+    g = synth.rng(seed, 41)
+    groups = []
+    for _ in range(20):
+        c = g.uniform([-1.5, -1.5, 0.0], [1.5, 1.5, 2.0])
+        h = g.uniform(0.025, 0.2, 3)
+        groups.append(synth.Group(a=c, b=c, radius=float(np.linalg.norm(h)) + 1e-3,
+                                  boxes=np.array([[*(c - h), *(c + h)]])))
+    for _ in range(20):
+        c = g.uniform([-1.5, -1.5, 0.0], [1.5, 1.5, 2.0])
+        r = float(g.uniform(0.05, 0.25))
+        groups.append(synth.Group(a=c, b=c, radius=r + 1e-3, spheres=np.array([[*c, r]])))
+    lo, hi = synth._bounds(groups)
+    return synth.Scene(groups, lo, hi)
+
+
+def forest_scene(seed: int, count: int) -> synth.Scene:
+    """`count` procedural pines within 2.5 m of the origin."""
+    g = synth.rng(seed, 43)
+    groups = []
+    for k in range(count):
+        off = np.zeros(3) if k == 0 else np.r_[g.uniform(-2.5, 2.5, 2), 0.0]
+        for gr in synth.pine_scene(seed * 100 + k).groups:
+            sp = gr.spheres.copy()
+            if len(sp):
+                sp[:, :3] += off
+            cy = gr.cylinders.copy()
+            if len(cy):
+                cy[:, :3] += off
+                cy[:, 3:6] += off
+            groups.append(synth.Group(a=gr.a + off, b=gr.b + off, radius=gr.radius,
+                                      spheres=sp, boxes=gr.boxes, cylinders=cy))
+    lo, hi = synth._bounds(groups)
+    return synth.Scene(groups, lo, hi)
+
+
+def batch_scenes(count: int = 64, seed: int = 3, n_lo: int = 2000, n_hi: int = 60000):
+    """Scenes of the batched workload: 1-4 pines or box/sphere clutter,
+    returns per frame ~ U[n_lo, n_hi], one of three tools, K in {16, 64, 128};
+    each scene orbited by its own Mid-360-like sensor."""
+    g = synth.rng(seed, 51)
+    out = []
+    for s in range(count):
+        p = dict(synth.PINE_STREAM)
+        kind = int(g.integers(0, 5))           # 0 clutter, 1-4 pines
+        sc = clutter_scene(seed * 1000 + s) if kind == 0 else forest_scene(seed * 1000 + s, kind)
+        p["tool"] = dict(BATCH_TOOLS[int(g.integers(0, 3))])
+        p["K"] = int(g.choice([16, 64, 128]))
+        p["n_returns"] = int(g.integers(n_lo, n_hi + 1))
+        p["seed"] = seed * 1000 + s
+        p["orbit_radius"] = 3.0 if kind <= 1 else 5.5
+        p["name"] = f"batch_scene_{s}"
+        r = p["orbit_radius"] + 0.5
+        lo = np.minimum(sc.lo, [-r, -r, 0.0])
+        hi = np.maximum(sc.hi, [r, r, p["orbit_height"]])
+        dmin, db = synth.domain_bricks(lo, hi, p["v"], margin=0.5)
+        out.append(Workload(p["name"], p, sc, dmin, db, synth.fibonacci_dirs(2 * p["K"])))
+    return out
