@@ -47,6 +47,9 @@ def _args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="the batched form (many scenes per tick) instead of the pine stream")
+    ap.add_argument("--scenes", type=int, default=64)
     return ap.parse_args()
 
 
@@ -440,9 +443,108 @@ def run_ours(args, W, ws, rank, local):
     }
 
 
+def run_batched(args, local):
+    """Batched form: 64 scenes of uneven size (1-4 pines or clutter, 2k-60k
+    returns per frame, three tools, K in {16, 64, 128}) ticked together, one
+    graph launch per tick; the same frames then go through the per-scene path
+    (af_integrate_scan + af_score per scene) for comparison. Each scene cycles
+    through 3 pre-generated frames."""
+    import torch
+    from paper_2608_06412_gb300 import af, workload
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    S = workload.batch_scenes(args.scenes)
+    nfr = 3
+    frames = [[workload.pine_frame(W, f) for f in range(nfr)] for W in S]
+    d_in = [[(torch.from_numpy(fr.pts).to(dev), fr.pose, torch.from_numpy(p).to(dev),
+              torch.from_numpy(n).to(dev)) for fr, p, n in fs] for fs in frames]
+    outs = [(torch.empty(max(len(fs[f][1]) for f in range(nfr)), dtype=torch.uint8, device=dev),
+             torch.empty(max(len(fs[f][1]) for f in range(nfr)), dtype=torch.int16, device=dev))
+            for fs in frames]
+    caps = dict(hash_capacity=1 << 18, pool_blocks=1 << 16, max_returns=1 << 16,
+                max_points=1 << 16)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    warm, steps = max(args.warmup, 20), (args.steps if args.steps <= 100 else 30)
+
+    def items(t):
+        out = []
+        for s in range(len(S)):
+            xyz, pose, p, n = d_in[s][t % nfr]
+            out.append((xyz, pose, p, n, outs[s][0][:len(p)], outs[s][1][:len(p)]))
+        return out
+
+    def run(batched: bool):
+        maps = [af.Map(W.af_config(**caps)) for W in S]
+        for W, m in zip(S, maps):
+            m.set_tool(W.af_tool(), W.dirs)
+        batch = af.Batch(maps) if batched else None
+
+        def tick(t):
+            it = items(t)
+            if batched:
+                batch.tick(it)
+            else:
+                for m, (xyz, pose, p, n, lab, best) in zip(maps, it):
+                    m.integrate_scan(xyz, pose)
+                    m.score(p, n, lab, best)
+            return it
+
+        for t in range(warm):
+            tick(t)
+        torch.cuda.synchronize()
+        t0 = sum(m.stats()["tests"] for m in maps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            it = tick(warm + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        tests = sum(m.stats()["tests"] for m in maps) - t0
+        labels = [np.concatenate([x[4].cpu().numpy(), x[5].cpu().numpy().view(np.uint8)])
+                  for x in it]
+        tuning = batch.tuning() if batched else None
+        if batch:
+            batch.close()
+        for m in maps:
+            m.close()
+        return ms, tests, labels, tuning
+
+    msb, testsb, labb, tuning = run(True)
+    msp, testsp, labp, _ = run(False)
+    agree = float(np.mean([np.array_equal(a, b) for a, b in zip(labb, labp)]))
+    returns = sum(len(frames[s][(warm + i) % nfr][0].pts) for s in range(len(S))
+                  for i in range(steps))
+    return {
+        "metric": "batched point x orientation tests/s", "value": testsb / (sum(msb) / 1e3),
+        "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": sum(msb) / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+        "config": {"workload": f"batched_{len(S)}_scenes_2k_60k_returns",
+                   "tools": "r 3/4/6 cm, L 15/25/40 cm, corridor 0.5/1.0/1.5 m",
+                   "K": "16/64/128", "l2": "flushed between steps (256 MiB write)"},
+        "latency_ms": {"p50": float(np.percentile(msb, 50)), "p99": float(np.percentile(msb, 99))},
+        "returns_per_s": returns / (sum(msb) / 1e3),
+        "tuning": tuning,
+        "per_scene_path": {"value": testsp / (sum(msp) / 1e3), "ms_per_step": sum(msp) / steps,
+                           "latency_ms": {"p50": float(np.percentile(msp, 50)),
+                                          "p99": float(np.percentile(msp, 99))}},
+        "speedup_vs_per_scene": (sum(msp) / steps) / (sum(msb) / steps),
+        "label_agreement": agree,
+        "tests_equal": testsb == testsp,
+    }
+
+
 def main():
     args = _args()
     ws, rank, local = _dist()
+    if args.batched:
+        out = run_batched(args, local)
+        print(json.dumps(out), flush=True)
+        return
     if ws > 1:
         import torch.distributed as dist
         backend = "nccl" if args.impl == "ours" else "gloo"
