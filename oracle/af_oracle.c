@@ -55,6 +55,26 @@
  *    window, Sec. 3.3): a return whose cube leaves the box is dropped, and
  *    cleared-band samples outside the box are skipped. Voxels outside the
  *    box read w = 0, not cleared.
+ *
+ * The differentiable form (soft clearance, not in the paper: a smooth
+ * companion of the Sec. 3.4 tool / corridor test) takes these readings:
+ *  - SDF of a voxel = S / (w 2^20) divided in double and rounded to single
+ *    precision; tau where w = 0 or outside the box (an unobserved voxel reads
+ *    as far from any surface).
+ *  - SDF(x) = trilinear interpolation over voxel centres: with
+ *    g = x / v - 1/2, the cell is floor(g) and the weights g - floor(g).
+ *  - Samples along the approach axis at a_j = h + j v, j = 1..J,
+ *    J = floor((L + L_c) / v); a sample with j v <= r_s is skipped (the
+ *    self-exclusion of Sec. 3.4 in the tool's own frame); its margin is r
+ *    when j v <= L (tool) and r_corr beyond (corridor).
+ *  - phi_j = SDF(x_j) - margin_j; C = -tau_s log sum_j exp(-phi_j / tau_s).
+ *  - Direction u = q / |q|, q = u0 + alpha t1 + beta t2, (t1, t2) the
+ *    orthonormal tangent basis of u0 of Duff et al. 2017.
+ *  - The cell of every sample is an integer decided by floating point, so
+ *    with fp32_cells it is decided as the kernel decides it: in single
+ *    precision in the fixed order of pair_frame_f / sample_cell_f below,
+ *    relative to the voxel of the point. The weights, SDF, softmin and
+ *    gradient are double. Without fp32_cells the cell is floor(g) in double.
  */
 #include "af_oracle.h"
 
@@ -472,4 +492,251 @@ void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G, c
     free(ntool);
     free(ncorr);
     free(arm);
+}
+
+
+/* ------------------------------------------------------------------------- */
+/* Soft clearance and its gradient (the differentiable form).                */
+/* ------------------------------------------------------------------------- */
+
+/* TSDF value of a voxel as single precision data: S / (w 2^20), or tau when
+ * the voxel is unobserved or outside the box. */
+static double sdf_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz) {
+    uint64_t S;
+    uint32_t w;
+    int32_t cl;
+    if (!in_domain(&m->cfg, ix, iy, iz)) return (double)m->cfg.tau;
+    or_get_voxel(m, ix, iy, iz, &S, &w, &cl);
+    if (w == 0) return (double)m->cfg.tau;
+    return (double)(float)((double)S / ((double)w * 1048576.0));
+}
+
+/* Trilinear SDF in the cell whose low corner is `cell`, at fractional
+ * position f (normally in [0, 1]); grad receives d SDF / d g (per voxel),
+ * each component a weighted sum of corner differences along its axis. */
+static double sdf_cell(const or_map *m, const int32_t cell[3], const double f[3], double grad[3]) {
+    double D[2][2][2]; /* [dz][dy][dx] */
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                D[dz][dy][dx] = sdf_voxel(m, cell[0] + dx, cell[1] + dy, cell[2] + dz);
+    const double w[3][2] = {{1.0 - f[0], f[0]}, {1.0 - f[1], f[1]}, {1.0 - f[2], f[2]}};
+    double val = 0.0;
+    grad[0] = grad[1] = grad[2] = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            grad[0] += (D[b][a][1] - D[b][a][0]) * w[1][a] * w[2][b];
+            grad[1] += (D[b][1][a] - D[b][0][a]) * w[0][a] * w[2][b];
+            grad[2] += (D[1][b][a] - D[0][b][a]) * w[0][a] * w[1][b];
+            for (int c = 0; c < 2; ++c) val += D[c][b][a] * w[0][a] * w[1][b] * w[2][c];
+        }
+    return val;
+}
+
+/* Orthonormal tangent basis (t1, t2) of the unit vector n (Duff et al. 2017,
+ * "Building an orthonormal basis, revisited"), in double ... */
+static void onb_d(const double n[3], double t1[3], double t2[3]) {
+    const double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+    const double a = -1.0 / (sg + n[2]);
+    const double b = n[0] * n[1] * a;
+    t1[0] = 1.0 + sg * n[0] * n[0] * a;
+    t1[1] = sg * b;
+    t1[2] = -sg * n[0];
+    t2[0] = b;
+    t2[1] = sg + n[1] * n[1] * a;
+    t2[2] = -n[1];
+}
+
+/* ... and in single precision, one rounded operation at a time. */
+static void onb_f(const float n[3], float t1[3], float t2[3]) {
+    const float sg = n[2] >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + n[2]);
+    const float b = (n[0] * n[1]) * a;
+    t1[0] = 1.0f + ((sg * n[0]) * n[0]) * a;
+    t1[1] = sg * b;
+    t1[2] = -(sg * n[0]);
+    t2[0] = b;
+    t2[1] = sg + (n[1] * n[1]) * a;
+    t2[2] = -n[1];
+}
+
+void or_soft_seed(const float *normals, int64_t npts, const float *table, int32_t K, float *u0) {
+    for (int64_t p = 0; p < npts; ++p) {
+        const float *n = normals + 3 * p;
+        float t1[3], t2[3];
+        onb_f(n, t1, t2);
+        for (int32_t k = 0; k < K; ++k) {
+            const float *e = table + 3 * k;
+            float *o = u0 + 3 * (p * K + k);
+            for (int i = 0; i < 3; ++i) o[i] = (e[0] * t1[i] + e[1] * t2[i]) + e[2] * n[i];
+        }
+    }
+}
+
+/* The single-precision frame of one (point, direction) pair: the cell I of
+ * the point on the sample grid (g = x / v - 1/2), the point's offset r in it,
+ * the direction u and the standoff in voxels h / v. Sample j then sits at
+ * g = I + r + (h / v + j) u. */
+typedef struct {
+    float I[3], r[3], w[3], e;
+} pair_frame;
+
+static void pair_frame_f(float v, const float s[3], const float u0[3], float al, float be,
+                         float h, pair_frame *F) {
+    float t1[3], t2[3], q[3];
+    onb_f(u0, t1, t2);
+    for (int i = 0; i < 3; ++i) q[i] = (u0[i] + al * t1[i]) + be * t2[i];
+    const float nq = sqrtf((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]);
+    for (int i = 0; i < 3; ++i) {
+        const float o = s[i] / v - 0.5f;
+        F->I[i] = floorf(o);
+        F->r[i] = o - F->I[i];
+        F->w[i] = q[i] / nq;
+    }
+    F->e = h / v;
+}
+
+/* Cell of sample j, decided in single precision; 0 if it is not a usable
+ * integer (then the sample is treated as outside the box). */
+static int sample_cell_f(const pair_frame *F, int j, int32_t cell[3]) {
+    const float t = F->e + (float)j;
+    for (int i = 0; i < 3; ++i) {
+        const float l = F->r[i] + t * F->w[i];
+        if (!(fabsf(l) < 1.0e7f)) return 0;
+        cell[i] = (int32_t)F->I[i] + (int32_t)floorf(l);
+    }
+    return 1;
+}
+
+static int all_finite(const float *x, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(x[i])) return 0;
+    return 1;
+}
+
+/* Soft clearance of one pair and its gradient, in double. */
+static double soft_pair(const or_map *m, const or_tool *t, const float s[3], const float u0[3],
+                        float al, float be, float h, double tau_s, int fp32_cells,
+                        double grad[3]) {
+    const float vf = m->cfg.v;
+    const double v = (double)vf;
+    const int J = (int)floorf((t->length + t->corr_length) / vf);
+    if (!all_finite(s, 3) || !all_finite(u0, 3) || !isfinite(al) || !isfinite(be) ||
+        !isfinite(h)) {
+        grad[0] = grad[1] = grad[2] = NAN;
+        return NAN;
+    }
+    /* direction and its derivatives */
+    double n0[3], t1[3], t2[3], q[3];
+    for (int i = 0; i < 3; ++i) n0[i] = (double)u0[i];
+    onb_d(n0, t1, t2);
+    double nq = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        q[i] = n0[i] + (double)al * t1[i] + (double)be * t2[i];
+        nq += q[i] * q[i];
+    }
+    nq = sqrt(nq);
+    double u[3], du_a[3], du_b[3];
+    for (int i = 0; i < 3; ++i) u[i] = q[i] / nq;
+    const double ut1 = u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2];
+    const double ut2 = u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2];
+    for (int i = 0; i < 3; ++i) {
+        du_a[i] = (t1[i] - u[i] * ut1) / nq;
+        du_b[i] = (t2[i] - u[i] * ut2) / nq;
+    }
+    pair_frame F;
+    pair_frame_f(vf, s, u0, al, be, h, &F);
+
+    double *phi = (double *)malloc(sizeof(double) * 4 * (size_t)(J > 0 ? J : 1));
+    double *dpa = phi + (J > 0 ? J : 1), *dpb = dpa + (J > 0 ? J : 1), *dph = dpb + (J > 0 ? J : 1);
+    int ns = 0;
+    double mn = INFINITY;
+    for (int j = 1; j <= J; ++j) {
+        const float aj = (float)j * vf;
+        if (!(aj > t->self_excl)) continue;
+        const double margin = aj <= t->length ? (double)t->radius : (double)t->corr_radius;
+        const double dist = (double)h + (double)j * v; /* a_j */
+        double g[3], f[3], G[3];
+        int32_t cell[3];
+        for (int i = 0; i < 3; ++i) g[i] = (double)s[i] / v - 0.5 + dist * u[i] / v;
+        int ok = 1;
+        if (fp32_cells) {
+            ok = sample_cell_f(&F, j, cell);
+        } else {
+            for (int i = 0; i < 3; ++i) {
+                if (!(fabs(g[i]) < 1.0e9)) ok = 0;
+                else cell[i] = (int32_t)floor(g[i]);
+            }
+        }
+        double D;
+        if (ok) {
+            for (int i = 0; i < 3; ++i) f[i] = g[i] - (double)cell[i];
+            D = sdf_cell(m, cell, f, G);
+        } else {
+            D = (double)m->cfg.tau;
+            G[0] = G[1] = G[2] = 0.0;
+        }
+        phi[ns] = D - margin;
+        /* x_j = s + a_j u: d x / d h = u, d x / d alpha = a_j du/dalpha;
+         * d SDF / d x = G / v */
+        dph[ns] = (G[0] * u[0] + G[1] * u[1] + G[2] * u[2]) / v;
+        dpa[ns] = dist * (G[0] * du_a[0] + G[1] * du_a[1] + G[2] * du_a[2]) / v;
+        dpb[ns] = dist * (G[0] * du_b[0] + G[1] * du_b[1] + G[2] * du_b[2]) / v;
+        if (phi[ns] < mn) mn = phi[ns];
+        ++ns;
+    }
+    double C;
+    if (ns == 0) {
+        C = NAN;
+        grad[0] = grad[1] = grad[2] = NAN;
+    } else {
+        /* softmin; d C / d phi_j = exp(-phi_j / tau_s) / sum_i exp(-phi_i / tau_s) */
+        double Z = 0.0, ga = 0.0, gb = 0.0, gh = 0.0;
+        for (int k = 0; k < ns; ++k) Z += exp(-(phi[k] - mn) / tau_s);
+        for (int k = 0; k < ns; ++k) {
+            const double wk = exp(-(phi[k] - mn) / tau_s) / Z;
+            ga += wk * dpa[k];
+            gb += wk * dpb[k];
+            gh += wk * dph[k];
+        }
+        C = mn - tau_s * log(Z);
+        grad[0] = ga;
+        grad[1] = gb;
+        grad[2] = gh;
+    }
+    free(phi);
+    return C;
+}
+
+void or_soft_clearance(const or_map *m, const or_tool *t, const float *pts, uint32_t per_point,
+                       const float *u0, const float *alpha, const float *beta, const float *h,
+                       int64_t npairs, double tau_s, int fp32_cells, double *c,
+                       double *g_alpha, double *g_beta, double *g_h) {
+    for (int64_t i = 0; i < npairs; ++i) {
+        double g[3];
+        c[i] = soft_pair(m, t, pts + 3 * (i / per_point), u0 + 3 * i, alpha[i], beta[i], h[i],
+                         tau_s, fp32_cells, g);
+        if (g_alpha) g_alpha[i] = g[0];
+        if (g_beta) g_beta[i] = g[1];
+        if (g_h) g_h[i] = g[2];
+    }
+}
+
+void or_soft_refine(const or_map *m, const or_tool *t, const float *pts, uint32_t per_point,
+                    const float *u0, float *alpha, float *beta, float *h, int64_t npairs,
+                    double tau_s, int steps, float lr_dir, float lr_h, float h_max, double *c) {
+    for (int64_t i = 0; i < npairs; ++i) {
+        const float *s = pts + 3 * (i / per_point);
+        double g[3];
+        for (int k = 0; k < steps; ++k) {
+            soft_pair(m, t, s, u0 + 3 * i, alpha[i], beta[i], h[i], tau_s, 1, g);
+            /* gradient ascent on C, standoff kept in [0, h_max] */
+            alpha[i] = (float)((double)alpha[i] + (double)lr_dir * g[0]);
+            beta[i] = (float)((double)beta[i] + (double)lr_dir * g[1]);
+            double hn = (double)h[i] + (double)lr_h * g[2];
+            hn = hn < 0.0 ? 0.0 : (hn > (double)h_max ? (double)h_max : hn);
+            h[i] = (float)hn;
+        }
+        c[i] = soft_pair(m, t, s, u0 + 3 * i, alpha[i], beta[i], h[i], tau_s, 1, g);
+    }
 }

@@ -70,6 +70,17 @@ def fibonacci_dirs(G: int) -> np.ndarray:
     return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1).astype(np.float32)
 
 
+def fibonacci_hemisphere(K: int, cos_max: float = 0.0) -> np.ndarray:
+    """K unit vectors on the Fibonacci cap z > cos_max around +z:
+    z_i = 1 - (i + 1/2)(1 - cos_max)/K, phi_i = i * pi * (3 - sqrt 5).
+    Computed in double, rounded to float32."""
+    i = np.arange(K, dtype=np.float64)
+    z = 1.0 - (i + 0.5) * (1.0 - cos_max) / K
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1).astype(np.float32)
+
+
 def halton(index: np.ndarray, base: int) -> np.ndarray:
     """Radical inverse of integer `index` in `base` (van der Corput)."""
     index = np.asarray(index, dtype=np.int64).copy()
