@@ -253,15 +253,92 @@ af_status af_batch_set_tuning(af_batch *batch, uint32_t returns_per_tile, uint32
 af_status af_batch_get_tuning(af_batch *batch, af_batch_tuning *out);
 
 /*
+ * The differentiable form: soft clearance. Not in the paper -- a smooth
+ * companion of the tool / corridor test of Sec. 3.4 whose gradient refines an
+ * approach direction and a standoff continuously.
+ *
+ * A pair is a surface point s and an approach direction. Pair i belongs to
+ * point i / per_point (points' pairs adjacent; the last point may have
+ * fewer). Its direction is u = (u0 + alpha t1 + beta t2) / |u0 + alpha t1 +
+ * beta t2|, (t1, t2) the orthonormal tangent basis of the unit vector u0
+ * (Duff et al. 2017), and its tool starts at standoff h along u. The axis is
+ * sampled at a_j = h + j v, j = 1..floor((L + L_c) / v), skipping j v <= r_s
+ * (the tool's self-exclusion); sample j has margin r while j v <= L, r_corr
+ * beyond (the af_tool set on the context). With SDF the trilinear
+ * interpolation over voxel centres of the TSDF S / (w 2^20) (Sec. 3.2; tau
+ * where w = 0 or outside the map box), phi_j = SDF(x_j) - margin_j and
+ *     C = -tau_s log sum_j exp(-phi_j / tau_s)   (softmin; C <= min_j phi_j).
+ * C > 0 means every axis sample clears its margin. Where every sample reads
+ * tau the gradient is exactly zero (truncation).
+ *
+ * Buffers are device memory owned by the caller; pairs are float32: d_pts
+ * (points x 3), d_u0 (n x 3, unit), d_alpha, d_beta, d_h, outputs (n).
+ * The first call builds single-precision views of the map (one float per
+ * voxel of the box plus 32 bytes per interpolation cell: 36 bytes per voxel
+ * of the box, allocated once, AF_ERR_CAPACITY if that fails) and later calls
+ * rebuild them when scans were integrated since; the map's updates must be
+ * ordered before the call on `stream`. AF_ERR_STATE without a tool or when
+ * no axis sample lies beyond r_s. Asynchronous on `stream`. Non-finite
+ * inputs give NaN outputs.
+ */
+typedef struct {
+    uint32_t steps;  /* ascent steps                                      */
+    float lr_dir;    /* alpha, beta += lr_dir * dC/d(alpha, beta)         */
+    float lr_h;      /* h += lr_h * dC/dh, then h kept in [0, h_max]      */
+    float h_max;
+} af_refine;
+
+/* Seeds: u0[p*K + k] = table_k rotated into the tangent frame of normal p
+ * (table +z -> the normal): h_table is K x 3 host floats (a hemisphere set
+ * of K approach orientations around +z), d_normals m x 3 unit normals.
+ * Synchronises `stream` before returning (the table buffer is reused). */
+af_status af_soft_seed(af_ctx *ctx, const float *d_normals, uint32_t m, const float *h_table,
+                       uint32_t K, float *d_u0, void *stream);
+
+/* C of n pairs -> d_c; if d_cmin is given, also the hard clearance
+ * min_j phi_j of each pair (> 0: every axis sample clears its margin). */
+af_status af_soft_clearance(af_ctx *ctx, const float *d_pts, uint32_t per_point,
+                            const float *d_u0, const float *d_alpha, const float *d_beta,
+                            const float *d_h, uint64_t n, float tau_s, float *d_c,
+                            float *d_cmin, void *stream);
+
+/* Adjoint: with g = d_gc[i] (1 if d_gc is NULL), writes g dC/dalpha,
+ * g dC/dbeta, g dC/dh (any of d_ga, d_gb, d_gh, d_c may be NULL to skip it;
+ * d_c receives C). Recomputes every sample from the map: nothing from the
+ * forward call is kept. */
+af_status af_soft_clearance_adjoint(af_ctx *ctx, const float *d_pts, uint32_t per_point,
+                                    const float *d_u0, const float *d_alpha, const float *d_beta,
+                                    const float *d_h, uint64_t n, float tau_s, const float *d_gc,
+                                    float *d_c, float *d_ga, float *d_gb, float *d_gh,
+                                    void *stream);
+
+/* R->steps gradient-ascent steps on C for every pair in one launch (alpha,
+ * beta, h updated in place), then C (and, if d_cmin is given, the hard
+ * clearance) at the final state. */
+af_status af_soft_refine(af_ctx *ctx, const float *d_pts, uint32_t per_point, const float *d_u0,
+                         float *d_alpha, float *d_beta, float *d_h, uint64_t n, float tau_s,
+                         const af_refine *R, float *d_c, float *d_cmin, void *stream);
+
+/* Per point of n pairs (per_point each, as above): the index within its
+ * pairs of the largest d_c (lowest index on ties, -1 if all are NaN) ->
+ * d_best_k, that value -> d_best_c, and, if d_best_u0 is given, that pair's
+ * base direction from d_u0 (NaN for -1). Outputs may be NULL to skip. Needs
+ * no map. */
+af_status af_soft_best(af_ctx *ctx, const float *d_c, uint64_t n, uint32_t per_point,
+                       const float *d_u0, int32_t *d_best_k, float *d_best_c, float *d_best_u0,
+                       void *stream);
+
+/*
  * Kernel timing: when enabled, every launch of the context is bracketed by
  * CUDA events recorded on the launch's own stream. Index 0 = brick
- * allocation, 1 = cube integration, 2 = weight cap + bit view, 3 = scoring.
+ * allocation, 1 = cube integration, 2 = weight cap + bit view, 3 = scoring,
+ * 4 = SDF view build, 5 = soft clearance, 6 = its adjoint, 7 = refinement.
  * af_profile_read synchronises, sums the elapsed times of the recorded
  * launches (milliseconds) and, if `reset`, forgets them.
  */
 typedef struct {
-    uint64_t launches[4];
-    double ms[4];
+    uint64_t launches[8];
+    double ms[8];
 } af_profile;
 af_status af_profile_enable(af_ctx *ctx, int enable);
 af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);

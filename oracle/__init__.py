@@ -93,11 +93,11 @@ def _load():
         lib.or_score.argtypes = [P, C.POINTER(_Tool), P, C.c_int32, P, P, C.c_int64,
                                  P, P, P]
         lib.or_soft_clearance.argtypes = [P, C.POINTER(_Tool), P, C.c_uint32, P, P, P, P,
-                                          C.c_int64, C.c_double, C.c_int, P, P, P, P]
+                                          C.c_int64, C.c_double, C.c_int, P, P, P, P, P]
         lib.or_soft_seed.argtypes = [P, C.c_int64, P, C.c_int32, P]
         lib.or_soft_refine.argtypes = [P, C.POINTER(_Tool), P, C.c_uint32, P, P, P, P,
                                        C.c_int64, C.c_double, C.c_int, C.c_float, C.c_float,
-                                       C.c_float, P]
+                                       C.c_float, P, P]
         _lib = lib
     return _lib
 
@@ -235,38 +235,40 @@ class Map:
     def soft_clearance(self, tool: Tool, pts: np.ndarray, per_point: int, u0: np.ndarray,
                        alpha: np.ndarray, beta: np.ndarray, h: np.ndarray,
                        tau_s: float = 0.005, fp32_cells: bool = True):
-        """Soft clearance C and dC/d(alpha, beta, h) of every pair, float64.
-        Pair i belongs to point i // per_point."""
+        """Soft clearance C, dC/d(alpha, beta, h) (n x 3) and the hard
+        clearance min_j phi_j of every pair, float64. Pair i belongs to point
+        i // per_point."""
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
         u0 = np.ascontiguousarray(u0, np.float32).reshape(-1, 3)
         n = len(u0)
         a, b, hh = (np.ascontiguousarray(x, np.float32).reshape(n) for x in (alpha, beta, h))
         if per_point < 1 or len(pts) * per_point < n:
             raise ValueError("need per_point >= 1 and a point for every pair")
-        c = np.zeros(n)
+        c, cmin = np.zeros(n), np.zeros(n)
         ga, gb, gh = np.zeros(n), np.zeros(n), np.zeros(n)
         tc = tool._c()
         self._lib.or_soft_clearance(self._h, C.byref(tc), _ptr(pts), per_point, _ptr(u0),
                                     _ptr(a), _ptr(b), _ptr(hh), n, tau_s, int(fp32_cells),
-                                    _ptr(c), _ptr(ga), _ptr(gb), _ptr(gh))
+                                    _ptr(c), _ptr(ga), _ptr(gb), _ptr(gh), _ptr(cmin))
+        self.last_cmin = cmin
         return c, np.stack([ga, gb, gh], 1)
 
     def soft_refine(self, tool: Tool, pts: np.ndarray, per_point: int, u0: np.ndarray,
                     alpha: np.ndarray, beta: np.ndarray, h: np.ndarray, steps: int,
                     lr_dir: float, lr_h: float, h_max: float, tau_s: float = 0.005):
-        """(alpha, beta, h, C) after `steps` ascent steps."""
+        """(alpha, beta, h, C, hard clearance) after `steps` ascent steps."""
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
         u0 = np.ascontiguousarray(u0, np.float32).reshape(-1, 3)
         n = len(u0)
         a, b, hh = (np.array(x, np.float32).reshape(n) for x in (alpha, beta, h))
         if per_point < 1 or len(pts) * per_point < n:
             raise ValueError("need per_point >= 1 and a point for every pair")
-        c = np.zeros(n)
+        c, cmin = np.zeros(n), np.zeros(n)
         tc = tool._c()
         self._lib.or_soft_refine(self._h, C.byref(tc), _ptr(pts), per_point, _ptr(u0), _ptr(a),
                                  _ptr(b), _ptr(hh), n, tau_s, steps, lr_dir, lr_h, h_max,
-                                 _ptr(c))
-        return a, b, hh, c
+                                 _ptr(c), _ptr(cmin))
+        return a, b, hh, c, cmin
 
 
 def soft_seed(normals: np.ndarray, table: np.ndarray) -> np.ndarray:

@@ -602,7 +602,7 @@ static int sample_cell_f(const pair_frame *F, int j, int32_t cell[3]) {
     const float t = F->e + (float)j;
     for (int i = 0; i < 3; ++i) {
         const float l = F->r[i] + t * F->w[i];
-        if (!(fabsf(l) < 1.0e7f)) return 0;
+        if (!(fabsf(l) < 1.0e7f) || !(fabsf(F->I[i]) < 1.0e9f)) return 0;
         cell[i] = (int32_t)F->I[i] + (int32_t)floorf(l);
     }
     return 1;
@@ -617,13 +617,14 @@ static int all_finite(const float *x, int n) {
 /* Soft clearance of one pair and its gradient, in double. */
 static double soft_pair(const or_map *m, const or_tool *t, const float s[3], const float u0[3],
                         float al, float be, float h, double tau_s, int fp32_cells,
-                        double grad[3]) {
+                        double grad[3], double *cmin) {
     const float vf = m->cfg.v;
     const double v = (double)vf;
     const int J = (int)floorf((t->length + t->corr_length) / vf);
     if (!all_finite(s, 3) || !all_finite(u0, 3) || !isfinite(al) || !isfinite(be) ||
         !isfinite(h)) {
         grad[0] = grad[1] = grad[2] = NAN;
+        *cmin = NAN;
         return NAN;
     }
     /* direction and its derivatives */
@@ -686,6 +687,7 @@ static double soft_pair(const or_map *m, const or_tool *t, const float s[3], con
         ++ns;
     }
     double C;
+    *cmin = ns ? mn : NAN;
     if (ns == 0) {
         C = NAN;
         grad[0] = grad[1] = grad[2] = NAN;
@@ -711,11 +713,12 @@ static double soft_pair(const or_map *m, const or_tool *t, const float s[3], con
 void or_soft_clearance(const or_map *m, const or_tool *t, const float *pts, uint32_t per_point,
                        const float *u0, const float *alpha, const float *beta, const float *h,
                        int64_t npairs, double tau_s, int fp32_cells, double *c,
-                       double *g_alpha, double *g_beta, double *g_h) {
+                       double *g_alpha, double *g_beta, double *g_h, double *cmin) {
     for (int64_t i = 0; i < npairs; ++i) {
-        double g[3];
+        double g[3], mn;
         c[i] = soft_pair(m, t, pts + 3 * (i / per_point), u0 + 3 * i, alpha[i], beta[i], h[i],
-                         tau_s, fp32_cells, g);
+                         tau_s, fp32_cells, g, &mn);
+        if (cmin) cmin[i] = mn;
         if (g_alpha) g_alpha[i] = g[0];
         if (g_beta) g_beta[i] = g[1];
         if (g_h) g_h[i] = g[2];
@@ -724,12 +727,13 @@ void or_soft_clearance(const or_map *m, const or_tool *t, const float *pts, uint
 
 void or_soft_refine(const or_map *m, const or_tool *t, const float *pts, uint32_t per_point,
                     const float *u0, float *alpha, float *beta, float *h, int64_t npairs,
-                    double tau_s, int steps, float lr_dir, float lr_h, float h_max, double *c) {
+                    double tau_s, int steps, float lr_dir, float lr_h, float h_max, double *c,
+                    double *cmin) {
     for (int64_t i = 0; i < npairs; ++i) {
         const float *s = pts + 3 * (i / per_point);
-        double g[3];
+        double g[3], mn;
         for (int k = 0; k < steps; ++k) {
-            soft_pair(m, t, s, u0 + 3 * i, alpha[i], beta[i], h[i], tau_s, 1, g);
+            soft_pair(m, t, s, u0 + 3 * i, alpha[i], beta[i], h[i], tau_s, 1, g, &mn);
             /* gradient ascent on C, standoff kept in [0, h_max] */
             alpha[i] = (float)((double)alpha[i] + (double)lr_dir * g[0]);
             beta[i] = (float)((double)beta[i] + (double)lr_dir * g[1]);
@@ -737,6 +741,7 @@ void or_soft_refine(const or_map *m, const or_tool *t, const float *pts, uint32_
             hn = hn < 0.0 ? 0.0 : (hn > (double)h_max ? (double)h_max : hn);
             h[i] = (float)hn;
         }
-        c[i] = soft_pair(m, t, s, u0 + 3 * i, alpha[i], beta[i], h[i], tau_s, 1, g);
+        c[i] = soft_pair(m, t, s, u0 + 3 * i, alpha[i], beta[i], h[i], tau_s, 1, g, &mn);
+        if (cmin) cmin[i] = mn;
     }
 }

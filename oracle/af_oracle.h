@@ -93,21 +93,23 @@ void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G,
 /* The differentiable form: soft clearance of (point, direction) pairs.
  * Pair i belongs to point i / per_point. For pair i with base direction u0,
  * tangent coordinates (alpha, beta) and standoff h it writes
- * C = softmin_{tau_s} over the axis samples of (SDF - margin) and
- * dC/d(alpha, beta, h) (gradients optional). Readings in af_oracle.c. */
+ * C = softmin_{tau_s} over the axis samples of (SDF - margin),
+ * dC/d(alpha, beta, h) and the hard clearance min_j (SDF - margin)
+ * (gradients and cmin optional). Readings in af_oracle.c. */
 void or_soft_clearance(const or_map *m, const or_tool *t, const float *pts, uint32_t per_point,
                        const float *u0, const float *alpha, const float *beta, const float *h,
                        int64_t npairs, double tau_s, int fp32_cells, double *c,
-                       double *g_alpha, double *g_beta, double *g_h);
+                       double *g_alpha, double *g_beta, double *g_h, double *cmin);
 /* Seed directions: u0[p*K + k] = table_k rotated into the tangent frame of
  * normal p (table +z -> normal), single precision in a fixed order. */
 void or_soft_seed(const float *normals, int64_t npts, const float *table, int32_t K, float *u0);
 /* `steps` gradient-ascent steps on C (alpha, beta += lr_dir * grad;
  * h += lr_h * grad, kept in [0, h_max]; state rounded to single precision
- * after each step), then C at the final state. */
+ * after each step), then C and the hard clearance at the final state. */
 void or_soft_refine(const or_map *m, const or_tool *t, const float *pts, uint32_t per_point,
                     const float *u0, float *alpha, float *beta, float *h, int64_t npairs,
-                    double tau_s, int steps, float lr_dir, float lr_h, float h_max, double *c);
+                    double tau_s, int steps, float lr_dir, float lr_h, float h_max, double *c,
+                    double *cmin);
 
 #ifdef __cplusplus
 }

@@ -26,10 +26,15 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_score", "af_frame_host", "af_sync_status", "af_get_stats", "af_block_count",
            "af_export_blocks", "af_kernel_offsets", "af_arm_offsets", "af_profile_enable",
            "af_profile_read", "af_integrate_scan_noalloc", "af_batch_create", "af_batch_destroy",
-           "af_batch_tick", "af_batch_set_tuning", "af_batch_get_tuning", "af_last_error")
+           "af_batch_tick", "af_batch_set_tuning", "af_batch_get_tuning", "af_soft_seed",
+           "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
+           "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
-KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score")
+KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
+           "k_soft_adjoint", "k_soft_refine")
+#: Softmin temperature of the soft clearance (m).
+TAU_S = 0.005
 
 
 class AfError(RuntimeError):
@@ -63,7 +68,12 @@ class _Stats(C.Structure):
 
 
 class _Profile(C.Structure):
-    _fields_ = [("launches", C.c_uint64 * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_uint64 * 8), ("ms", C.c_double * 8)]
+
+
+class _Refine(C.Structure):
+    _fields_ = [("steps", C.c_uint32), ("lr_dir", C.c_float), ("lr_h", C.c_float),
+                ("h_max", C.c_float)]
 
 
 class _BatchItem(C.Structure):
@@ -113,6 +123,14 @@ def load(build: bool = True) -> C.CDLL:
             "af_batch_tick": (C.c_int, [P, P, P]),
             "af_batch_set_tuning": (C.c_int, [P, U32, U32]),
             "af_batch_get_tuning": (C.c_int, [P, C.POINTER(_Tuning)]),
+            "af_soft_seed": (C.c_int, [P, P, U32, P, U32, P, P]),
+            "af_soft_clearance": (C.c_int, [P, P, U32, P, P, P, P, C.c_uint64, C.c_float, P,
+                                            P, P]),
+            "af_soft_clearance_adjoint": (C.c_int, [P, P, U32, P, P, P, P, C.c_uint64,
+                                                    C.c_float, P, P, P, P, P, P]),
+            "af_soft_refine": (C.c_int, [P, P, U32, P, P, P, P, C.c_uint64, C.c_float,
+                                         C.POINTER(_Refine), P, P, P]),
+            "af_soft_best": (C.c_int, [P, P, C.c_uint64, U32, P, P, P, P, P]),
             "af_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -303,6 +321,143 @@ class Map:
                                           _np_ptr(fl), C.byref(out)), self._h)
         n = int(out.value)
         return dict(key=key[:n], S=S[:n], w=w[:n], flags=fl[:n])
+
+    # ---- the differentiable form ----
+
+    def soft_seed(self, normals, table, stream=None):
+        """af_soft_seed: (m*K, 3) base directions, the K rows of `table`
+        (K x 3, around +z) rotated into each normal's tangent frame."""
+        import torch
+        m = int(normals.shape[0])
+        table = np.ascontiguousarray(table, np.float32).reshape(-1, 3)
+        u0 = torch.empty((m * len(table), 3), dtype=torch.float32, device=normals.device)
+        _check(self._lib.af_soft_seed(self._h, _dev_ptr(normals, torch.float32, (3,)) if m
+                                      else C.c_void_p(0), m, _np_ptr(table), len(table),
+                                      _dev_ptr(u0, torch.float32, (3,)) if m else C.c_void_p(0),
+                                      _stream_ptr(stream)), self._h)
+        return u0
+
+    def _pair_ptrs(self, pts, u0, alpha, beta, h, per_point):
+        import torch
+        n = int(u0.shape[0])
+        if per_point < 1 or int(pts.shape[0]) * per_point < n:
+            raise ValueError("need per_point >= 1 and a point for every pair")
+        for t in (alpha, beta, h):
+            if t.shape != (n,):
+                raise ValueError("alpha, beta and h need one value per pair")
+        if n == 0:
+            return n, [C.c_void_p(0)] * 5
+        return n, [_dev_ptr(pts, torch.float32, (3,)), _dev_ptr(u0, torch.float32, (3,)),
+                   _dev_ptr(alpha, torch.float32), _dev_ptr(beta, torch.float32),
+                   _dev_ptr(h, torch.float32)]
+
+    def soft_clearance_raw(self, pts, u0, alpha, beta, h, per_point, tau_s=TAU_S, out=None,
+                           cmin=None, stream=None):
+        """af_soft_clearance: C of every pair (no autograd); `cmin`, if
+        given, receives the hard clearance."""
+        import torch
+        n, ptr = self._pair_ptrs(pts, u0, alpha, beta, h, per_point)
+        c = torch.empty(n, dtype=torch.float32, device=u0.device) if out is None else out
+        _check(self._lib.af_soft_clearance(self._h, ptr[0], per_point, *ptr[1:], n, tau_s,
+                                           _dev_ptr(c, torch.float32) if n else C.c_void_p(0),
+                                           _dev_ptr(cmin, torch.float32) if (cmin is not None
+                                                                            and n)
+                                           else C.c_void_p(0), _stream_ptr(stream)), self._h)
+        return c
+
+    def soft_clearance_adjoint(self, pts, u0, alpha, beta, h, per_point, tau_s=TAU_S,
+                               grad_c=None, stream=None):
+        """af_soft_clearance_adjoint: (C, g dC/dalpha, g dC/dbeta, g dC/dh)."""
+        import torch
+        n, ptr = self._pair_ptrs(pts, u0, alpha, beta, h, per_point)
+        out = [torch.empty(n, dtype=torch.float32, device=u0.device) for _ in range(4)]
+        op = [_dev_ptr(t, torch.float32) if n else C.c_void_p(0) for t in out]
+        gp = _dev_ptr(grad_c, torch.float32) if (grad_c is not None and n) else C.c_void_p(0)
+        _check(self._lib.af_soft_clearance_adjoint(self._h, ptr[0], per_point, *ptr[1:], n,
+                                                   tau_s, gp, *op, _stream_ptr(stream)),
+               self._h)
+        return tuple(out)
+
+    def soft_clearance(self, pts, u0, alpha, beta, h, per_point, tau_s=TAU_S):
+        """C of every pair, differentiable in alpha, beta and h (SoftClearance)."""
+        return SoftClearance.apply(self, pts, u0, alpha, beta, h, per_point, tau_s)
+
+    def soft_refine(self, pts, u0, alpha, beta, h, per_point=1, steps=20, lr_dir=0.05,
+                    lr_h=0.005, h_max=0.05, tau_s=TAU_S, stream=None):
+        """af_soft_refine: `steps` ascent steps on every pair in one launch;
+        alpha, beta, h are updated in place. Returns (C, hard clearance)."""
+        import torch
+        n, ptr = self._pair_ptrs(pts, u0, alpha, beta, h, per_point)
+        R = _Refine(steps, lr_dir, lr_h, h_max)
+        c = torch.empty(n, dtype=torch.float32, device=u0.device)
+        cmin = torch.empty(n, dtype=torch.float32, device=u0.device)
+        op = [_dev_ptr(t, torch.float32) if n else C.c_void_p(0) for t in (c, cmin)]
+        _check(self._lib.af_soft_refine(self._h, ptr[0], per_point, *ptr[1:], n, tau_s,
+                                        C.byref(R), *op, _stream_ptr(stream)), self._h)
+        return c, cmin
+
+    def soft_best(self, c, per_point, u0=None, stream=None):
+        """af_soft_best: per point (index of its largest C, that C, and --
+        with u0 -- that pair's base direction)."""
+        import torch
+        n = int(c.shape[0])
+        npts = (n + per_point - 1) // per_point
+        bk = torch.empty(npts, dtype=torch.int32, device=c.device)
+        bc = torch.empty(npts, dtype=torch.float32, device=c.device)
+        bu = torch.empty((npts, 3), dtype=torch.float32, device=c.device) if u0 is not None \
+            else None
+        z = C.c_void_p(0)
+        _check(self._lib.af_soft_best(self._h, _dev_ptr(c, torch.float32) if n else z, n,
+                                      per_point, _dev_ptr(u0, torch.float32, (3,))
+                                      if (u0 is not None and n) else z,
+                                      _dev_ptr(bk, torch.int32) if npts else z,
+                                      _dev_ptr(bc, torch.float32) if npts else z,
+                                      _dev_ptr(bu, torch.float32, (3,)) if (bu is not None and
+                                                                           npts) else z,
+                                      _stream_ptr(stream)), self._h)
+        return (bk, bc, bu) if u0 is not None else (bk, bc)
+
+
+def _soft_function():
+    import torch
+
+    class SoftClearance(torch.autograd.Function):
+        """C = soft clearance of (point, direction) pairs; backward runs the
+        adjoint kernel, which recomputes every SDF sample from the map (only
+        the inputs are saved)."""
+
+        @staticmethod
+        def forward(ctx, m, pts, u0, alpha, beta, h, per_point, tau_s):
+            ctx.save_for_backward(pts, u0, alpha, beta, h)
+            ctx.m, ctx.per_point, ctx.tau_s = m, per_point, tau_s
+            return m.soft_clearance_raw(pts, u0, alpha.detach(), beta.detach(), h.detach(),
+                                        per_point, tau_s)
+
+        @staticmethod
+        def backward(ctx, grad_c):
+            pts, u0, alpha, beta, h = ctx.saved_tensors
+            _, ga, gb, gh = ctx.m.soft_clearance_adjoint(
+                pts, u0, alpha.detach(), beta.detach(), h.detach(), ctx.per_point, ctx.tau_s,
+                grad_c.contiguous())
+            return (None, None, None, ga if ctx.needs_input_grad[3] else None,
+                    gb if ctx.needs_input_grad[4] else None,
+                    gh if ctx.needs_input_grad[5] else None, None, None)
+
+    return SoftClearance
+
+
+class _LazySoft:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazySoft._fn is None:
+            _LazySoft._fn = _soft_function()
+        return _LazySoft._fn.apply(*args)
+
+
+#: torch.autograd.Function of the soft clearance: SoftClearance.apply(map,
+#: pts, u0, alpha, beta, h, per_point, tau_s).
+SoftClearance = _LazySoft()
 
 
 def export_voxels(blocks: dict) -> dict:

@@ -30,6 +30,15 @@ struct af_ctx {
   int2* d_fruns = nullptr;
   int4* d_dtab = nullptr;
   short4* d_arm = nullptr;
+  af_tool tool{};
+  // views of the differentiable form (built on first use, rebuilt when the
+  // map has changed since)
+  float* d_dense = nullptr;
+  float4* d_cells = nullptr;
+  bool views_valid = false;
+  uint32_t views_frame = 0;
+  float* d_table = nullptr;  // seed directions
+  uint32_t table_cap = 0;
   // host counters
   uint64_t scans = 0, returns_in = 0, points_in = 0;
   // kernel profiling: CUDA events around each launch on its own stream

@@ -25,6 +25,21 @@ cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts
                          cudaStream_t stream);
 cudaError_t launch_export_flags(const MapView& M, uint32_t count, uint8_t* d_flags,
                                 cudaStream_t stream);
+cudaError_t launch_views(const MapView& M, int num_sms, bool fill, float* dense, float4* cells,
+                         cudaStream_t stream);
+cudaError_t launch_soft_seed(const float* d_nrm, uint32_t m, const float* d_table, uint32_t K,
+                             float* d_u0, int num_sms, cudaStream_t stream);
+cudaError_t launch_soft(const SoftView& S, bool grad, const float* pts, uint32_t per_point,
+                        const float* u0, const float* al, const float* be, const float* h,
+                        uint64_t n, const float* gc, float* c, float* cmin, float* ga,
+                        float* gb, float* gh, int num_sms, cudaStream_t stream);
+cudaError_t launch_soft_refine(const SoftView& S, const RefineArgs& R, const float* pts,
+                               uint32_t per_point, const float* u0, float* al, float* be,
+                               float* h, uint64_t n, float* c, float* cmin, int num_sms,
+                               cudaStream_t stream);
+cudaError_t launch_soft_best(const float* c, uint64_t n, uint32_t per_point, const float* u0,
+                             int32_t* best_k, float* best_c, float* best_u0, int num_sms,
+                             cudaStream_t stream);
 }  // namespace af
 
 using af::MapView;
@@ -254,6 +269,9 @@ static void free_all(af_ctx* c) {
   cudaFree(c->d_nrm);
   cudaFree(c->d_label);
   cudaFree(c->d_best);
+  cudaFree(c->d_dense);
+  cudaFree(c->d_cells);
+  cudaFree(c->d_table);
   cudaFreeHost(c->h_status);
 }
 
@@ -479,6 +497,7 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
   ctx->T.n_c = (int)tool->n_c;
   ctx->T.cos_max = tool->cos_theta_max;
   ctx->T.strict = tool->corridor_strict;
+  ctx->tool = *tool;
   ctx->has_tool = true;
   return AF_OK;
 }
@@ -623,5 +642,195 @@ extern "C" af_status af_profile_read(af_ctx* ctx, af_profile* out, int reset) {
     }
     ctx->prof.clear();
   }
+  return AF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The differentiable form
+// ---------------------------------------------------------------------------
+
+// Builds (or rebuilds, if the map changed since) the dense and cell views.
+static af_status ensure_views(af_ctx* ctx, cudaStream_t s) {
+  const MapView& M = ctx->M;
+  bool fill = false;
+  if (!ctx->d_cells) {
+    const size_t nd = (size_t)M.dim_vox[0] * M.dim_vox[1] * M.dim_vox[2];
+    const size_t nc = ((size_t)M.dim_vox[0] + 1) * (M.dim_vox[1] + 1) * (M.dim_vox[2] + 1);
+    if (cudaMalloc(&ctx->d_dense, nd * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_cells, nc * 2 * sizeof(float4)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ctx->d_dense);
+      ctx->d_dense = nullptr;
+      ctx->d_cells = nullptr;
+      return fail(ctx, AF_ERR_CAPACITY,
+                  "soft clearance: cannot allocate the SDF views (%zu + %zu bytes) of the map box",
+                  nd * sizeof(float), nc * 2 * sizeof(float4));
+    }
+    fill = true;
+  }
+  if (fill || !ctx->views_valid || ctx->views_frame != ctx->frame) {
+    AF_CUDA(ctx, timed(ctx, 4, s, [&] {
+      return af::launch_views(M, ctx->num_sms, fill, ctx->d_dense, ctx->d_cells, s);
+    }));
+    ctx->views_valid = true;
+    ctx->views_frame = ctx->frame;
+  }
+  return AF_OK;
+}
+
+// The axis samples of the tool, decided in single precision: j = j0..J with
+// j v > r_s, tool margin while j v <= L.
+static af_status soft_view(af_ctx* ctx, float tau_s, af::SoftView* S) {
+  if (!ctx->has_tool) return fail(ctx, AF_ERR_STATE, "soft clearance: call af_set_tool first");
+  if (!(tau_s > 0.f) || !std::isfinite(tau_s))
+    return fail(ctx, AF_ERR_INVALID_ARG, "soft clearance: tau_s must be finite and > 0");
+  const af_tool& t = ctx->tool;
+  const float v = ctx->cfg.voxel_size;
+  const float span = t.length + t.corr_length;
+  const float q = span / v;
+  if (!(q < 1.0e6f)) return fail(ctx, AF_ERR_INVALID_ARG, "soft clearance: tool too long");
+  const int J = (int)std::floor(q);
+  int j0 = J + 1, jt = 0;
+  for (int j = J; j >= 1; --j) {
+    const float a = (float)j * v;
+    if (a > t.self_excl) j0 = j;
+    if (a <= t.length && jt == 0) jt = j;
+  }
+  if (j0 > J)
+    return fail(ctx, AF_ERR_STATE, "soft clearance: no axis sample lies beyond the self-exclusion radius");
+  const MapView& M = ctx->M;
+  S->cells = ctx->d_cells;
+  for (int k = 0; k < 3; ++k) {
+    S->lo[k] = M.dom_vox[k] - 1;
+    S->ncell[k] = M.dim_vox[k] + 1;
+  }
+  S->v = v;
+  S->tau = ctx->cfg.truncation;
+  S->r = t.radius;
+  S->r_corr = t.corr_radius;
+  S->j0 = j0;
+  S->jt = jt;
+  S->J = J;
+  S->k2 = (float)(1.4426950408889634 / (double)tau_s);
+  S->ln2_tau_s = (float)(0.6931471805599453 * (double)tau_s);
+  return AF_OK;
+}
+
+static af_status check_pairs(af_ctx* ctx, const char* fn, const float* d_pts, uint32_t per_point,
+                             const float* d_u0, const float* a, const float* b, const float* h,
+                             uint64_t n) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "%s: NULL context", fn);
+  if (per_point < 1) return fail(ctx, AF_ERR_INVALID_ARG, "%s: per_point must be >= 1", fn);
+  if (n > (1ull << 40)) return fail(ctx, AF_ERR_INVALID_ARG, "%s: too many pairs", fn);
+  if (n > 0 && (!d_pts || !d_u0 || !a || !b || !h))
+    return fail(ctx, AF_ERR_INVALID_ARG, "%s: NULL input", fn);
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_seed(af_ctx* ctx, const float* d_normals, uint32_t m,
+                                  const float* h_table, uint32_t K, float* d_u0, void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_soft_seed: NULL context");
+  if (K < 1 || K > 65536 || !h_table)
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_seed: need a table of 1..65536 directions");
+  if (m > 0 && (!d_normals || !d_u0)) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_seed: NULL buffer");
+  for (uint32_t k = 0; k < 3 * K; ++k)
+    if (!std::isfinite(h_table[k])) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_seed: non-finite table");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (K > ctx->table_cap) {
+    AF_CUDA(ctx, cudaStreamSynchronize(s));
+    cudaFree(ctx->d_table);
+    ctx->d_table = nullptr;
+    ctx->table_cap = 0;
+    AF_CUDA(ctx, cudaMalloc(&ctx->d_table, (size_t)K * 3 * sizeof(float)));
+    ctx->table_cap = K;
+  }
+  AF_CUDA(ctx, cudaMemcpyAsync(ctx->d_table, h_table, (size_t)K * 3 * sizeof(float),
+                               cudaMemcpyHostToDevice, s));
+  AF_CUDA(ctx, af::launch_soft_seed(d_normals, m, ctx->d_table, K, d_u0, ctx->num_sms, s));
+  // the table is reused by the next call: keep this call's copy alive until
+  // its kernel has read it
+  AF_CUDA(ctx, cudaStreamSynchronize(s));
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_clearance(af_ctx* ctx, const float* d_pts, uint32_t per_point,
+                                       const float* d_u0, const float* d_alpha,
+                                       const float* d_beta, const float* d_h, uint64_t n,
+                                       float tau_s, float* d_c, float* d_cmin, void* stream) {
+  af_status st = check_pairs(ctx, "af_soft_clearance", d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n);
+  if (st != AF_OK) return st;
+  if (n > 0 && !d_c) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_clearance: NULL output");
+  af::SoftView S;
+  if ((st = soft_view(ctx, tau_s, &S)) != AF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = ensure_views(ctx, s)) != AF_OK) return st;
+  S.cells = ctx->d_cells;
+  AF_CUDA(ctx, timed(ctx, 5, s, [&] {
+    return af::launch_soft(S, false, d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n, nullptr,
+                           d_c, d_cmin, nullptr, nullptr, nullptr, ctx->num_sms, s);
+  }));
+  ctx->last_stream = s;
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_clearance_adjoint(af_ctx* ctx, const float* d_pts, uint32_t per_point,
+                                               const float* d_u0, const float* d_alpha,
+                                               const float* d_beta, const float* d_h, uint64_t n,
+                                               float tau_s, const float* d_gc, float* d_c,
+                                               float* d_ga, float* d_gb, float* d_gh,
+                                               void* stream) {
+  af_status st = check_pairs(ctx, "af_soft_clearance_adjoint", d_pts, per_point, d_u0, d_alpha,
+                             d_beta, d_h, n);
+  if (st != AF_OK) return st;
+  af::SoftView S;
+  if ((st = soft_view(ctx, tau_s, &S)) != AF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = ensure_views(ctx, s)) != AF_OK) return st;
+  S.cells = ctx->d_cells;
+  AF_CUDA(ctx, timed(ctx, 6, s, [&] {
+    return af::launch_soft(S, true, d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n, d_gc, d_c,
+                           nullptr, d_ga, d_gb, d_gh, ctx->num_sms, s);
+  }));
+  ctx->last_stream = s;
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_refine(af_ctx* ctx, const float* d_pts, uint32_t per_point,
+                                    const float* d_u0, float* d_alpha, float* d_beta, float* d_h,
+                                    uint64_t n, float tau_s, const af_refine* R, float* d_c,
+                                    float* d_cmin, void* stream) {
+  af_status st = check_pairs(ctx, "af_soft_refine", d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n);
+  if (st != AF_OK) return st;
+  if (!R) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_refine: NULL parameters");
+  if (R->steps > 100000 || !std::isfinite(R->lr_dir) || !std::isfinite(R->lr_h) ||
+      !(R->h_max >= 0.f) || !std::isfinite(R->h_max))
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_refine: bad steps / step sizes / h_max");
+  if (n > 0 && !d_c) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_refine: NULL output");
+  af::SoftView S;
+  if ((st = soft_view(ctx, tau_s, &S)) != AF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = ensure_views(ctx, s)) != AF_OK) return st;
+  S.cells = ctx->d_cells;
+  const af::RefineArgs A{(int)R->steps, R->lr_dir, R->lr_h, R->h_max};
+  AF_CUDA(ctx, timed(ctx, 7, s, [&] {
+    return af::launch_soft_refine(S, A, d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n, d_c,
+                                  d_cmin, ctx->num_sms, s);
+  }));
+  ctx->last_stream = s;
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_best(af_ctx* ctx, const float* d_c, uint64_t n, uint32_t per_point,
+                                  const float* d_u0, int32_t* d_best_k, float* d_best_c,
+                                  float* d_best_u0, void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_soft_best: NULL context");
+  if (per_point < 1) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_best: per_point must be >= 1");
+  if (n > (1ull << 40)) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_best: too many pairs");
+  if (n > 0 && (!d_c || (d_best_u0 && !d_u0)))
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_best: NULL input");
+  cudaStream_t s = (cudaStream_t)stream;
+  AF_CUDA(ctx, af::launch_soft_best(d_c, n, per_point, d_u0, d_best_k, d_best_c, d_best_u0,
+                                    ctx->num_sms, s));
+  ctx->last_stream = s;
   return AF_OK;
 }

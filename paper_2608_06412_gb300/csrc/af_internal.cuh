@@ -175,6 +175,26 @@ struct Pose {
   float r[3][4];  // row-major [R | t]
 };
 
+// ---- the differentiable form (soft clearance) ----
+
+// What the soft-clearance kernels read: the cell view of the map and the
+// axis samples of the tool. Built per call by the host.
+struct SoftView {
+  const float4* cells;  // ncell[0] * ncell[1] * ncell[2] cells, 2 float4 each
+  int lo[3];            // absolute voxel index of the lowest cell's low corner
+  int ncell[3];         // cells per axis: box voxels + 1
+  float v, tau;
+  float r, r_corr;      // margins: tool, corridor
+  int j0, jt, J;        // samples j0..J; tool margin for j <= jt
+  float k2;             // log2(e) / tau_s
+  float ln2_tau_s;      // tau_s ln 2
+};
+
+struct RefineArgs {
+  int steps;
+  float lr_dir, lr_h, h_max;
+};
+
 // ---- batched ticks: many maps in one set of persistent launches ----
 
 // One map's share of a batched tick, rewritten every tick. The offsets are

@@ -88,6 +88,21 @@ def pine_frame(W: Workload, f: int):
     return fr, pts, nrm
 
 
+def soft_points(frames, v: float, count: int = 100_000, seed: int = 0):
+    """Surface points of the differentiable-form workload: one point (and
+    normal) per voxel that the stream's surface points fall in, its first
+    occurrence in stream order, then `count` of them drawn without
+    replacement by a seeded generator (all of them if fewer)."""
+    pts = np.concatenate([f[1] for f in frames])
+    nrm = np.concatenate([f[2] for f in frames])
+    ijk = np.floor(pts.astype(np.float64) / np.float64(np.float32(v))).astype(np.int64)
+    _, first = np.unique(ijk, axis=0, return_index=True)
+    first = np.sort(first)
+    g = synth.rng(seed, 61)
+    pick = np.sort(g.choice(len(first), min(count, len(first)), replace=False))
+    sel = first[pick]
+    return np.ascontiguousarray(pts[sel]), np.ascontiguousarray(nrm[sel])
+
 #: Map capacities the benchmark uses for the pine stream (and the full-size
 #: parity test runs with): 512k hash slots, 256k bricks (1.1 GB), 64k returns
 #: and points per call.

@@ -132,10 +132,12 @@ def test_softmin_tends_to_minimum(linear_map):
     tool = _tool()
     s, u0, ab, h = _pairs(rng, 8)
     c, _ = linear_map.soft_clearance(tool, s, 1, u0, ab[:, 0], ab[:, 1], h, 1e-7)
+    cmin = linear_map.last_cmin
     for i in range(len(s)):
         _, phi = _closed_form(s[i], u0[i], float(ab[i, 0]), float(ab[i, 1]), float(h[i]),
                               tool, 0.005)
         assert abs(c[i] - phi.min()) < 3e-6
+        assert abs(cmin[i] - phi.min()) < 3e-6      # the hard clearance
     # and C never exceeds the minimum: softmin is a lower bound of min
     c2, _ = linear_map.soft_clearance(tool, s, 1, u0, ab[:, 0], ab[:, 1], h, 0.02)
     assert (c2 <= c + 1e-12).all()
@@ -247,7 +249,8 @@ def test_refine_raises_clearance(scene):
     n = len(u0)
     z = np.zeros(n, np.float32)
     c0, _ = mp.soft_clearance(tool, pts[idx], 4, u0, z, z, z)
-    a, b, h, c = mp.soft_refine(tool, pts[idx], 4, u0, z, z, z, 20, 0.02, 0.002, 0.05)
+    a, b, h, c, cmin = mp.soft_refine(tool, pts[idx], 4, u0, z, z, z, 20, 0.02, 0.002, 0.05)
+    assert (c <= cmin).all()
     assert (h >= 0).all() and (h <= np.float32(0.05)).all()
     # plain gradient ascent with a small step: clearance does not drop (beyond
     # the kinks of trilinear interpolation) and rises on average
