@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--batched", action="store_true",
                     help="the batched form (many scenes per tick) instead of the pine stream")
     ap.add_argument("--scenes", type=int, default=64)
+    ap.add_argument("--soft", action="store_true",
+                    help="the differentiable form on the pine map after 300 frames")
+    ap.add_argument("--soft-points", type=int, default=100_000)
     return ap.parse_args()
 
 
@@ -538,12 +541,203 @@ def run_batched(args, local):
     }
 
 
+SOFT_METRIC = ("soft clearance evaluations/s (plain scoring of 100k points, then 20 ascent "
+               "steps from each accessible point's best orientation)")
+SOFT_UNIT = "evaluations/s"
+SOFT_STEPS = 20
+SOFT_LR = dict(lr_dir=0.05, lr_h=0.005, h_max=0.05)
+
+
+def soft_cpu_baseline(W, frames, P, N, n_points=40, n_frames=6):
+    """The oracle's differentiable step on a bounded sample: a map of the
+    first frames, then plain scoring, start, soft clearance and refinement
+    of n_points points."""
+    import oracle
+    from paper_2608_06412_gb300 import af
+    om, tool = _oracle_objs(W)
+    for fr, _, _ in frames[:n_frames]:
+        om.integrate(fr.pts, fr.pose)
+    sel = np.random.default_rng(2).choice(len(P), n_points, replace=False)
+    p, nrm = P[sel], N[sel]
+    t0 = time.perf_counter()
+    lab, best = om.score(tool, W.dirs, p, nrm)
+    acc = (lab == 1) & (best >= 0)
+    u0 = np.where(acc[:, None], W.dirs[np.maximum(best, 0)], np.nan).astype(np.float32)
+    z = np.zeros(n_points, np.float32)
+    om.soft_clearance(tool, p[acc], 1, u0[acc], z[acc], z[acc], z[acc], af.TAU_S)
+    om.soft_refine(tool, p[acc], 1, u0[acc], z[acc], z[acc], z[acc], SOFT_STEPS,
+                   tau_s=af.TAU_S, **SOFT_LR)
+    secs = time.perf_counter() - t0
+    evals = int(acc.sum()) * (SOFT_STEPS + 2)
+    return {"value": evals / secs, "unit": SOFT_UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"single-threaded C oracle: map of frames 0-{n_frames - 1}, then plain "
+                      f"scoring of {n_points} random points and the soft step of the "
+                      f"{int(acc.sum())} accessible ones ({secs:.1f} s)"}
+
+
+def run_soft(args, local):
+    """Differentiable form on the pine map after 300 frames with 100k surface
+    points. One step: plain scoring of the points (K = 64 of G = 128), the
+    start direction of each accessible point (its best), its soft clearance,
+    and 20 ascent steps on (alpha, beta, h) in one launch. Also timed: the
+    soft clearance over all K hemisphere orientations of every point (the
+    field, 6.4M pairs), the heaviest use of the forward kernel."""
+    import torch
+    from paper_2608_06412_gb300 import af, synth, workload
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = workload.pine_stream()
+    frames = _frames(W, 0, 300)
+    P, N = workload.soft_points(frames, W.params["v"], args.soft_points)
+    K = W.params["K"]
+    m = len(P)
+    caps = dict(workload.BENCH_CAPS, max_points=max(m, workload.BENCH_CAPS["max_points"]))
+    g = af.Map(W.af_config(**caps))
+    g.set_tool(W.af_tool(), W.dirs)
+    for fr, _, _ in frames:
+        g.integrate_scan(torch.from_numpy(fr.pts).to(dev), fr.pose)
+    torch.cuda.synchronize()
+    Pd, Nd = torch.from_numpy(P).to(dev), torch.from_numpy(N).to(dev)
+    lab = torch.empty(m, dtype=torch.uint8, device=dev)
+    best = torch.empty(m, dtype=torch.int16, device=dev)
+    u0 = torch.empty((m, 3), dtype=torch.float32, device=dev)
+    z = torch.zeros(m, dtype=torch.float32, device=dev)
+    al, be, hh, c0, c, cmin = (torch.empty(m, dtype=torch.float32, device=dev) for _ in range(6))
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    steps, warm = max(1, min(args.steps, 50)), max(args.warmup, 3)
+
+    def step(p_d=Pd, n_d=Nd):
+        g.score(p_d, n_d, lab, best)
+        g.soft_start(lab, best, out=u0)
+        g.soft_clearance_raw(p_d, u0, z, z, z, 1, out=c0)
+        al.zero_()
+        be.zero_()
+        hh.zero_()
+        g.soft_refine(p_d, u0, al, be, hh, 1, steps=SOFT_STEPS, out=(c, cmin), **SOFT_LR)
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        for i in range(k):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    n_acc = int((lab == af.ACCESSIBLE).sum().item())
+    clocks = Clocks(local)
+    clocks.start()
+    clocks.mark(True)
+    ms = timed(step, steps)
+    clocks.mark(False)
+    clk = clocks.stop()
+    evals = n_acc * (SOFT_STEPS + 2)
+
+    g.profile(True)
+    g.profile_read(reset=True)
+    timed(step, 3)
+    prof = g.profile_read(reset=True)
+    kt = {k: v for k, v in prof.items() if v[0] > 0}
+
+    # the field: soft clearance of every point at its K hemisphere orientations
+    table = synth.fibonacci_hemisphere(K, W.tool()["cos_theta_max"])
+    uf = torch.empty((m * K, 3), dtype=torch.float32, device=dev)
+    zf = torch.zeros(m * K, dtype=torch.float32, device=dev)
+    cf = torch.empty(m * K, dtype=torch.float32, device=dev)
+
+    def field():
+        g.soft_seed(Nd, table, out=uf)
+        g.soft_clearance_raw(Pd, uf, zf, zf, zf, K, out=cf)
+
+    field()
+    g.profile_read(reset=True)
+    ms_field = timed(field, max(3, steps // 4))
+    prof_f = g.profile_read(reset=True)
+    g.profile(False)
+
+    # outcome of one step
+    step()
+    torch.cuda.synchronize()
+    acc = (lab == af.ACCESSIBLE).cpu().numpy()
+    gain = (c - c0).cpu().numpy()[acc]
+    cmin_h = cmin.cpu().numpy()[acc]
+
+    # end to end: points and normals from pinned host memory; labels, best
+    # directions and refined poses back
+    hP, hN = torch.from_numpy(P).pin_memory(), torch.from_numpy(N).pin_memory()
+    outs = [torch.empty(m, dtype=torch.float32).pin_memory() for _ in range(5)]
+    hl = torch.empty(m, dtype=torch.uint8).pin_memory()
+    hb = torch.empty(m, dtype=torch.int16).pin_memory()
+    dP, dN = torch.empty_like(Pd), torch.empty_like(Nd)
+
+    def e2e_step():
+        dP.copy_(hP, non_blocking=True)
+        dN.copy_(hN, non_blocking=True)
+        step(dP, dN)
+        hl.copy_(lab, non_blocking=True)
+        hb.copy_(best, non_blocking=True)
+        for h_t, d_t in zip(outs, (al, be, hh, c, cmin)):
+            h_t.copy_(d_t, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    t_e2e = (time.perf_counter() - t0) / steps
+
+    total = sum(ms)
+    share = sum(v[1] for v in kt.values())
+    dom = max(kt, key=lambda k: kt[k][1])
+    roof = {"kernel": dom, "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in kt.items()},
+            "kernel_share": {k: round(v[1] / share, 4) for k, v in kt.items()}}
+    n_field = m * K
+    out = {
+        "metric": SOFT_METRIC, "value": evals / (total / steps / 1e3), "unit": SOFT_UNIT,
+        "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": total / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"soft_refine_pine_300_frames_{m}_points_K{K}",
+                   "points": m, "K": K, "G": len(W.dirs), "refine_steps": SOFT_STEPS,
+                   **SOFT_LR, "tau_s": af.TAU_S, "l2": "flushed between steps (256 MiB write)"},
+        "points_per_s": m / (total / steps / 1e3),
+        "accessible_points": n_acc,
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "roofline": roof,
+        "gpu_launches": int(round(sum(v[0] for v in kt.values()) / 3 * steps)),
+        "labels": "the plain path's (exact); refinement changes directions and standoffs only",
+        "refine": {"gain_m_mean": float(gain.mean()) if len(gain) else None,
+                   "gain_m_p10": float(np.percentile(gain, 10)) if len(gain) else None,
+                   "gain_m_p90": float(np.percentile(gain, 90)) if len(gain) else None,
+                   "hard_clear_after": float((cmin_h > 0).mean()) if len(cmin_h) else None},
+        "field": {"pairs": n_field, "ms": sum(ms_field) / len(ms_field),
+                  "evaluations_per_s": n_field / (sum(ms_field) / len(ms_field) / 1e3),
+                  "kernel_ms": {k: round(v[1] / v[0], 4) for k, v in prof_f.items() if v[0]}},
+        "e2e": {"value": evals / t_e2e, "unit": SOFT_UNIT, "h2d_bytes_per_step": 24 * m,
+                "d2h_bytes_per_step": 23 * m, "ms_per_step": t_e2e * 1e3},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = soft_cpu_baseline(W, frames, P, N)
+    g.close()
+    return out
+
+
 def main():
     args = _args()
     ws, rank, local = _dist()
     if args.batched:
         out = run_batched(args, local)
         print(json.dumps(out), flush=True)
+        return
+    if args.soft:
+        print(json.dumps(run_soft(args, local)), flush=True)
         return
     if ws > 1:
         import torch.distributed as dist

@@ -291,9 +291,18 @@ typedef struct {
 /* Seeds: u0[p*K + k] = table_k rotated into the tangent frame of normal p
  * (table +z -> the normal): h_table is K x 3 host floats (a hemisphere set
  * of K approach orientations around +z), d_normals m x 3 unit normals.
- * Synchronises `stream` before returning (the table buffer is reused). */
+ * The table is uploaded when it differs from the previous call's (the
+ * device is synchronised first); repeated calls with the same table are
+ * asynchronous. */
 af_status af_soft_seed(af_ctx *ctx, const float *d_normals, uint32_t m, const float *h_table,
                        uint32_t K, float *d_u0, void *stream);
+
+/* Start directions of refinement from the plain path: for each of m points
+ * scored by af_score, u0[p] = the context's direction best[p] when label[p]
+ * is AF_ACCESSIBLE, NaN otherwise (the soft calls return NaN for such pairs
+ * without sampling). d_label / d_best are af_score's outputs, d_u0 m x 3. */
+af_status af_soft_start(af_ctx *ctx, const uint8_t *d_label, const int16_t *d_best, uint32_t m,
+                        float *d_u0, void *stream);
 
 /* C of n pairs -> d_c; if d_cmin is given, also the hard clearance
  * min_j phi_j of each pair (> 0: every axis sample clears its margin). */
@@ -332,13 +341,14 @@ af_status af_soft_best(af_ctx *ctx, const float *d_c, uint64_t n, uint32_t per_p
  * Kernel timing: when enabled, every launch of the context is bracketed by
  * CUDA events recorded on the launch's own stream. Index 0 = brick
  * allocation, 1 = cube integration, 2 = weight cap + bit view, 3 = scoring,
- * 4 = SDF view build, 5 = soft clearance, 6 = its adjoint, 7 = refinement.
+ * 4 = SDF view build, 5 = soft clearance, 6 = its adjoint, 7 = refinement,
+ * 8 = seeding (af_soft_seed, af_soft_start), 9 = per-point best.
  * af_profile_read synchronises, sums the elapsed times of the recorded
  * launches (milliseconds) and, if `reset`, forgets them.
  */
 typedef struct {
-    uint64_t launches[8];
-    double ms[8];
+    uint64_t launches[10];
+    double ms[10];
 } af_profile;
 af_status af_profile_enable(af_ctx *ctx, int enable);
 af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);

@@ -28,11 +28,11 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_profile_read", "af_integrate_scan_noalloc", "af_batch_create", "af_batch_destroy",
            "af_batch_tick", "af_batch_set_tuning", "af_batch_get_tuning", "af_soft_seed",
            "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
-           "af_last_error")
+           "af_soft_start", "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
-           "k_soft_adjoint", "k_soft_refine")
+           "k_soft_adjoint", "k_soft_refine", "k_soft_seed", "k_soft_best")
 #: Softmin temperature of the soft clearance (m).
 TAU_S = 0.005
 
@@ -68,7 +68,7 @@ class _Stats(C.Structure):
 
 
 class _Profile(C.Structure):
-    _fields_ = [("launches", C.c_uint64 * 8), ("ms", C.c_double * 8)]
+    _fields_ = [("launches", C.c_uint64 * 10), ("ms", C.c_double * 10)]
 
 
 class _Refine(C.Structure):
@@ -131,6 +131,7 @@ def load(build: bool = True) -> C.CDLL:
             "af_soft_refine": (C.c_int, [P, P, U32, P, P, P, P, C.c_uint64, C.c_float,
                                          C.POINTER(_Refine), P, P, P]),
             "af_soft_best": (C.c_int, [P, P, C.c_uint64, U32, P, P, P, P, P]),
+            "af_soft_start": (C.c_int, [P, P, P, U32, P, P]),
             "af_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -324,17 +325,33 @@ class Map:
 
     # ---- the differentiable form ----
 
-    def soft_seed(self, normals, table, stream=None):
+    def soft_seed(self, normals, table, out=None, stream=None):
         """af_soft_seed: (m*K, 3) base directions, the K rows of `table`
         (K x 3, around +z) rotated into each normal's tangent frame."""
         import torch
         m = int(normals.shape[0])
         table = np.ascontiguousarray(table, np.float32).reshape(-1, 3)
-        u0 = torch.empty((m * len(table), 3), dtype=torch.float32, device=normals.device)
+        u0 = out if out is not None else \
+            torch.empty((m * len(table), 3), dtype=torch.float32, device=normals.device)
         _check(self._lib.af_soft_seed(self._h, _dev_ptr(normals, torch.float32, (3,)) if m
                                       else C.c_void_p(0), m, _np_ptr(table), len(table),
                                       _dev_ptr(u0, torch.float32, (3,)) if m else C.c_void_p(0),
                                       _stream_ptr(stream)), self._h)
+        return u0
+
+    def soft_start(self, label, best, out=None, stream=None):
+        """af_soft_start: (m, 3) start directions of refinement -- the best
+        direction of each ACCESSIBLE point of af_score's output, NaN for the
+        others."""
+        import torch
+        m = int(label.shape[0])
+        u0 = out if out is not None else \
+            torch.empty((m, 3), dtype=torch.float32, device=label.device)
+        z = C.c_void_p(0)
+        _check(self._lib.af_soft_start(self._h, _dev_ptr(label, torch.uint8) if m else z,
+                                       _dev_ptr(best, torch.int16) if m else z, m,
+                                       _dev_ptr(u0, torch.float32, (3,)) if m else z,
+                                       _stream_ptr(stream)), self._h)
         return u0
 
     def _pair_ptrs(self, pts, u0, alpha, beta, h, per_point):
@@ -383,29 +400,33 @@ class Map:
         return SoftClearance.apply(self, pts, u0, alpha, beta, h, per_point, tau_s)
 
     def soft_refine(self, pts, u0, alpha, beta, h, per_point=1, steps=20, lr_dir=0.05,
-                    lr_h=0.005, h_max=0.05, tau_s=TAU_S, stream=None):
+                    lr_h=0.005, h_max=0.05, tau_s=TAU_S, out=None, stream=None):
         """af_soft_refine: `steps` ascent steps on every pair in one launch;
         alpha, beta, h are updated in place. Returns (C, hard clearance)."""
         import torch
         n, ptr = self._pair_ptrs(pts, u0, alpha, beta, h, per_point)
         R = _Refine(steps, lr_dir, lr_h, h_max)
-        c = torch.empty(n, dtype=torch.float32, device=u0.device)
-        cmin = torch.empty(n, dtype=torch.float32, device=u0.device)
+        c, cmin = out if out is not None else \
+            (torch.empty(n, dtype=torch.float32, device=u0.device),
+             torch.empty(n, dtype=torch.float32, device=u0.device))
         op = [_dev_ptr(t, torch.float32) if n else C.c_void_p(0) for t in (c, cmin)]
         _check(self._lib.af_soft_refine(self._h, ptr[0], per_point, *ptr[1:], n, tau_s,
                                         C.byref(R), *op, _stream_ptr(stream)), self._h)
         return c, cmin
 
-    def soft_best(self, c, per_point, u0=None, stream=None):
+    def soft_best(self, c, per_point, u0=None, out=None, stream=None):
         """af_soft_best: per point (index of its largest C, that C, and --
         with u0 -- that pair's base direction)."""
         import torch
         n = int(c.shape[0])
         npts = (n + per_point - 1) // per_point
-        bk = torch.empty(npts, dtype=torch.int32, device=c.device)
-        bc = torch.empty(npts, dtype=torch.float32, device=c.device)
-        bu = torch.empty((npts, 3), dtype=torch.float32, device=c.device) if u0 is not None \
-            else None
+        if out is not None:
+            bk, bc, bu = out
+        else:
+            bk = torch.empty(npts, dtype=torch.int32, device=c.device)
+            bc = torch.empty(npts, dtype=torch.float32, device=c.device)
+            bu = torch.empty((npts, 3), dtype=torch.float32, device=c.device) \
+                if u0 is not None else None
         z = C.c_void_p(0)
         _check(self._lib.af_soft_best(self._h, _dev_ptr(c, torch.float32) if n else z, n,
                                       per_point, _dev_ptr(u0, torch.float32, (3,))

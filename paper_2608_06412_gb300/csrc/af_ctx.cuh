@@ -37,8 +37,9 @@ struct af_ctx {
   float4* d_cells = nullptr;
   bool views_valid = false;
   uint32_t views_frame = 0;
-  float* d_table = nullptr;  // seed directions
+  float* d_table = nullptr;  // seed directions, and their host copy
   uint32_t table_cap = 0;
+  std::vector<float> h_table;
   // host counters
   uint64_t scans = 0, returns_in = 0, points_in = 0;
   // kernel profiling: CUDA events around each launch on its own stream

@@ -40,6 +40,9 @@ cudaError_t launch_soft_refine(const SoftView& S, const RefineArgs& R, const flo
 cudaError_t launch_soft_best(const float* c, uint64_t n, uint32_t per_point, const float* u0,
                              int32_t* best_k, float* best_c, float* best_u0, int num_sms,
                              cudaStream_t stream);
+cudaError_t launch_soft_start(const uint8_t* label, const int16_t* best, uint32_t m,
+                              const float* dirs, int G, float* u0, int num_sms,
+                              cudaStream_t stream);
 }  // namespace af
 
 using af::MapView;
@@ -713,6 +716,16 @@ static af_status soft_view(af_ctx* ctx, float tau_s, af::SoftView* S) {
   S->J = J;
   S->k2 = (float)(1.4426950408889634 / (double)tau_s);
   S->ln2_tau_s = (float)(0.6931471805599453 * (double)tau_s);
+  // phi = SDF - margin lies in [-max margin, tau - min margin] (the TSDF is
+  // clamped to [0, tau]); weights against the lower bound then span at most
+  // 2^-E, and below E = 96 no weight underflows single precision.
+  const double mx = std::max(t.radius, t.corr_radius), mnm = std::min(t.radius, t.corr_radius);
+  const double E = ((double)ctx->cfg.truncation + 1e-3 + mx - mnm) * 1.4426950408889634 / (double)tau_s;
+  S->fixed = E <= 96.0 ? 1 : 0;
+  S->ref = (float)-mx;
+  const uint64_t cells = (uint64_t)S->ncell[0] * S->ncell[1] * S->ncell[2];
+  if (cells >= (1ull << 31))
+    return fail(ctx, AF_ERR_CAPACITY, "soft clearance: the map box has too many cells for the SDF view");
   return AF_OK;
 }
 
@@ -736,20 +749,26 @@ extern "C" af_status af_soft_seed(af_ctx* ctx, const float* d_normals, uint32_t 
   for (uint32_t k = 0; k < 3 * K; ++k)
     if (!std::isfinite(h_table[k])) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_seed: non-finite table");
   cudaStream_t s = (cudaStream_t)stream;
-  if (K > ctx->table_cap) {
-    AF_CUDA(ctx, cudaStreamSynchronize(s));
-    cudaFree(ctx->d_table);
-    ctx->d_table = nullptr;
-    ctx->table_cap = 0;
-    AF_CUDA(ctx, cudaMalloc(&ctx->d_table, (size_t)K * 3 * sizeof(float)));
-    ctx->table_cap = K;
+  const bool same = ctx->h_table.size() == (size_t)K * 3 &&
+                    std::memcmp(ctx->h_table.data(), h_table, (size_t)K * 3 * sizeof(float)) == 0;
+  if (!same) {
+    // the previous table may still be read by earlier launches
+    AF_CUDA(ctx, cudaDeviceSynchronize());
+    if (K > ctx->table_cap) {
+      cudaFree(ctx->d_table);
+      ctx->d_table = nullptr;
+      ctx->table_cap = 0;
+      AF_CUDA(ctx, cudaMalloc(&ctx->d_table, (size_t)K * 3 * sizeof(float)));
+      ctx->table_cap = K;
+    }
+    AF_CUDA(ctx, cudaMemcpy(ctx->d_table, h_table, (size_t)K * 3 * sizeof(float),
+                            cudaMemcpyHostToDevice));
+    ctx->h_table.assign(h_table, h_table + (size_t)K * 3);
   }
-  AF_CUDA(ctx, cudaMemcpyAsync(ctx->d_table, h_table, (size_t)K * 3 * sizeof(float),
-                               cudaMemcpyHostToDevice, s));
-  AF_CUDA(ctx, af::launch_soft_seed(d_normals, m, ctx->d_table, K, d_u0, ctx->num_sms, s));
-  // the table is reused by the next call: keep this call's copy alive until
-  // its kernel has read it
-  AF_CUDA(ctx, cudaStreamSynchronize(s));
+  AF_CUDA(ctx, timed(ctx, 8, s, [&] {
+    return af::launch_soft_seed(d_normals, m, ctx->d_table, K, d_u0, ctx->num_sms, s);
+  }));
+  ctx->last_stream = s;
   return AF_OK;
 }
 
@@ -829,8 +848,24 @@ extern "C" af_status af_soft_best(af_ctx* ctx, const float* d_c, uint64_t n, uin
   if (n > 0 && (!d_c || (d_best_u0 && !d_u0)))
     return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_best: NULL input");
   cudaStream_t s = (cudaStream_t)stream;
-  AF_CUDA(ctx, af::launch_soft_best(d_c, n, per_point, d_u0, d_best_k, d_best_c, d_best_u0,
-                                    ctx->num_sms, s));
+  AF_CUDA(ctx, timed(ctx, 9, s, [&] {
+    return af::launch_soft_best(d_c, n, per_point, d_u0, d_best_k, d_best_c, d_best_u0,
+                                ctx->num_sms, s);
+  }));
+  ctx->last_stream = s;
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_start(af_ctx* ctx, const uint8_t* d_label, const int16_t* d_best,
+                                   uint32_t m, float* d_u0, void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_soft_start: NULL context");
+  if (!ctx->has_tool) return fail(ctx, AF_ERR_STATE, "af_soft_start: call af_set_tool first");
+  if (m > 0 && (!d_label || !d_best || !d_u0))
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_start: NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  AF_CUDA(ctx, timed(ctx, 8, s, [&] {
+    return af::launch_soft_start(d_label, d_best, m, ctx->T.dirs, ctx->T.G, d_u0, ctx->num_sms, s);
+  }));
   ctx->last_stream = s;
   return AF_OK;
 }

@@ -188,6 +188,8 @@ struct SoftView {
   int j0, jt, J;        // samples j0..J; tool margin for j <= jt
   float k2;             // log2(e) / tau_s
   float ln2_tau_s;      // tau_s ln 2
+  int fixed;            // 1: softmin weights against the fixed bound `ref`
+  float ref;            // lower bound of every phi: -max(r, r_corr)
 };
 
 struct RefineArgs {

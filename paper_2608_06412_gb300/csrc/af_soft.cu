@@ -106,92 +106,137 @@ __device__ inline void onb(const float n[3], float t1[3], float t2[3]) {
   t2[2] = -n[1];
 }
 
-struct Pair {
-  float I[3];          // cell of the point on the sample grid (g = x / v - 1/2)
-  float r[3];          // the point's offset in that cell
-  float u[3];          // unit direction
-  float e;             // h / v
+// The point's cell on the sample grid (g = x / v - 1/2) and its offset r in
+// it, once per pair. `ok` is false for a point whose cell is not a usable
+// integer (then every sample reads as outside the view).
+struct PointCell {
+  float I[3], r[3];
+  bool finite, ok;
+};
+
+__device__ inline PointCell point_cell(const SoftView& S, const float s[3]) {
+  PointCell pc;
+  pc.finite = isfinite(s[0]) && isfinite(s[1]) && isfinite(s[2]);
+  pc.ok = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float o = __fsub_rn(__fdiv_rn(s[i], S.v), 0.5f);
+    pc.I[i] = floorf(o);
+    pc.r[i] = __fsub_rn(o, pc.I[i]);
+    pc.ok = pc.ok && fabsf(pc.I[i]) < 1.0e9f;
+  }
+  return pc;
+}
+
+// The direction of (alpha, beta) around u0 and the standoff in voxels.
+struct Dir {
+  float u[3];            // unit direction
+  float e;               // h / v
   float dua[3], dub[3];  // du / dalpha, du / dbeta
   bool finite;
 };
 
-__device__ inline Pair make_pair(const SoftView& S, const float s[3], const float u0[3],
-                                 const float t1[3], const float t2[3], float al, float be,
-                                 float h) {
-  Pair P;
+__device__ inline Dir make_dir(const SoftView& S, const float u0[3], const float t1[3],
+                               const float t2[3], float al, float be, float h) {
+  Dir d;
   float q[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) q[i] = __fadd_rn(__fadd_rn(u0[i], __fmul_rn(al, t1[i])), __fmul_rn(be, t2[i]));
+  for (int i = 0; i < 3; ++i)
+    q[i] = __fadd_rn(__fadd_rn(u0[i], __fmul_rn(al, t1[i])), __fmul_rn(be, t2[i]));
   const float nq = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(q[0], q[0]), __fmul_rn(q[1], q[1])),
                                         __fmul_rn(q[2], q[2])));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    P.u[i] = __fdiv_rn(q[i], nq);
-    const float o = __fsub_rn(__fdiv_rn(s[i], S.v), 0.5f);
-    P.I[i] = floorf(o);
-    P.r[i] = __fsub_rn(o, P.I[i]);
-  }
-  P.e = __fdiv_rn(h, S.v);
-  const float ut1 = P.u[0] * t1[0] + P.u[1] * t1[1] + P.u[2] * t1[2];
-  const float ut2 = P.u[0] * t2[0] + P.u[1] * t2[1] + P.u[2] * t2[2];
+  for (int i = 0; i < 3; ++i) d.u[i] = __fdiv_rn(q[i], nq);
+  d.e = __fdiv_rn(h, S.v);
+  const float ut1 = d.u[0] * t1[0] + d.u[1] * t1[1] + d.u[2] * t1[2];
+  const float ut2 = d.u[0] * t2[0] + d.u[1] * t2[1] + d.u[2] * t2[2];
   const float inq = 1.0f / nq;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    P.dua[i] = (t1[i] - P.u[i] * ut1) * inq;
-    P.dub[i] = (t2[i] - P.u[i] * ut2) * inq;
+    d.dua[i] = (t1[i] - d.u[i] * ut1) * inq;
+    d.dub[i] = (t2[i] - d.u[i] * ut2) * inq;
   }
-  bool fin = isfinite(al) && isfinite(be) && isfinite(h);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) fin = fin && isfinite(s[i]) && isfinite(u0[i]);
-  P.finite = fin;
-  return P;
+  d.finite = isfinite(al) && isfinite(be) && isfinite(h) && isfinite(u0[0]) &&
+             isfinite(u0[1]) && isfinite(u0[2]);
+  return d;
 }
 
-// Corner record of sample j: false when the cell lies outside the view (all
-// corners read tau). f receives the fractional position in the cell.
-__device__ inline bool sample_cell(const SoftView& S, const Pair& P, int j, float f[3],
-                                   size_t* idx) {
-  const float t = __fadd_rn(P.e, (float)j);
+// Cell record index of sample j: false when the cell lies outside the view
+// (all corners read tau). f receives the fractional position in the cell.
+__device__ inline bool sample_cell(const SoftView& S, const PointCell& pc, const Dir& d, int j,
+                                   float f[3], uint32_t* idx) {
+  const float t = __fadd_rn(d.e, (float)j);
   int c[3];
-  bool in = true;
+  bool in = pc.ok;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float l = __fadd_rn(P.r[i], __fmul_rn(t, P.u[i]));
+    const float l = __fadd_rn(pc.r[i], __fmul_rn(t, d.u[i]));
     const float fl = floorf(l);
     f[i] = l - fl;  // exact
-    const bool ok = fabsf(l) < 1.0e7f && fabsf(P.I[i]) < 1.0e9f;
-    c[i] = ok ? (int)P.I[i] + (int)fl - S.lo[i] : -1;
+    const bool ok = fabsf(l) < 1.0e7f;
+    c[i] = ok ? (int)pc.I[i] + (int)fl - S.lo[i] : -1;
     in = in && ok && (unsigned)c[i] < (unsigned)S.ncell[i];
   }
-  *idx = ((size_t)c[2] * S.ncell[1] + c[1]) * S.ncell[0] + c[0];
+  *idx = ((uint32_t)c[2] * (uint32_t)S.ncell[1] + (uint32_t)c[1]) * (uint32_t)S.ncell[0] +
+         (uint32_t)c[0];
   return in;
 }
 
 __device__ inline float lerp(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
-// Online softmin over the samples; with GRAD also the weighted sums
-// sum w_j (h/v + j) G_j and sum w_j G_j of the per-voxel SDF gradients G_j.
-template <bool GRAD>
+__device__ inline float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ inline float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Pairs are split across kLanes adjacent lanes: lane g of a pair's group
+// takes the samples j0 + g, j0 + g + kLanes, ... and the group merges its
+// partial softmin states in a fixed tree onto its first lane, whose result is
+// broadcast. Every soft kernel uses the same split, so a pair's C is the same
+// bit for bit whichever kernel computes it.
+constexpr int kLanes = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Softmin state over samples. With FIXED the weights are taken against a
+// fixed lower bound `ref` of every phi (no rescaling; the host picks FIXED
+// only when the exponents cannot underflow), otherwise against the running
+// minimum. m = min phi, Z = sum of exp(-(phi - base) / tau_s), and with GRAD
+// the weighted sums sum w_j (h/v + j) G_j and sum w_j G_j of the per-voxel
+// SDF gradients G_j.
+template <bool GRAD, bool FIXED>
 struct Softmin {
   float m = INFINITY, Z = 0.f;
   float at[3] = {0.f, 0.f, 0.f}, a0[3] = {0.f, 0.f, 0.f};
 
-  __device__ inline void add(float phi, float t, const float G[3], float k2) {
-    float w;
-    if (phi < m) {
-      const float sc = exp2f((phi - m) * k2);
-      Z *= sc;
-      if (GRAD) {
+  __device__ inline void scale(float sc) {
+    Z *= sc;
+    if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          at[i] *= sc;
-          a0[i] *= sc;
-        }
+      for (int i = 0; i < 3; ++i) {
+        at[i] *= sc;
+        a0[i] *= sc;
       }
+    }
+  }
+
+  __device__ inline void add(float phi, float t, const float G[3], const SoftView& S) {
+    float w;
+    if (FIXED) {
+      w = ex2((S.ref - phi) * S.k2);
+      m = fminf(m, phi);
+    } else if (phi < m) {
+      scale(ex2((phi - m) * S.k2));
       m = phi;
       w = 1.0f;
     } else {
-      w = exp2f((m - phi) * k2);
+      w = ex2((m - phi) * S.k2);
     }
     Z += w;
     if (GRAD) {
@@ -203,43 +248,123 @@ struct Softmin {
       }
     }
   }
+
+  // this <- this (+) o
+  __device__ inline void merge(const Softmin& o, float k2) {
+    float sa = 1.f, sb = 1.f;
+    const float mm = fminf(m, o.m);
+    if (!FIXED) {
+      sa = m == INFINITY ? 0.f : ex2((mm - m) * k2);
+      sb = o.m == INFINITY ? 0.f : ex2((mm - o.m) * k2);
+    }
+    Z = Z * sa + o.Z * sb;
+    if (GRAD) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        at[i] = at[i] * sa + o.at[i] * sb;
+        a0[i] = a0[i] * sa + o.a0[i] * sb;
+      }
+    }
+    m = mm;
+  }
+
+  // Merge the kLanes partial states of the group; every lane gets the result.
+  __device__ inline void reduce(float k2) {
+#pragma unroll
+    for (int off = kLanes / 2; off >= 1; off >>= 1) {
+      Softmin o;
+      o.m = __shfl_down_sync(kFull, m, off, kLanes);
+      o.Z = __shfl_down_sync(kFull, Z, off, kLanes);
+      if (GRAD) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          o.at[i] = __shfl_down_sync(kFull, at[i], off, kLanes);
+          o.a0[i] = __shfl_down_sync(kFull, a0[i], off, kLanes);
+        }
+      }
+      merge(o, k2);
+    }
+    m = __shfl_sync(kFull, m, 0, kLanes);
+    Z = __shfl_sync(kFull, Z, 0, kLanes);
+    if (GRAD) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        at[i] = __shfl_sync(kFull, at[i], 0, kLanes);
+        a0[i] = __shfl_sync(kFull, a0[i], 0, kLanes);
+      }
+    }
+  }
 };
 
-// C of one pair and, with GRAD, dC / d(alpha, beta, h).
+// One corner record, 32 bytes, in one 256-bit read-only load.
+__device__ inline void load_cell(const SoftView& S, uint32_t idx, float4& lo, float4& hi) {
+  const float4* p = S.cells + 2 * (size_t)idx;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z),
+        "=f"(hi.w)
+      : "l"(p));
+}
+
+// Trilinear value (and with GRAD its per-voxel gradient) of one record.
 template <bool GRAD>
-__device__ inline float soft_eval(const SoftView& S, const Pair& P, float* ga, float* gb,
-                                  float* gh, float* cmin) {
-  Softmin<GRAD> sm;
-  for (int j = S.j0; j <= S.J; ++j) {
-    const float margin = j <= S.jt ? S.r : S.r_corr;
-    float f[3];
-    size_t idx;
-    float D, G[3] = {0.f, 0.f, 0.f};
-    if (sample_cell(S, P, j, f, &idx)) {
-      const float4 lo = __ldg(S.cells + 2 * idx), hi = __ldg(S.cells + 2 * idx + 1);
-      const float dx00 = lo.y - lo.x, dx10 = lo.w - lo.z, dx01 = hi.y - hi.x, dx11 = hi.w - hi.z;
-      const float a00 = __fmaf_rn(f[0], dx00, lo.x), a10 = __fmaf_rn(f[0], dx10, lo.z);
-      const float a01 = __fmaf_rn(f[0], dx01, hi.x), a11 = __fmaf_rn(f[0], dx11, hi.z);
-      const float dy0 = a10 - a00, dy1 = a11 - a01;
-      const float b0 = __fmaf_rn(f[1], dy0, a00), b1 = __fmaf_rn(f[1], dy1, a01);
-      D = __fmaf_rn(f[2], b1 - b0, b0);
-      if (GRAD) {
-        G[0] = lerp(lerp(dx00, dx10, f[1]), lerp(dx01, dx11, f[1]), f[2]);
-        G[1] = lerp(dy0, dy1, f[2]);
-        G[2] = b1 - b0;
-      }
-    } else {
-      D = S.tau;
-    }
-    sm.add(D - margin, P.e + (float)j, G, S.k2);
+__device__ inline float trilinear(const float4& lo, const float4& hi, const float f[3],
+                                  float G[3]) {
+  const float dx00 = lo.y - lo.x, dx10 = lo.w - lo.z, dx01 = hi.y - hi.x, dx11 = hi.w - hi.z;
+  const float a00 = __fmaf_rn(f[0], dx00, lo.x), a10 = __fmaf_rn(f[0], dx10, lo.z);
+  const float a01 = __fmaf_rn(f[0], dx01, hi.x), a11 = __fmaf_rn(f[0], dx11, hi.z);
+  const float dy0 = a10 - a00, dy1 = a11 - a01;
+  const float b0 = __fmaf_rn(f[1], dy0, a00), b1 = __fmaf_rn(f[1], dy1, a01);
+  if (GRAD) {
+    G[0] = lerp(lerp(dx00, dx10, f[1]), lerp(dx01, dx11, f[1]), f[2]);
+    G[1] = lerp(dy0, dy1, f[2]);
+    G[2] = b1 - b0;
   }
-  const float C = sm.m - S.ln2_tau_s * log2f(sm.Z);
+  return __fmaf_rn(f[2], b1 - b0, b0);
+}
+
+// Records in flight per lane: the lane computes kInFlight sample cells,
+// issues their loads, then folds them into the softmin in sample order.
+constexpr int kInFlight = 2;
+
+// C of one pair and, with GRAD, dC / d(alpha, beta, h); *cmin = min_j phi_j.
+// Called by all kLanes lanes of the pair's group (lane g of it); with
+// `live` false the lane samples nothing.
+template <bool GRAD, bool FIXED>
+__device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const Dir& d, bool live,
+                                  int g, float* ga, float* gb, float* gh, float* cmin) {
+  Softmin<GRAD, FIXED> sm;
+  if (live) {
+    for (int j = S.j0 + g; j <= S.J; j += kInFlight * kLanes) {
+      float f[kInFlight][3];
+      uint32_t id[kInFlight];
+      bool has[kInFlight], in[kInFlight];
+#pragma unroll
+      for (int q = 0; q < kInFlight; ++q) {
+        has[q] = j + q * kLanes <= S.J;
+        in[q] = has[q] && sample_cell(S, pc, d, j + q * kLanes, f[q], &id[q]);
+      }
+      float4 lo[kInFlight], hi[kInFlight];
+#pragma unroll
+      for (int q = 0; q < kInFlight; ++q)
+        if (in[q]) load_cell(S, id[q], lo[q], hi[q]);
+#pragma unroll
+      for (int q = 0; q < kInFlight; ++q) {
+        if (!has[q]) break;
+        const int jq = j + q * kLanes;
+        float G[3] = {0.f, 0.f, 0.f};
+        const float D = in[q] ? trilinear<GRAD>(lo[q], hi[q], f[q], G) : S.tau;
+        sm.add(D - (jq <= S.jt ? S.r : S.r_corr), d.e + (float)jq, G, S);
+      }
+    }
+  }
+  sm.reduce(S.k2);
+  const float C = (FIXED ? S.ref : sm.m) - S.ln2_tau_s * lg2(sm.Z);
   *cmin = sm.m;
   if (GRAD) {
     const float iz = 1.0f / sm.Z;
-    *ga = (sm.at[0] * P.dua[0] + sm.at[1] * P.dua[1] + sm.at[2] * P.dua[2]) * iz;
-    *gb = (sm.at[0] * P.dub[0] + sm.at[1] * P.dub[1] + sm.at[2] * P.dub[2]) * iz;
-    *gh = (sm.a0[0] * P.u[0] + sm.a0[1] * P.u[1] + sm.a0[2] * P.u[2]) * iz / S.v;
+    *ga = (sm.at[0] * d.dua[0] + sm.at[1] * d.dua[1] + sm.at[2] * d.dua[2]) * iz;
+    *gb = (sm.at[0] * d.dub[0] + sm.at[1] * d.dub[1] + sm.at[2] * d.dub[2]) * iz;
+    *gh = (sm.a0[0] * d.u[0] + sm.a0[1] * d.u[1] + sm.a0[2] * d.u[2]) * iz / S.v;
   }
   return C;
 }
@@ -251,7 +376,7 @@ __device__ inline void load3(const float* __restrict__ p, size_t i, float o[3]) 
 }
 
 // ---------------------------------------------------------------------------
-// Kernels: one thread per pair, pairs of a point adjacent
+// Kernels
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_soft_seed(const float* __restrict__ nrm, uint32_t m,
@@ -271,7 +396,23 @@ __global__ void __launch_bounds__(256) k_soft_seed(const float* __restrict__ nrm
   }
 }
 
-template <bool GRAD>
+// Pair groups of a warp, walked so that every lane of the warp takes the same
+// number of iterations (the group merges are warp-wide shuffles).
+struct GroupWalk {
+  size_t first, stride;
+  int g, slot;
+  __device__ GroupWalk() {
+    const int lane = threadIdx.x & 31;
+    g = lane % kLanes;
+    slot = lane / kLanes;
+    const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    first = warp * (32 / kLanes);
+    stride = warps * (32 / kLanes);
+  }
+};
+
+template <bool GRAD, bool FIXED>
 __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restrict__ pts,
                                               uint32_t per_point, const float* __restrict__ u0,
                                               const float* __restrict__ alpha,
@@ -280,28 +421,36 @@ __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restric
                                               const float* __restrict__ gc, float* __restrict__ c,
                                               float* __restrict__ cmin, float* __restrict__ ga,
                                               float* __restrict__ gb, float* __restrict__ gh) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const GroupWalk w;
+  for (size_t base = w.first; base < n; base += w.stride) {
+    const size_t i0 = base + w.slot;
+    const bool act = i0 < n;
+    const size_t i = act ? i0 : n - 1;
     float s[3], u[3], t1[3], t2[3];
     load3(pts, i / per_point, s);
     load3(u0, i, u);
     onb(u, t1, t2);
-    const Pair P = make_pair(S, s, u, t1, t2, __ldg(alpha + i), __ldg(beta + i), __ldg(hh + i));
-    float da = 0.f, db = 0.f, dh = 0.f, mn;
-    float C = soft_eval<GRAD>(S, P, &da, &db, &dh, &mn);
-    if (!P.finite) C = mn = da = db = dh = NAN;
+    const PointCell pc = point_cell(S, s);
+    const Dir d = make_dir(S, u, t1, t2, __ldg(alpha + i), __ldg(beta + i), __ldg(hh + i));
+    const bool fin = pc.finite && d.finite;
+    float da, db, dh, mn;
+    float C = soft_eval<GRAD, FIXED>(S, pc, d, fin && act, w.g, &da, &db, &dh, &mn);
+    if (!act || w.g != 0) continue;
+    if (!fin) C = mn = da = db = dh = NAN;
     if (c) c[i] = C;
     if (cmin) cmin[i] = mn;
     if (GRAD) {
-      const float g = gc ? __ldg(gc + i) : 1.0f;
-      if (ga) ga[i] = g * da;
-      if (gb) gb[i] = g * db;
-      if (gh) gh[i] = g * dh;
+      const float gg = gc ? __ldg(gc + i) : 1.0f;
+      if (ga) ga[i] = gg * da;
+      if (gb) gb[i] = gg * db;
+      if (gh) gh[i] = gg * dh;
     }
   }
 }
 
 // `steps` ascent steps on C per pair in registers, then C at the final state.
+// The group's lanes update identical copies of (alpha, beta, h).
+template <bool FIXED>
 __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
                                                      const float* __restrict__ pts,
                                                      uint32_t per_point,
@@ -311,30 +460,55 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
                                                      float* __restrict__ hh, uint64_t n,
                                                      float* __restrict__ c,
                                                      float* __restrict__ cmin) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const GroupWalk w;
+  for (size_t base = w.first; base < n; base += w.stride) {
+    const size_t i0 = base + w.slot;
+    const bool act = i0 < n;
+    const size_t i = act ? i0 : n - 1;
     float s[3], u[3], t1[3], t2[3];
     load3(pts, i / per_point, s);
     load3(u0, i, u);
     onb(u, t1, t2);
+    const PointCell pc = point_cell(S, s);
     float al = alpha[i], be = beta[i], h = hh[i];
+    // a pair that is not finite (e.g. a point with no start) samples nothing
+    const bool fin = pc.finite && make_dir(S, u, t1, t2, al, be, h).finite;
     for (int k = 0; k < R.steps; ++k) {
-      const Pair P = make_pair(S, s, u, t1, t2, al, be, h);
+      const Dir d = make_dir(S, u, t1, t2, al, be, h);
+      const bool live = fin && act && d.finite;
       float da, db, dh, mn;
-      soft_eval<true>(S, P, &da, &db, &dh, &mn);
-      al = __fmaf_rn(R.lr_dir, da, al);
-      be = __fmaf_rn(R.lr_dir, db, be);
-      h = fminf(fmaxf(__fmaf_rn(R.lr_h, dh, h), 0.0f), R.h_max);
+      soft_eval<true, FIXED>(S, pc, d, live, w.g, &da, &db, &dh, &mn);
+      if (live) {
+        al = __fmaf_rn(R.lr_dir, da, al);
+        be = __fmaf_rn(R.lr_dir, db, be);
+        h = fminf(fmaxf(__fmaf_rn(R.lr_h, dh, h), 0.0f), R.h_max);
+      }
     }
-    const Pair P = make_pair(S, s, u, t1, t2, al, be, h);
+    const Dir d = make_dir(S, u, t1, t2, al, be, h);
+    const bool ok = fin && d.finite;
     float mn;
-    float C = soft_eval<false>(S, P, nullptr, nullptr, nullptr, &mn);
-    if (!P.finite) C = mn = al = be = h = NAN;
+    float C = soft_eval<false, FIXED>(S, pc, d, ok && act, w.g, nullptr, nullptr, nullptr, &mn);
+    if (!act || w.g != 0) continue;
+    if (!ok) C = mn = al = be = h = NAN;
     alpha[i] = al;
     beta[i] = be;
     hh[i] = h;
     c[i] = C;
     if (cmin) cmin[i] = mn;
+  }
+}
+
+// Start of each point's refinement from the plain path's result: the best
+// direction of an ACCESSIBLE point, NaN otherwise (refinement skips it).
+__global__ void __launch_bounds__(256) k_soft_start(const uint8_t* __restrict__ label,
+                                                    const int16_t* __restrict__ best, uint32_t m,
+                                                    const float* __restrict__ dirs, int G,
+                                                    float* __restrict__ u0) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < m; p += gridDim.x * blockDim.x) {
+    const int b = best[p];
+    const bool ok = label[p] == 1 && b >= 0 && b < G;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u0[3 * p + d] = ok ? __ldg(dirs + 3 * b + d) : NAN;
   }
 }
 
@@ -402,13 +576,19 @@ cudaError_t launch_soft(const SoftView& S, bool grad, const float* pts, uint32_t
                         uint64_t n, const float* gc, float* c, float* cmin, float* ga,
                         float* gb, float* gh, int num_sms, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
-  const unsigned g = grid_for(n, 128, num_sms, 16);
-  if (grad)
-    k_soft<true><<<g, 128, 0, stream>>>(S, pts, per_point, u0, al, be, h, n, gc, c, cmin, ga, gb,
-                                        gh);
+  const unsigned g = grid_for(n * kLanes, 128, num_sms, 16);
+#define AF_SOFT_LAUNCH(GR, FX)                                                                 \
+  k_soft<GR, FX><<<g, 128, 0, stream>>>(S, pts, per_point, u0, al, be, h, n, gc, c, cmin, ga,  \
+                                        gb, gh)
+  if (grad && S.fixed)
+    AF_SOFT_LAUNCH(true, true);
+  else if (grad)
+    AF_SOFT_LAUNCH(true, false);
+  else if (S.fixed)
+    AF_SOFT_LAUNCH(false, true);
   else
-    k_soft<false><<<g, 128, 0, stream>>>(S, pts, per_point, u0, al, be, h, n, nullptr, c, cmin,
-                                         nullptr, nullptr, nullptr);
+    AF_SOFT_LAUNCH(false, false);
+#undef AF_SOFT_LAUNCH
   return cudaGetLastError();
 }
 
@@ -417,8 +597,19 @@ cudaError_t launch_soft_refine(const SoftView& S, const RefineArgs& R, const flo
                                float* h, uint64_t n, float* c, float* cmin, int num_sms,
                                cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
-  k_soft_refine<<<grid_for(n, 128, num_sms, 16), 128, 0, stream>>>(S, R, pts, per_point, u0, al,
-                                                                    be, h, n, c, cmin);
+  const unsigned g = grid_for(n * kLanes, 128, num_sms, 16);
+  if (S.fixed)
+    k_soft_refine<true><<<g, 128, 0, stream>>>(S, R, pts, per_point, u0, al, be, h, n, c, cmin);
+  else
+    k_soft_refine<false><<<g, 128, 0, stream>>>(S, R, pts, per_point, u0, al, be, h, n, c, cmin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_soft_start(const uint8_t* label, const int16_t* best, uint32_t m,
+                              const float* dirs, int G, float* u0, int num_sms,
+                              cudaStream_t stream) {
+  if (m == 0) return cudaSuccess;
+  k_soft_start<<<grid_for(m, 256, num_sms, 8), 256, 0, stream>>>(label, best, m, dirs, G, u0);
   return cudaGetLastError();
 }
 

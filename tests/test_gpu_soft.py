@@ -242,3 +242,26 @@ def test_argument_errors(scene):
     e1 = torch.empty(0, dtype=torch.float32, device="cuda")
     assert g.soft_clearance_raw(e0, e0, e1, e1, e1, 4).numel() == 0
     assert g.soft_refine(e0, e0, e1, e1, e1, 4)[0].numel() == 0
+
+
+def test_start_from_plain_best(scene):
+    """Refinement starts from the plain path's result: the best direction of
+    each accessible point, NaN (skipped, NaN outputs) for the others."""
+    import torch
+    W, fr, g, om, P, N, table, u0, al, be, h = scene
+    lab, best = g.score(_gpu(P), _gpu(N))
+    start = g.soft_start(lab, best).cpu().numpy()
+    lab_h, best_h = lab.cpu().numpy(), best.cpu().numpy()
+    acc = lab_h == af.ACCESSIBLE
+    assert acc.any() and (~acc).any()
+    np.testing.assert_array_equal(start[acc], W.dirs[best_h[acc]])
+    assert np.isnan(start[~acc]).all()
+    z = np.zeros(len(P), np.float32)
+    A, B, H = _gpu(z), _gpu(z), _gpu(z)
+    c, cmin = g.soft_refine(_gpu(P), _gpu(start), A, B, H, 1, steps=20)
+    c = c.cpu().numpy()
+    assert np.isnan(c[~acc]).all() and np.isfinite(c[acc]).all()
+    assert np.isnan(A.cpu().numpy()[~acc]).all()
+    ra, rb, rh, rc, rm = om.soft_refine(oracle_tool(W), P[acc], 1, W.dirs[best_h[acc]],
+                                        z[acc], z[acc], z[acc], 20, 0.05, 0.005, 0.05)
+    assert (np.abs(c[acc] - rc) <= 1e-5).mean() >= 0.99
