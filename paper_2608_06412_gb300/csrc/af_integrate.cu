@@ -24,7 +24,6 @@
 // it, so the result is reproducible bit for bit on any IEEE machine; where a
 // cheaper approximate value is used, it only takes decisions that the exact
 // value is certain to agree with (margins of 2^-16).
-#include <cooperative_groups.h>
 
 #include "af_internal.cuh"
 
@@ -69,20 +68,22 @@ __device__ uint32_t insert_brick(const MapView& M, uint64_t key, uint32_t* slot,
 
 // Appends blk (hash slot h, whose stamp was read as `seen`) to the scan's
 // dirty list once per scan: the stamp decides which thread appends. Appends
-// are aggregated over the threads that call together: one counter atomic per
-// group instead of one per brick.
+// are aggregated over the threads of the same map (`group`) that call
+// together: one counter atomic per map and call instead of one per brick.
+// Threads of different maps may call together (batched ticks), and each
+// map's appends go through its own counter.
 __device__ inline void mark_dirty(const MapView& M, uint32_t h, uint32_t blk, uint32_t frame,
-                                  uint32_t seen) {
-  namespace cg = cooperative_groups;
-  const cg::coalesced_group g = cg::coalesced_threads();
+                                  uint32_t seen, uint32_t group) {
+  const unsigned active = __activemask();
+  const unsigned same = __match_any_sync(active, group);
   const bool need = seen != frame && atomicExch(&M.slots[h].stamp, frame) != frame;
-  const unsigned nm = g.ballot(need);
-  if (nm == 0u) return;
-  const int first = __ffs(nm) - 1;
+  const unsigned nm = __ballot_sync(active, need) & same;
+  const int lane = threadIdx.x & 31;
+  const int first = nm ? __ffs(nm) - 1 : lane;
   uint32_t base = 0;
-  if ((int)g.thread_rank() == first) base = atomicAdd(&M.ctl->dirty_count, (unsigned)__popc(nm));
-  base = g.shfl(base, first);
-  if (need) M.dirty[base + __popc(nm & ((1u << g.thread_rank()) - 1u))] = blk;
+  if (nm && lane == first) base = atomicAdd(&M.ctl->dirty_count, (unsigned)__popc(nm));
+  base = __shfl_sync(active, base, first);
+  if (need) M.dirty[base + __popc(nm & ((1u << lane) - 1u))] = blk;
 }
 
 // Cube bricks of a return: first brick b0 and count nb per axis.
@@ -156,7 +157,7 @@ __device__ void alloc_slot(const MapView& M, const float* __restrict__ xyz, uint
     if (lane == leader) {
       uint32_t h, seen;
       blk = insert_brick(M, key, &h, &seen);
-      if (blk != kNoBlock) mark_dirty(M, h, blk, frame, seen);
+      if (blk != kNoBlock) mark_dirty(M, h, blk, frame, seen, group);
     }
     blk = __shfl_sync(peers, blk, leader);
   }
@@ -250,7 +251,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
         uint32_t val, seen;
         const int h = find_slot(M, pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz), &val, &seen);
         blk = (h >= 0 && val < M.pool_blocks) ? val : kNoBlock;
-        if (blk != kNoBlock) mark_dirty(M, (uint32_t)h, blk, frame, seen);
+        if (blk != kNoBlock) mark_dirty(M, (uint32_t)h, blk, frame, seen, 0u);
       }
     }
     s_blk[t][j] = blk;
@@ -337,7 +338,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     if (h < 0 || blk >= M.pool_blocks) continue;
     const int l = (sv[0] & 7) | ((sv[1] & 7) << 3) | ((sv[2] & 7) << 6);
     atomicOr(M.cleared + blk * 16 + (l >> 5), 1u << (l & 31));
-    mark_dirty(M, (uint32_t)h, blk, frame, seen);
+    mark_dirty(M, (uint32_t)h, blk, frame, seen, 0u);
   }
 }
 
