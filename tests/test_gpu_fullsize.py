@@ -77,3 +77,60 @@ def test_sampled_points_labels(stream, want):
     np.testing.assert_array_equal(lab[near], ol)
     np.testing.assert_array_equal(best[near], ob)
     assert (ol == want).any()
+
+
+SOFT_RADIUS = POINT_RADIUS + 0.05     # refinement may move the tool out by h_max
+
+
+@pytest.fixture(scope="module")
+def soft(stream):
+    """The differentiable step exactly as the benchmark runs it: the pine map
+    after 300 frames, 100k surface points, plain scoring, start from each
+    accessible point's best direction, 20 ascent steps."""
+    import torch
+    W, frames, _, _, _ = stream
+    fr300 = frames[:300]
+    P, N = workload.soft_points(fr300, W.params["v"], 100_000)
+    g = af.Map(W.af_config(**dict(workload.BENCH_CAPS, max_points=1 << 17)))
+    g.set_tool(W.af_tool(), W.dirs)
+    for fr, _, _ in fr300:
+        g.integrate_scan(to_dev(fr.pts), fr.pose)
+    Pd, Nd = to_dev(P), to_dev(N)
+    lab, best = g.score(Pd, Nd)
+    u0 = g.soft_start(lab, best)
+    z = torch.zeros(len(P), dtype=torch.float32, device="cuda")
+    c0 = g.soft_clearance_raw(Pd, u0, z, z, z, 1)
+    al, be, hh = z.clone(), z.clone(), z.clone()
+    c, cmin = g.soft_refine(Pd, u0, al, be, hh, 1, steps=20, lr_dir=0.05, lr_h=0.005, h_max=0.05)
+    torch.cuda.synchronize()
+    out = {k: t.cpu().numpy() for k, t in dict(lab=lab, best=best, c0=c0, al=al, be=be, h=hh,
+                                                 c=c, cmin=cmin).items()}
+    return W, fr300, P, N, out
+
+
+def test_sampled_soft_refinement(soft):
+    W, fr300, P, N, o = soft
+    acc = np.nonzero(o["lab"] == af.ACCESSIBLE)[0]
+    assert len(acc) > 50_000
+    rng = np.random.default_rng(11)
+    seed = rng.choice(acc)
+    near = np.nonzero(np.linalg.norm(P - P[seed], axis=1) < 0.25)[0][:30]
+    om = _oracle_near(W, fr300, P[near].astype(np.float64), SOFT_RADIUS)
+    tool = oracle_tool(W)
+    ol, ob = om.score(tool, W.dirs, P[near], N[near])
+    np.testing.assert_array_equal(o["lab"][near], ol)
+    np.testing.assert_array_equal(o["best"][near], ob)
+    a = ol == af.ACCESSIBLE
+    assert a.sum() >= 5
+    # non-accessible points are not refined
+    assert np.isnan(o["c"][near][~a]).all()
+    pts, u0 = P[near][a], W.dirs[ob[a]]
+    z = np.zeros(a.sum(), np.float32)
+    c0, _ = om.soft_clearance(tool, pts, 1, u0, z, z, z, af.TAU_S)
+    np.testing.assert_allclose(o["c0"][near][a], c0, rtol=0, atol=1e-5)
+    ra, rb, rh, rc, rm = om.soft_refine(tool, pts, 1, u0, z, z, z, 20, 0.05, 0.005, 0.05)
+    close = np.abs(o["c"][near][a] - rc) <= 1e-5
+    # a trajectory may part from the oracle's at a kink met within rounding
+    assert close.sum() >= len(close) - 1, np.abs(o["c"][near][a] - rc)
+    assert (np.abs(o["cmin"][near][a] - rm)[close] <= 1e-5).all()
+    assert (np.abs(o["h"][near][a] - rh)[close] <= 1e-4).all()
