@@ -130,9 +130,9 @@ __device__ inline PointCell point_cell(const SoftView& S, const float s[3]) {
 
 // The direction of (alpha, beta) around u0 and the standoff in voxels.
 struct Dir {
-  float u[3];            // unit direction
-  float e;               // h / v
-  float dua[3], dub[3];  // du / dalpha, du / dbeta
+  float u[3];  // unit direction
+  float e;     // h / v
+  float inq;   // 1 / |u0 + alpha t1 + beta t2|
   bool finite;
 };
 
@@ -148,14 +148,7 @@ __device__ inline Dir make_dir(const SoftView& S, const float u0[3], const float
 #pragma unroll
   for (int i = 0; i < 3; ++i) d.u[i] = __fdiv_rn(q[i], nq);
   d.e = __fdiv_rn(h, S.v);
-  const float ut1 = d.u[0] * t1[0] + d.u[1] * t1[1] + d.u[2] * t1[2];
-  const float ut2 = d.u[0] * t2[0] + d.u[1] * t2[1] + d.u[2] * t2[2];
-  const float inq = 1.0f / nq;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    d.dua[i] = (t1[i] - d.u[i] * ut1) * inq;
-    d.dub[i] = (t2[i] - d.u[i] * ut2) * inq;
-  }
+  d.inq = 1.0f / nq;
   d.finite = isfinite(al) && isfinite(be) && isfinite(h) && isfinite(u0[0]) &&
              isfinite(u0[1]) && isfinite(u0[2]);
   return d;
@@ -330,8 +323,9 @@ constexpr int kInFlight = 2;
 // Called by all kLanes lanes of the pair's group (lane g of it); with
 // `live` false the lane samples nothing.
 template <bool GRAD, bool FIXED>
-__device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const Dir& d, bool live,
-                                  int g, float* ga, float* gb, float* gh, float* cmin) {
+__device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const Dir& d,
+                                  const float t1[3], const float t2[3], bool live, int g,
+                                  float* ga, float* gb, float* gh, float* cmin) {
   Softmin<GRAD, FIXED> sm;
   if (live) {
     for (int j = S.j0 + g; j <= S.J; j += kInFlight * kLanes) {
@@ -361,9 +355,15 @@ __device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const 
   const float C = (FIXED ? S.ref : sm.m) - S.ln2_tau_s * lg2(sm.Z);
   *cmin = sm.m;
   if (GRAD) {
+    // du/dalpha = (t1 - u (u . t1)) / |q|, likewise for beta with t2
     const float iz = 1.0f / sm.Z;
-    *ga = (sm.at[0] * d.dua[0] + sm.at[1] * d.dua[1] + sm.at[2] * d.dua[2]) * iz;
-    *gb = (sm.at[0] * d.dub[0] + sm.at[1] * d.dub[1] + sm.at[2] * d.dub[2]) * iz;
+    const float au = sm.at[0] * d.u[0] + sm.at[1] * d.u[1] + sm.at[2] * d.u[2];
+    const float ut1 = d.u[0] * t1[0] + d.u[1] * t1[1] + d.u[2] * t1[2];
+    const float ut2 = d.u[0] * t2[0] + d.u[1] * t2[1] + d.u[2] * t2[2];
+    const float at1 = sm.at[0] * t1[0] + sm.at[1] * t1[1] + sm.at[2] * t1[2];
+    const float at2 = sm.at[0] * t2[0] + sm.at[1] * t2[1] + sm.at[2] * t2[2];
+    *ga = (at1 - au * ut1) * d.inq * iz;
+    *gb = (at2 - au * ut2) * d.inq * iz;
     *gh = (sm.a0[0] * d.u[0] + sm.a0[1] * d.u[1] + sm.a0[2] * d.u[2]) * iz / S.v;
   }
   return C;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restric
     const Dir d = make_dir(S, u, t1, t2, __ldg(alpha + i), __ldg(beta + i), __ldg(hh + i));
     const bool fin = pc.finite && d.finite;
     float da, db, dh, mn;
-    float C = soft_eval<GRAD, FIXED>(S, pc, d, fin && act, w.g, &da, &db, &dh, &mn);
+    float C = soft_eval<GRAD, FIXED>(S, pc, d, t1, t2, fin && act, w.g, &da, &db, &dh, &mn);
     if (!act || w.g != 0) continue;
     if (!fin) C = mn = da = db = dh = NAN;
     if (c) c[i] = C;
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
       const Dir d = make_dir(S, u, t1, t2, al, be, h);
       const bool live = fin && act && d.finite;
       float da, db, dh, mn;
-      soft_eval<true, FIXED>(S, pc, d, live, w.g, &da, &db, &dh, &mn);
+      soft_eval<true, FIXED>(S, pc, d, t1, t2, live, w.g, &da, &db, &dh, &mn);
       if (live) {
         al = __fmaf_rn(R.lr_dir, da, al);
         be = __fmaf_rn(R.lr_dir, db, be);
@@ -487,7 +487,8 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
     const Dir d = make_dir(S, u, t1, t2, al, be, h);
     const bool ok = fin && d.finite;
     float mn;
-    float C = soft_eval<false, FIXED>(S, pc, d, ok && act, w.g, nullptr, nullptr, nullptr, &mn);
+    float C = soft_eval<false, FIXED>(S, pc, d, t1, t2, ok && act, w.g, nullptr, nullptr, nullptr,
+                                      &mn);
     if (!act || w.g != 0) continue;
     if (!ok) C = mn = al = be = h = NAN;
     alpha[i] = al;

@@ -94,3 +94,42 @@ def test_batch_fixed_shape_and_argument_errors(scenes):
     with pytest.raises(af.AfError) as e:
         b2.tick(_items(S[:1], 0, empty=-1, no_points=-1))
     assert e.value.status == af.ERR_STATE
+
+
+def test_batch_many_tiny_scenes_share_warps():
+    """40 scenes of 2-12 returns: nearly every allocation warp holds lanes of
+    several maps, so per-map bookkeeping (dirty lists, counters) must not
+    mix maps. Maps and labels equal the per-scene path's after every tick."""
+    import torch
+    S = workload.batch_scenes(40, seed=17, n_lo=2, n_hi=12)
+    caps = dict(hash_capacity=1 << 12, pool_blocks=1 << 10, max_returns=64, max_points=64)
+    plain = [af.Map(W.af_config(**caps)) for W in S]
+    mapsb = [af.Map(W.af_config(**caps)) for W in S]
+    for W, a, b in zip(S, plain, mapsb):
+        a.set_tool(W.af_tool(), W.dirs)
+        b.set_tool(W.af_tool(), W.dirs)
+    batch = af.Batch(mapsb)
+    batch.set_tuning(8, 2)
+    rng = np.random.default_rng(3)
+    for f in range(6):
+        items = []
+        for W in S:
+            fr, pts, nrm = workload.pine_frame(W, f)
+            take = rng.choice(len(fr.pts), min(len(fr.pts), W.params["n_returns"]), replace=False)
+            pts, nrm = pts[:8], nrm[:8]
+            items.append((to_dev(fr.pts[take]), fr.pose, to_dev(pts), to_dev(nrm),
+                          torch.empty(len(pts), dtype=torch.uint8, device="cuda"),
+                          torch.empty(len(pts), dtype=torch.int16, device="cuda")))
+        batch.tick(items)
+        ref = []
+        for (xyz, pose, pts, nrm, _, _), mp in zip(items, plain):
+            mp.integrate_scan(xyz, pose)
+            ref.append(mp.score(pts, nrm))
+        torch.cuda.synchronize()
+        for s, (it, r) in enumerate(zip(items, ref)):
+            np.testing.assert_array_equal(it[4].cpu().numpy(), r[0].cpu().numpy(), f"tick {f} scene {s}")
+            np.testing.assert_array_equal(it[5].cpu().numpy(), r[1].cpu().numpy(), f"tick {f} scene {s}")
+        for s, (a, b) in enumerate(zip(plain, mapsb)):
+            va, vb = gpu_voxels(a), gpu_voxels(b)
+            for k in va:
+                np.testing.assert_array_equal(va[k], vb[k], f"tick {f} scene {s} field {k}")
