@@ -310,9 +310,10 @@ class Map:
         _check(self._lib.af_block_count(self._h, C.byref(n)), self._h)
         return int(n.value)
 
-    def export_blocks(self) -> dict:
-        """All allocated bricks: absolute brick keys and per-voxel S, w, flags."""
-        n = self.block_count()
+    def export_blocks(self, cap: int | None = None) -> dict:
+        """Allocated bricks (all, or the first `cap` in pool order): absolute
+        brick keys and per-voxel S, w, flags."""
+        n = self.block_count() if cap is None else min(cap, self.block_count())
         key = np.zeros((max(n, 1), 3), np.int32)
         S = np.zeros((max(n, 1), 512), np.uint64)
         w = np.zeros((max(n, 1), 512), np.uint32)

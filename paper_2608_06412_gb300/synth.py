@@ -51,6 +51,20 @@ PINE_STREAM = dict(
 )
 
 
+#: Large map: 8 pines on a noisy 40 x 40 m ground, the sensor orbiting each
+#: pine in turn (375 frames per pine, 3,000 frames), v = 1 cm, K = 256.
+LARGE_MAP = dict(
+    name="large_map_8_pines_40m_3000x20k_v1cm",
+    v=0.01, tau=0.04, r_c=0.005, cube_radius=4, clear_samples=10,
+    w_min=3, w_cap=2000, cone_cos=0.95, range_min=0.1, range_max=40.0,
+    clear_lo=1.0, clear_hi=2.25,
+    tool=dict(radius=0.04, length=0.25, self_excl=0.04, corr_radius=0.05,
+              corr_length=1.5, cos_theta_max=0.0, n_c=5, strict=0),
+    K=256, n_returns=20000, sigma=0.02, seed=5, frames=3000, frames_per_pine=375,
+    pines=8, ground_half=20.0, ground_tile=1.0, ground_sigma=0.02,
+    orbit_radius=3.0, orbit_height=2.0,
+)
+
 # ---------------------------------------------------------------------------
 # Counter-free RNG helpers
 # ---------------------------------------------------------------------------
@@ -126,6 +140,7 @@ class Scene:
     groups: list
     lo: np.ndarray   # axis-aligned bounds of all geometry
     hi: np.ndarray
+    clusters: list = None   # optional contiguous group ranges (start, end) culled together
 
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -150,17 +165,45 @@ def _raycaster():
     global _rc
     if _rc is None:
         lib = ctypes.CDLL(build_raycaster())
-        lib.sr_raycast.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 8 + \
+        lib.sr_raycast.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 10 + \
             [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _rc = lib
     return _rc
+
+
+def _seg_dist(p, a, b):
+    ab = b - a
+    ee = float(ab @ ab)
+    s = 0.0 if ee < 1e-18 else min(1.0, max(0.0, float((p - a) @ ab) / ee))
+    return float(np.linalg.norm(p - (a + s * ab)))
+
+
+def _cluster_capsule(groups):
+    """A vertical capsule through the groups' endpoints that encloses every
+    group capsule (distance to a segment is convex, so the farthest point of
+    a group capsule lies at an endpoint, plus its radius)."""
+    ends = np.array([e for g in groups for e in (g.a, g.b)], np.float64)
+    c = ends[:, :2].mean(0)
+    a = np.array([c[0], c[1], ends[:, 2].min()])
+    b = np.array([c[0], c[1], ends[:, 2].max()])
+    r = max(max(_seg_dist(g.a, a, b), _seg_dist(g.b, a, b)) + g.radius for g in groups)
+    return [*a, *b, r * (1 + 1e-9) + 1e-9]
 
 
 def _packed(scene: "Scene"):
     if getattr(scene, "_packed", None) is None:
         gs = scene.groups
         caps = np.array([[*g.a, *g.b, g.radius] for g in gs], np.float64).reshape(-1, 7)
-        out = [np.ascontiguousarray(caps)]
+        if scene.clusters:
+            ranges = list(scene.clusters)
+            assert ranges[0][0] == 0 and ranges[-1][1] == len(gs)
+            assert all(ranges[i][1] == ranges[i + 1][0] for i in range(len(ranges) - 1))
+            cl_caps = np.array([_cluster_capsule(gs[a:b]) for a, b in ranges], np.float64)
+            cl_off = np.array([r[0] for r in ranges] + [len(gs)], np.int64)
+        else:
+            cl_caps = np.array([[0, 0, 0, 0, 0, 0, np.inf]], np.float64)
+            cl_off = np.array([0, len(gs)], np.int64)
+        out = [np.ascontiguousarray(cl_caps), cl_off, np.ascontiguousarray(caps)]
         for attr, width in (("spheres", 4), ("boxes", 6), ("cylinders", 7)):
             arrs = [np.asarray(getattr(g, attr), np.float64).reshape(-1, width) for g in gs]
             off = np.zeros(len(gs) + 1, np.int64)
@@ -181,10 +224,10 @@ def raycast(scene: "Scene", o: np.ndarray, d: np.ndarray):
     nrm = np.zeros((n, 3))
     if n == 0 or not scene.groups:
         return t, nrm
-    caps, so, sp, bo, bx, co, cy = _packed(scene)
+    clc, clo, caps, so, sp, bo, bx, co, cy = _packed(scene)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    _raycaster().sr_raycast(len(scene.groups), p(caps), p(so), p(sp), p(bo), p(bx), p(co),
-                            p(cy), p(o), n, p(d), p(t), p(nrm))
+    _raycaster().sr_raycast(len(clc), p(clc), p(clo), p(caps), p(so), p(sp), p(bo), p(bx),
+                            p(co), p(cy), p(o), n, p(d), p(t), p(nrm))
     return t, nrm
 
 
@@ -260,6 +303,56 @@ class Frame:
     normal: np.ndarray    # (n,3) float64 analytic outward normal at each hit
 
 
+def pine_positions(seed: int, count: int, half: float):
+    """Pine positions: a jittered 4 x 2 grid over the square of half-width
+    `half` (x in 4 columns, y in 2 rows), jitter U(+-1 m)."""
+    g = rng(seed, 71)
+    cols, rows = 4, max(1, (count + 3) // 4)
+    out = []
+    for k in range(count):
+        cx = -half + (2 * half) * ((k % cols) + 0.5) / cols
+        cy = -half + (2 * half) * ((k // cols) + 0.5) / rows
+        out.append((cx + g.uniform(-1, 1), cy + g.uniform(-1, 1)))
+    return np.array(out)
+
+
+def forest_ground_scene(seed: int, count: int = 8, half: float = 20.0, tile: float = 1.0,
+                        ground_sigma: float = 0.02) -> Scene:
+    """`count` procedural pines (pine_scene(seed * 100 + k)) at
+    pine_positions, on a ground of square tiles of edge `tile` covering
+    [-half, half]^2, each tile's top at height N(0, ground_sigma); one group
+    per tile row."""
+    groups, clusters = [], []
+    for k, (cx, cy) in enumerate(pine_positions(seed, count, half)):
+        start = len(groups)
+        off = np.array([cx, cy, 0.0])
+        for gr in pine_scene(seed * 100 + k).groups:
+            sp = gr.spheres.copy()
+            if len(sp):
+                sp[:, :3] += off
+            cy_ = gr.cylinders.copy()
+            if len(cy_):
+                cy_[:, :3] += off
+                cy_[:, 3:6] += off
+            groups.append(Group(a=gr.a + off, b=gr.b + off, radius=gr.radius, spheres=sp,
+                                boxes=gr.boxes, cylinders=cy_))
+        clusters.append((start, len(groups)))
+    g = rng(seed, 73)
+    n = int(round(2 * half / tile))
+    for r in range(n):
+        y0 = -half + r * tile
+        tops = g.normal(0.0, ground_sigma, n)
+        boxes = np.array([[-half + c * tile, y0, -0.2, -half + (c + 1) * tile, y0 + tile, tops[c]]
+                          for c in range(n)])
+        zc, hz = (tops.max() - 0.2) / 2, (tops.max() + 0.2) / 2
+        groups.append(Group(a=np.array([-half, y0 + tile / 2, zc]),
+                            b=np.array([half, y0 + tile / 2, zc]),
+                            radius=math.hypot(tile / 2, hz) + 1e-3, boxes=boxes))
+        clusters.append((len(groups) - 1, len(groups)))
+    lo, hi = _bounds(groups)
+    return Scene(groups, lo, hi, clusters)
+
+
 def yaw_pose(origin, yaw: float) -> np.ndarray:
     c, s = math.cos(yaw), math.sin(yaw)
     T = np.eye(4)
@@ -313,14 +406,16 @@ def rosette_frame(scene: Scene, frame: int, seed: int, n_hits: int = 20000,
                   sigma: float = 0.02, orbit_radius: float = 3.0,
                   orbit_height: float = 2.0, frames_per_orbit: int = 300,
                   el_lo: float = -7.0, el_hi: float = 52.0,
-                  range_lo: float = 0.1, range_hi: float = 40.0) -> Frame:
+                  range_lo: float = 0.1, range_hi: float = 40.0,
+                  centre=(0.0, 0.0)) -> Frame:
     """Livox-Mid-360-like frame: a Cranley-Patterson-rotated Halton(2,3)
     pattern over azimuth [0, 360) deg and elevation [el_lo, el_hi] deg, from
-    a sensor orbiting the origin; rays are drawn until n_hits returns with
-    range in [range_lo, range_hi]; range noise N(0, sigma)."""
+    a sensor orbiting `centre` (x, y); rays are drawn until n_hits returns
+    with range in [range_lo, range_hi]; range noise N(0, sigma)."""
     g = rng(seed, 31, frame)
     phi = 2.0 * math.pi * frame / frames_per_orbit
-    o = np.array([orbit_radius * math.cos(phi), orbit_radius * math.sin(phi), orbit_height])
+    o = np.array([centre[0] + orbit_radius * math.cos(phi),
+                  centre[1] + orbit_radius * math.sin(phi), orbit_height])
     T = yaw_pose(o, phi + math.pi)
     shift = g.uniform(0.0, 1.0, 2)
     world, normal = [], []

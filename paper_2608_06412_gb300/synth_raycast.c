@@ -103,7 +103,11 @@ static void hit_cylinder(const double *o, const double *d, const double *cy, dou
     }
 }
 
-void sr_raycast(int64_t n_groups, const double *caps, const int64_t *sph_off, const double *sph,
+/* Groups are arranged in clusters (contiguous group ranges, cl_off) with a
+ * bounding capsule each (cl_caps, same layout as caps) that encloses every
+ * group capsule of the cluster: a ray that misses it skips the cluster. */
+void sr_raycast(int64_t n_clusters, const double *cl_caps, const int64_t *cl_off,
+                const double *caps, const int64_t *sph_off, const double *sph,
                 const int64_t *box_off, const double *box, const int64_t *cyl_off,
                 const double *cyl, const double *o, int64_t n, const double *dirs, double *t_out,
                 double *n_out) {
@@ -111,12 +115,16 @@ void sr_raycast(int64_t n_groups, const double *caps, const int64_t *sph_off, co
     for (int64_t i = 0; i < n; ++i) {
         const double *d = dirs + 3 * i;
         double tb = INFINITY, nb[3] = {0, 0, 0};
-        for (int64_t g = 0; g < n_groups; ++g) {
-            const double *cp = caps + 7 * g;
-            if (ray_seg_dist2(o, d, cp, cp + 3) > cp[6] * cp[6]) continue;
-            for (int64_t k = sph_off[g]; k < sph_off[g + 1]; ++k) hit_sphere(o, d, sph + 4 * k, &tb, nb);
-            for (int64_t k = box_off[g]; k < box_off[g + 1]; ++k) hit_box(o, d, box + 6 * k, &tb, nb);
-            for (int64_t k = cyl_off[g]; k < cyl_off[g + 1]; ++k) hit_cylinder(o, d, cyl + 7 * k, &tb, nb);
+        for (int64_t c = 0; c < n_clusters; ++c) {
+            const double *cc = cl_caps + 7 * c;
+            if (ray_seg_dist2(o, d, cc, cc + 3) > cc[6] * cc[6]) continue;
+            for (int64_t g = cl_off[c]; g < cl_off[c + 1]; ++g) {
+                const double *cp = caps + 7 * g;
+                if (ray_seg_dist2(o, d, cp, cp + 3) > cp[6] * cp[6]) continue;
+                for (int64_t k = sph_off[g]; k < sph_off[g + 1]; ++k) hit_sphere(o, d, sph + 4 * k, &tb, nb);
+                for (int64_t k = box_off[g]; k < box_off[g + 1]; ++k) hit_box(o, d, box + 6 * k, &tb, nb);
+                for (int64_t k = cyl_off[g]; k < cyl_off[g + 1]; ++k) hit_cylinder(o, d, cyl + 7 * k, &tb, nb);
+            }
         }
         double nn = sqrt(dot3(nb, nb));
         t_out[i] = tb;

@@ -88,6 +88,69 @@ def pine_frame(W: Workload, f: int):
     return fr, pts, nrm
 
 
+def large_map(seed: int | None = None) -> Workload:
+    """8 pines on a noisy 40 x 40 m ground, 3,000 frames (375 orbit frames
+    around each pine), v = 1 cm, tau = 4 cm, K = 256, corridor 1.5 m."""
+    p = dict(synth.LARGE_MAP)
+    if seed is not None:
+        p["seed"] = seed
+    sc = synth.forest_ground_scene(p["seed"], p["pines"], p["ground_half"], p["ground_tile"],
+                                   p["ground_sigma"])
+    lo = np.minimum(sc.lo, [-p["ground_half"], -p["ground_half"], -0.3])
+    hi = np.maximum(sc.hi, [p["ground_half"], p["ground_half"], p["orbit_height"]])
+    dmin, db = synth.domain_bricks(lo, hi, p["v"], margin=0.1)
+    return Workload(p["name"], p, sc, dmin, db, synth.fibonacci_dirs(2 * p["K"]))
+
+
+def large_frame(W: Workload, f: int):
+    """Frame f of the large map: the sensor orbits pine f // frames_per_pine.
+    Returns (frame, surface points, normals)."""
+    p = W.params
+    centre = synth.pine_positions(p["seed"], p["pines"], p["ground_half"])[f // p["frames_per_pine"]]
+    fr = synth.rosette_frame(W.scene, f, p["seed"], n_hits=p["n_returns"], sigma=p["sigma"],
+                             orbit_radius=p["orbit_radius"], orbit_height=p["orbit_height"],
+                             frames_per_orbit=p["frames_per_pine"], centre=centre)
+    pts, nrm = synth.surface_points(fr.world, fr.normal, p["v"])
+    return fr, pts, nrm
+
+
+def _large_frames_chunk(args):
+    seed, fs = args
+    W = large_map(seed)
+    out = []
+    for f in fs:
+        fr, pts, nrm = large_frame(W, f)
+        out.append((fr.pts, fr.pose, fr.world.astype(np.float32), pts, nrm))
+    return out
+
+
+def large_frames(W: Workload, frames, workers: int = 0):
+    """Frames of the large map as (sensor-frame returns, pose, world returns
+    (float32), surface points, normals), generated by `workers` spawned
+    processes (0: os.cpu_count()). Start it before any CUDA call."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    frames = list(frames)
+    workers = workers or os.cpu_count() or 1
+    chunks = [frames[i::workers] for i in range(workers)]
+    env = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    try:
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_large_frames_chunk, [(W.params["seed"], c) for c in chunks]))
+    finally:
+        if env is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = env
+    by = {}
+    for c, part in zip(chunks, parts):
+        for f, item in zip(c, part):
+            by[f] = item
+    return [by[f] for f in frames]
+
+
 def soft_points(frames, v: float, count: int = 100_000, seed: int = 0):
     """Surface points of the differentiable-form workload: one point (and
     normal) per voxel that the stream's surface points fall in, its first
