@@ -25,10 +25,6 @@
 
 namespace af {
 
-// Runs each lane evaluates per warp step: more loads in flight per step,
-// at the price of a little wasted work when a step decides early.
-constexpr int kRunsPerLane = 1;
-
 struct Pt {
   int px, py, pz;  // box-relative voxel of the point
   int row;         // plane-word index of the point's row (FAST path only)
@@ -59,16 +55,33 @@ __device__ inline unsigned long long row_bits(const unsigned long long* __restri
   return win << (xa - x0);
 }
 
-// Bits of run r of the tables for point P; *len receives the run length.
+// One run-table entry: the fast form (plane-word row offset, dx0 | len << 16)
+// or the plain form (dx0 | len << 16, dy | dz << 16), 16-bit fields.
+struct RunEntry {
+  int a, b;
+};
+
+template <bool FAST>
+__device__ inline RunEntry load_run(const ToolView& T, int r) {
+  if (FAST) {
+    const int2 f = __ldg(T.fruns + r);
+    return {f.x, f.y};
+  }
+  const short4 s = __ldg(T.runs + r);
+  return {(int)((uint32_t)(uint16_t)s.x | ((uint32_t)(uint16_t)s.y << 16)),
+          (int)((uint32_t)(uint16_t)s.z | ((uint32_t)(uint16_t)s.w << 16))};
+}
+
+// Bits of the run of entry e for point P; *len receives the run length.
 template <bool FAST>
 __device__ inline unsigned long long run_bits(const unsigned long long* __restrict__ plane,
-                                              const MapView& M, const ToolView& T, int r,
-                                              const Pt& P, int* len, bool* outside) {
+                                              const MapView& M, RunEntry e, const Pt& P,
+                                              int* len, bool* outside) {
+  const int dx0 = (int)(short)(e.a & 0xffff), dxy = (int)(short)(e.b & 0xffff);
   if (FAST) {
-    const int2 fr = __ldg(T.fruns + r);
-    const int n = fr.y >> 16;
-    const int xa = P.px + (int)(short)(fr.y & 0xffff);
-    const int row = P.row + fr.x;
+    const int n = e.b >> 16;
+    const int xa = P.px + dxy;
+    const int row = P.row + e.a;
     const int wa = xa >> 6, wb = (xa + n - 1) >> 6, sh = xa & 63;
     unsigned long long win = __ldg(plane + row + wa) >> sh;
     if (wb != wa) win |= __ldg(plane + row + wb) << (64 - sh);
@@ -76,9 +89,20 @@ __device__ inline unsigned long long run_bits(const unsigned long long* __restri
     *len = n;
     return win;
   }
-  const short4 run = __ldg(T.runs + r);
-  *len = run.y;
-  return row_bits(plane, M, P.px + run.x, P.py + run.z, P.pz + run.w, run.y, outside);
+  const int n = (int)((uint32_t)e.a >> 16), dz = (int)(short)((uint32_t)e.b >> 16);
+  *len = n;
+  return row_bits(plane, M, P.px + dx0, P.py + dxy, P.pz + dz, n, outside);
+}
+
+// Walks runs [r0, r1) of the tables a warp step (32 runs, one per lane) at a
+// time; the caller's `step(entry, valid)` returns true to stop the walk.
+template <bool FAST, class F>
+__device__ inline void walk_runs(const ToolView& T, int r0, int r1, int lane, F&& step) {
+  for (int b = r0; b < r1; b += 32) {
+    const int r = b + lane;
+    const RunEntry e = r < r1 ? load_run<FAST>(T, r) : RunEntry{0, 0};
+    if (step(e, r < r1)) return;
+  }
 }
 
 template <bool FAST>
@@ -99,33 +123,32 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, con
                                  int lane) {
   const int4 dt = __ldg(T.dtab + g);
   int total = 0;
-  for (int r0 = dt.x; r0 < dt.y; r0 += 32 * kRunsPerLane) {
+  walk_runs<FAST>(T, dt.x, dt.y, lane, [&](RunEntry e, bool valid) {
     int c = 0;
-#pragma unroll
-    for (int k = 0; k < kRunsPerLane; ++k) {
-      const int r = r0 + 32 * k + lane;
-      if (r < dt.y) {
-        int len;
-        bool out = false;
-        c += __popcll(run_bits<FAST>(M.occ, M, T, r, P, &len, &out));
-      }
+    if (valid) {
+      int len;
+      bool out = false;
+      c = __popcll(run_bits<FAST>(M.occ, M, e, P, &len, &out));
     }
     total += __reduce_add_sync(0xffffffffu, c);
-    if (total >= sat) return sat;
-  }
-  return total;
+    return total >= sat;
+  });
+  return total >= sat ? sat : total;
 }
 
 // The three arm samples of direction g (one lane): clear iff none is
-// occupied or unknown.
+// occupied or unknown. All nine loads are issued together (no short
+// circuit), so the screen costs two dependent round trips, not up to nine.
 template <bool FAST>
 __device__ inline bool arm_clear(const MapView& M, const ToolView& T, int g, const Pt& P) {
+  short4 a[3];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const short4 a = __ldg(T.arm + 3 * g + s);
-    if (bit_at<FAST>(M.occ, M, P, a) || !bit_at<FAST>(M.known, M, P, a)) return false;
-  }
-  return true;
+  for (int s = 0; s < 3; ++s) a[s] = __ldg(T.arm + 3 * g + s);
+  bool blocked = false;
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+    blocked = blocked | bit_at<FAST>(M.occ, M, P, a[s]) | !bit_at<FAST>(M.known, M, P, a[s]);
+  return !blocked;
 }
 
 // Corridor of direction g: any occupied voxel (strict: or unknown) blocks.
@@ -133,26 +156,23 @@ template <bool FAST>
 __device__ inline bool corridor_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
                                         int lane) {
   const int4 dt = __ldg(T.dtab + g);
-  for (int r0 = dt.z; r0 < dt.w; r0 += 32 * kRunsPerLane) {
+  bool blocked = false;
+  walk_runs<FAST>(T, dt.z, dt.w, lane, [&](RunEntry e, bool valid) {
     bool h = false;
-#pragma unroll
-    for (int k = 0; k < kRunsPerLane; ++k) {
-      const int r = r0 + 32 * k + lane;
-      if (r < dt.w) {
-        int len;
-        bool out = false;
-        bool hk = run_bits<FAST>(M.occ, M, T, r, P, &len, &out) != 0ull;
-        if (T.strict && !hk) {
-          const unsigned long long kb = run_bits<FAST>(M.known, M, T, r, P, &len, &out);
-          const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
-          hk = out || (kb != full);
-        }
-        h = h || hk;
+    if (valid) {
+      int len;
+      bool out = false;
+      h = run_bits<FAST>(M.occ, M, e, P, &len, &out) != 0ull;
+      if (T.strict && !h) {
+        const unsigned long long kb = run_bits<FAST>(M.known, M, e, P, &len, &out);
+        const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
+        h = out || (kb != full);
       }
     }
-    if (__any_sync(0xffffffffu, h)) return true;
-  }
-  return false;
+    blocked = __any_sync(0xffffffffu, h);
+    return blocked;
+  });
+  return blocked;
 }
 
 __device__ inline bool candidate(const ToolView& T, int g, float n0, float n1, float n2) {
