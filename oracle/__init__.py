@@ -22,7 +22,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "af_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("af_oracle.c", "af_oracle_points.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 UNSCORED, ACCESSIBLE, BLOCKED = 0, 1, 2
@@ -31,12 +31,13 @@ KERNEL_TOOL, KERNEL_CORRIDOR = 0, 1
 
 def build(force: bool = False) -> str:
     """Compile af_oracle.c with strict IEEE single-precision semantics."""
+    deps = _SRCS + [os.path.join(_HERE, "af_oracle.h")]
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(d) for d in deps)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-Wall", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -60,6 +61,14 @@ class _Tool(C.Structure):
 
 
 _lib = None
+
+
+class _PtsConfig(C.Structure):
+    _fields_ = [("k_nn", C.c_uint32), ("nn_radius", C.c_int32), ("max_views", C.c_uint32),
+                ("view_min_dist", C.c_float), ("obs_dot", C.c_float), ("trig_tsdf", C.c_float),
+                ("trig_move", C.c_float), ("budget", C.c_uint32), ("k_c", C.c_float),
+                ("c_min", C.c_float), ("a_decay", C.c_float), ("a_recover", C.c_float),
+                ("ca_min", C.c_float)]
 
 
 def _load():
@@ -95,6 +104,21 @@ def _load():
         lib.or_soft_clearance.argtypes = [P, C.POINTER(_Tool), P, C.c_uint32, P, P, P, P,
                                           C.c_int64, C.c_double, C.c_int, P, P, P, P, P]
         lib.or_soft_seed.argtypes = [P, C.c_int64, P, C.c_int32, P]
+        lib.or_integrate2.restype = C.c_int64
+        lib.or_integrate2.argtypes = [P, P, C.c_int64, P, P]
+        lib.or_pts_new.restype = P
+        lib.or_pts_new.argtypes = [P, C.POINTER(_PtsConfig), C.POINTER(_Tool), P, C.c_int32]
+        lib.or_pts_free.argtypes = [P]
+        lib.or_pts_frame.restype = C.c_int64
+        lib.or_pts_frame.argtypes = [P, P, P, C.c_int64, P]
+        lib.or_pts_drain.restype = C.c_int64
+        lib.or_pts_drain.argtypes = [P, P, C.c_int64]
+        lib.or_pts_count.restype = C.c_int64
+        lib.or_pts_count.argtypes = [P]
+        lib.or_pts_export.argtypes = [P, P, P, P, P, P, P, P, P]
+        lib.or_jacobi3.argtypes = [P, C.c_int, P, P]
+        lib.or_pts_state_step.argtypes = [C.POINTER(_PtsConfig), C.c_int32, C.c_int32, C.c_int32,
+                                          C.c_float, P, P, P, P]
         lib.or_soft_refine.argtypes = [P, C.POINTER(_Tool), P, C.c_uint32, P, P, P, P,
                                        C.c_int64, C.c_double, C.c_int, C.c_float, C.c_float,
                                        C.c_float, P, P]
@@ -298,3 +322,91 @@ def arm_offsets(v: float, tau: float, u) -> np.ndarray:
     out = np.zeros((3, 3), np.int32)
     lib.or_arm_offsets(C.c_float(v), C.c_float(tau), _ptr(u), _ptr(out))
     return out
+
+
+@dataclass
+class PointsConfig:
+    """The stateful layer's parameters (Sec. 3.4, 3.5); trig_tsdf is 2v."""
+    trig_tsdf: float
+    k_nn: int = 10
+    nn_radius: int = 3
+    max_views: int = 8
+    view_min_dist: float = 0.1
+    obs_dot: float = 0.25
+    trig_move: float = 0.1
+    budget: int = 1 << 30
+    k_c: float = 5.0
+    c_min: float = 0.2
+    a_decay: float = 0.75
+    a_recover: float = 0.15
+    ca_min: float = 0.7
+
+    def _c(self) -> _PtsConfig:
+        c = _PtsConfig()
+        for k, _ in _PtsConfig._fields_:
+            setattr(c, k, getattr(self, k))
+        return c
+
+
+class PointSet:
+    """The oracle's stateful point layer over one oracle Map."""
+
+    def __init__(self, mp: "Map", pc: PointsConfig, tool: "Tool", dirs: np.ndarray):
+        self._lib = _load()
+        self._map = mp
+        self._dirs = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+        self._pc = pc._c()
+        self._tc = tool._c()
+        self._h = self._lib.or_pts_new(mp._h, C.byref(self._pc), C.byref(self._tc),
+                                       _ptr(self._dirs), len(self._dirs))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.or_pts_free(self._h)
+            self._h = None
+
+    def frame(self, pts: np.ndarray, pose) -> int:
+        pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
+        pose = np.ascontiguousarray(pose, np.float32).reshape(16)
+        return int(self._lib.or_pts_frame(self._h, self._map._h, _ptr(pts), len(pts), _ptr(pose)))
+
+    def drain(self, max_evals: int) -> int:
+        return int(self._lib.or_pts_drain(self._h, self._map._h, max_evals))
+
+    def __len__(self):
+        return int(self._lib.or_pts_count(self._h))
+
+    def export(self) -> dict:
+        n = len(self)
+        out = dict(ijk=np.zeros((n, 3), np.int32), normal=np.zeros((n, 3), np.float32),
+                   label=np.zeros(n, np.uint8), score=np.zeros(n, np.int16),
+                   best=np.zeros(n, np.int16), a=np.zeros(n, np.float32),
+                   queued=np.zeros(n, np.uint8), nviews=np.zeros(n, np.int32))
+        if n:
+            self._lib.or_pts_export(self._h, *(_ptr(out[k]) for k in
+                                               ("ijk", "normal", "label", "score", "best", "a",
+                                                "queued", "nviews")))
+        return out
+
+
+def jacobi3(A: np.ndarray, sweeps: int = 8):
+    """(eigenvalues, eigenvectors as columns) of a symmetric 3 x 3 matrix by
+    the oracle's cyclic Jacobi routine, single precision."""
+    lib = _load()
+    A = np.ascontiguousarray(A, np.float32).reshape(9)
+    ev = np.zeros(3, np.float32)
+    V = np.zeros(9, np.float32)
+    lib.or_jacobi3(_ptr(A), sweeps, _ptr(ev), _ptr(V))
+    return ev, V.reshape(3, 3)
+
+
+def pts_state_step(pc: PointsConfig, n_c: int, state: dict, s: int, g: int, c: float) -> dict:
+    """One evaluation's state update (score, best, a, label) by the oracle."""
+    lib = _load()
+    cc = pc._c()
+    sc = np.array([state["score"]], np.int16)
+    bs = np.array([state["best"]], np.int16)
+    a = np.array([state["a"]], np.float32)
+    lab = np.array([state.get("label", 0)], np.uint8)
+    lib.or_pts_state_step(C.byref(cc), n_c, s, g, c, _ptr(sc), _ptr(bs), _ptr(a), _ptr(lab))
+    return dict(score=int(sc[0]), best=int(bs[0]), a=float(a[0]), label=int(lab[0]))

@@ -78,6 +78,7 @@
  */
 #include "af_oracle.h"
 
+#include <limits.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -198,6 +199,11 @@ static int voxel_index(float c, float v, int32_t *out) {
 static float voxel_centre(int32_t i, float v) { return ((float)i + 0.5f) * v; }
 
 int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16]) {
+    return or_integrate2(m, pts, n, pose, NULL);
+}
+
+int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[16],
+                      int32_t *voxel_out) {
     const or_config *c = &m->cfg;
     const float v = c->v, tau = c->tau;
     const int32_t mr = c->cube_radius;
@@ -205,6 +211,8 @@ int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16
     const float q[3] = {pose[3], pose[7], pose[11]};
     int64_t accepted = 0;
 
+    if (voxel_out)
+        for (int64_t k = 0; k < 3 * n; ++k) voxel_out[k] = INT32_MIN;
     for (int64_t k = 0; k < n; ++k) {
         const float *ps = pts + 3 * k;
         if (!isfinite(ps[0]) || !isfinite(ps[1]) || !isfinite(ps[2])) continue;
@@ -229,6 +237,8 @@ int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16
             !in_domain(c, ip[0] + mr, ip[1] + mr, ip[2] + mr))
             continue;
         accepted++;
+        if (voxel_out)
+            for (int r = 0; r < 3; ++r) voxel_out[3 * k + r] = ip[r];
 
         /* every voxel x of the (2m+1)^3 cube around p_i */
         for (int32_t oz = -mr; oz <= mr; ++oz)
@@ -308,6 +318,8 @@ void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const uint64_t *S,
 }
 
 int64_t or_voxel_count(const or_map *m) { return (int64_t)m->count; }
+
+const or_config *or_map_config(const or_map *m) { return &m->cfg; }
 
 /* TSDF < r_c, with r_c on the same 2^-20 m grid as S. */
 static int occ_of(const or_map *m, const or_voxel *vx) {

@@ -59,6 +59,10 @@ void or_map_free(or_map *m);
  * Sec. 3.6 weight cap). pts: n x 3 floats in the sensor frame; pose: 4x4
  * row-major world_from_sensor. Returns the number of accepted returns. */
 int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16]);
+/* The same, also writing the voxel of every accepted return to voxel_out
+ * (n x 3, INT32_MIN for dropped returns) when it is not NULL. */
+int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[16],
+                      int32_t *voxel_out);
 
 /* Voxel state. Absent voxels report S = 0, w = 0, cleared = 0. */
 int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz,
@@ -68,6 +72,7 @@ void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz,
 void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const uint64_t *S,
                    const uint32_t *w, const uint8_t *cleared);
 int64_t or_voxel_count(const or_map *m);
+const or_config *or_map_config(const or_map *m);
 /* Writes every stored voxel: ijk (count x 3), S, w, cleared, occ, known. */
 void or_export(const or_map *m, int32_t *ijk, uint64_t *S, uint32_t *w,
                uint8_t *cleared, uint8_t *occ, uint8_t *known);
@@ -110,6 +115,52 @@ void or_soft_refine(const or_map *m, const or_tool *t, const float *pts, uint32_
                     const float *u0, float *alpha, float *beta, float *h, int64_t npairs,
                     double tau_s, int steps, float lr_dir, float lr_h, float h_max, double *c,
                     double *cmin);
+
+/* ---- The stateful layer around scoring (Sec. 3.4 normals and
+ * observation-side filter, Sec. 3.5 incremental updates and confidence). ---- */
+typedef struct {
+    uint32_t k_nn;        /* neighbours of the PCA normal, the point included (10)   */
+    int32_t nn_radius;    /* neighbour search cube half-width, voxels (3)              */
+    uint32_t max_views;   /* stored historical viewpoints per point, <= 8              */
+    float view_min_dist;  /* a viewpoint is stored if farther than this from all others */
+    float obs_dot;        /* observation-side filter threshold (0.25)                  */
+    float trig_tsdf;      /* re-evaluate when the point's TSDF moves more (2v)         */
+    float trig_move;      /* sensor motion that re-queues blocked points (0.1 m)      */
+    uint32_t budget;      /* evaluations per frame; the rest waits in the backlog      */
+    float k_c;            /* confidence c = w / (w + k_c)                              */
+    float c_min;          /* points with c below are not evaluated (0.2)               */
+    float a_decay;        /* accessibility confidence a *= a_decay on conflict (0.75)  */
+    float a_recover;      /* a += a_recover (1 - a) on confirmation (0.15)             */
+    float ca_min;         /* confident-accessible iff score < n_c and c a > ca_min    */
+} or_pts_config;
+
+typedef struct or_pts or_pts;
+
+/* A point set that follows map m, scored with tool t over the G directions. */
+or_pts *or_pts_new(const or_map *m, const or_pts_config *pc, const or_tool *t, const float *dirs,
+                   int32_t G);
+void or_pts_free(or_pts *P);
+/* One frame: integrate the scan into m, then ingest its returns as surface
+ * points, raise the re-evaluation triggers and evaluate up to `budget`
+ * queued points in id order. Returns the number of evaluations. */
+int64_t or_pts_frame(or_pts *P, or_map *m, const float *pts, int64_t n, const float pose[16]);
+/* Evaluate up to max queued points (the backlog between frames). */
+int64_t or_pts_drain(or_pts *P, const or_map *m, int64_t max);
+int64_t or_pts_count(const or_pts *P);
+/* Per point in id order: voxel (n x 3), normal (n x 3), label, stored score
+ * (-1 never scored), stored best direction, accessibility confidence a,
+ * queued flag, number of stored viewpoints. */
+void or_pts_export(const or_pts *P, int32_t *ijk, float *normal, uint8_t *label, int16_t *score,
+                   int16_t *best, float *a, uint8_t *queued, int32_t *nviews);
+/* The state update of one evaluation (exposed for its pins): score s and
+ * direction g of the evaluation at confidence c update the stored score and
+ * direction, the accessibility confidence a and the label. */
+void or_pts_state_step(const or_pts_config *pc, int32_t n_c, int32_t s, int32_t g, float c,
+                       int16_t *score, int16_t *best, float *a, uint8_t *label);
+/* The symmetric-eigenvector routine of the normal (exposed for its pins):
+ * cyclic Jacobi on A (3 x 3, row-major), `sweeps` sweeps; writes the
+ * eigenvalues (diagonal after the sweeps) and eigenvectors (columns of V). */
+void or_jacobi3(const float A[9], int sweeps, float evals[3], float V[9]);
 
 #ifdef __cplusplus
 }

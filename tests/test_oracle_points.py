@@ -1,0 +1,274 @@
+"""Pins of the oracle's stateful layer (Sec. 3.4 normals and observation-side
+filter, Sec. 3.5 incremental updates and confidence) against what the paper
+and mathematics fix:
+
+* the Jacobi eigen-solver against numpy's LAPACK solver, residuals and
+  orthonormality, and the diagonal case (no rotation at all);
+* PCA normals on an axis-aligned wall equal the wall normal exactly, facing
+  the sensor; points are numbered in (z, y, x) order within a frame;
+* viewpoints are stored only when farther than the minimum distance from all
+  stored ones, at most max_views;
+* every scored best direction is aligned (> obs_dot) with a stored viewpoint;
+* the budget evaluates the lowest ids first and the backlog drains in order;
+* the paper's worked example: a well-observed accessible point stays
+  accessible after one conflicting evaluation (c a = 0.75) and leaves the
+  accessible set after two (c a = 0.5625 < 0.7), its stored score unchanged;
+* a sensor move above trig_move re-queues blocked points, a smaller one
+  does not; returns far away queue nothing.
+Parity status: pinned.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_06412_gb300 import synth
+
+V = 0.02
+
+
+def _cfg():
+    return oracle.Config(v=V, tau=0.06, r_c=0.01, cube_radius=3, clear_samples=8,
+                         dom_min=(-64, -64, -64), dom_size=(256, 128, 128), w_min=1)
+
+
+def _tool(**kw):
+    base = dict(radius=0.04, length=0.25, self_excl=0.04, corr_radius=0.05, corr_length=0.5,
+                cos_theta_max=0.0, n_c=5, strict=0)
+    base.update(kw)
+    return oracle.Tool(**base)
+
+
+def _wall(x0=2.0, half=0.5):
+    g = synth.Group(a=np.array([x0 + 0.02, 0, -half]), b=np.array([x0 + 0.02, 0, half]),
+                    radius=half * 1.5, boxes=np.array([[x0, -half, -half, x0 + 0.04, half, half]]))
+    return synth.Scene([g], *synth._bounds([g]))
+
+
+def _frame(scene, origin, n=4000, seed=0):
+    fr = synth.cone_frame(scene, n, 0.0, seed, origin=origin)
+    return fr.pts, fr.pose
+
+
+def test_jacobi_matches_lapack():
+    rng = np.random.default_rng(0)
+    for k in range(300):
+        if k % 3 == 0:   # integer covariance-like matrices, as the normal forms them
+            d = rng.integers(-3, 4, (10, 3))
+            A = (10 * d.T @ d - np.outer(d.sum(0), d.sum(0))).astype(np.float32)
+        else:
+            B = rng.normal(size=(3, 3))
+            A = (B + B.T).astype(np.float32)
+        ev, Vm = oracle.jacobi3(A)
+        ref = np.linalg.eigvalsh(A.astype(np.float64))
+        scale = max(np.abs(ref).max(), 1e-6)
+        np.testing.assert_allclose(np.sort(ev), ref, atol=3e-6 * scale)
+        Vd = Vm.astype(np.float64)
+        np.testing.assert_allclose(Vd.T @ Vd, np.eye(3), atol=2e-6)
+        np.testing.assert_allclose(A @ Vd, Vd * ev, atol=2e-5 * scale)
+    A = np.diag([3.0, 1.0, 2.0]).astype(np.float32)
+    ev, Vm = oracle.jacobi3(A)
+    assert (Vm == np.eye(3)).all() and (ev == [3, 1, 2]).all()
+
+
+def test_wall_normals_ids_and_views():
+    mp = oracle.Map(_cfg())
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V), _tool(), synth.fibonacci_dirs(64))
+    pts, pose = _frame(_wall(), (0.0, 0.0, 0.0))
+    P.frame(pts, pose)
+    e = P.export()
+    # ids in (z, y, x) order of the voxels
+    order = np.lexsort((e["ijk"][:, 0], e["ijk"][:, 1], e["ijk"][:, 2]))
+    assert (order == np.arange(len(order))).all()
+    # interior wall points: exactly the -x normal, facing the sensor at x < 2
+    scored = e["score"] >= 0
+    interior = scored & (np.abs(e["ijk"][:, 1]) < 20) & (np.abs(e["ijk"][:, 2]) < 20)
+    assert interior.sum() > 50
+    assert (e["normal"][interior] == np.array([-1, 0, 0], np.float32)).all()
+    # one scan, one viewpoint each
+    assert (e["nviews"] == 1).all()
+
+
+def test_view_storage_rule():
+    mp = oracle.Map(_cfg())
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, budget=0), _tool(),
+                        synth.fibonacci_dirs(32))
+    wall = _wall()
+    for k in range(20):   # sensor steps of 6 cm: every second position is stored
+        pts, pose = _frame(wall, (0.0, 0.06 * k, 0.0), n=3000, seed=k)
+        P.frame(pts, pose)
+    e = P.export()
+    seen_all = e["nviews"][(np.abs(e["ijk"][:, 1]) < 5) & (np.abs(e["ijk"][:, 2]) < 5)]
+    assert seen_all.max() == 8            # capped at max_views
+    P2 = oracle.PointSet(oracle.Map(_cfg()), oracle.PointsConfig(trig_tsdf=2 * V, budget=0),
+                         _tool(), synth.fibonacci_dirs(32))
+    for k in range(5):    # positions 0, 6, 12, 18, 24 cm: stored 0, 12, 24
+        pts, pose = _frame(wall, (0.0, 0.06 * k, 0.0), n=3000, seed=k)
+        P2.frame(pts, pose)
+    e2 = P2.export()
+    # greedy storage: any two stored positions are > 10 cm apart, so at most
+    # 3 of these 5 (storing every scan would give 5, a reversed test 1)
+    assert e2["nviews"].max() == 3 and (e2["nviews"] == 3).sum() > 20
+
+
+def test_observation_side_filter():
+    mp = oracle.Map(_cfg())
+    dirs = synth.fibonacci_dirs(128)
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V), _tool(cos_theta_max=-1.0), dirs)
+    pts, pose = _frame(_wall(), (0.0, 0.4, 0.0))
+    P.frame(pts, pose)
+    e = P.export()
+    s = (e["ijk"] + 0.5) * np.float32(V)
+    ok = e["best"] >= 0
+    assert ok.sum() > 50
+    to_q = np.array([0.0, 0.4, 0.0]) - s[ok]
+    to_q /= np.linalg.norm(to_q, axis=1, keepdims=True)
+    assert ((dirs[e["best"][ok]] * to_q).sum(1) > 0.25).all()
+    # without the filter some best directions point away from the sensor side
+    P2 = oracle.PointSet(oracle.Map(_cfg()), oracle.PointsConfig(trig_tsdf=2 * V, obs_dot=-2.0),
+                         _tool(cos_theta_max=-1.0), dirs)
+    P2.frame(pts, pose)
+    e2 = P2.export()
+    ok2 = e2["best"] >= 0
+    to_q2 = np.array([0.0, 0.4, 0.0]) - s[ok2]
+    to_q2 /= np.linalg.norm(to_q2, axis=1, keepdims=True)
+    assert ((dirs[e2["best"][ok2]] * to_q2).sum(1) <= 0.25).any()
+
+
+def test_budget_and_backlog_in_id_order():
+    mp = oracle.Map(_cfg())
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, budget=7), _tool(),
+                        synth.fibonacci_dirs(32))
+    pts, pose = _frame(_wall(), (0.0, 0.0, 0.0))
+    assert P.frame(pts, pose) == 7
+    e = P.export()
+    assert (e["queued"][:7] == 0).all() and (e["queued"][7:] == 1).all()
+    assert P.drain(10) == 10
+    e = P.export()
+    assert (e["queued"][:17] == 0).all() and (e["queued"][17:] == 1).all()
+    assert P.drain(10 ** 9) == len(P) - 17
+    assert P.drain(5) == 0
+
+
+def test_two_conflicts_leave_the_accessible_set():
+    """Sec. 3.5: for a well-observed point (c ~ 1) one conflicting evaluation
+    leaves it accessible, two push c a below 0.7; the stored score stays."""
+    mp = oracle.Map(_cfg())
+    dirs = np.array([[-1.0, 0.0, 0.0]], np.float32)     # one approach direction: from -x
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, k_c=1e-3), _tool(), dirs)
+    wall = _wall(half=0.3)
+    for k in range(3):
+        pts, pose = _frame(wall, (0.0, 0.0, 0.0), n=4000, seed=k)
+        P.frame(pts, pose)
+    e = P.export()
+    centre = np.nonzero((e["ijk"][:, 1] == 0) & (e["ijk"][:, 2] == 0) & (e["score"] >= 0))[0]
+    assert len(centre) == 1
+    c0 = centre[0]
+    assert e["label"][c0] == oracle.ACCESSIBLE and e["score"][c0] < 5 and e["a"][c0] == 1.0
+    # an obstacle appears in the corridor (a plate 40 cm in front of the wall)
+    plate = synth.Group(a=np.array([1.7, 0, 0]), b=np.array([1.7, 0, 0]), radius=0.2,
+                        boxes=np.array([[1.68, -0.1, -0.1, 1.72, 0.1, 0.1]]))
+    both = synth.Scene(wall.groups + [plate], *synth._bounds(wall.groups + [plate]))
+    labels, a = [], []
+    for k in range(2):
+        pts, pose = _frame(both, (0.0, 0.0, 0.0), n=4000, seed=10 + k)
+        P.frame(pts, pose)
+        e = P.export()
+        labels.append(int(e["label"][c0]))
+        a.append(float(e["a"][c0]))
+    assert a == [np.float32(0.75), np.float32(np.float32(0.75) * np.float32(0.75))]
+    assert labels == [oracle.ACCESSIBLE, oracle.BLOCKED]
+    assert e["score"][c0] < 5              # the stored score never increases
+
+
+def test_motion_trigger_and_locality():
+    """Budget 0: frames only queue; drains evaluate."""
+    dirs = synth.fibonacci_dirs(64)
+    P = oracle.PointSet(oracle.Map(_cfg()), oracle.PointsConfig(trig_tsdf=2 * V, budget=0),
+                        _tool(corr_length=1.0), dirs)
+    # a wall with a slot too narrow for the tool, and a second wall behind it
+    g = synth.Group(a=np.array([2.02, 0, 0]), b=np.array([2.02, 0, 0]), radius=0.8,
+                    boxes=np.array([[2.0, -0.5, -0.5, 2.04, -0.01, 0.5],
+                                    [2.0, 0.01, -0.5, 2.04, 0.5, 0.5],
+                                    [2.3, -0.5, -0.5, 2.34, 0.5, 0.5]]))
+    scene = synth.Scene([g], *synth._bounds([g]))
+    pts, pose = _frame(scene, (0.0, 0.0, 0.0), n=6000)
+    assert P.frame(pts, pose) == 0
+    n0 = len(P)
+    assert (P.export()["queued"] == 1).all()          # new points are always queued
+    P.drain(10 ** 9)
+    e = P.export()
+    blocked = e["label"] == oracle.BLOCKED
+    assert blocked.any() and (e["label"] == oracle.ACCESSIBLE).any() and (e["queued"] == 0).all()
+    # returns 1.2 m aside only, the sensor moved 3 cm: nothing near the wall is queued
+    far = synth.Group(a=np.array([0.5, 1.2, 0]), b=np.array([0.5, 1.2, 0]), radius=0.2,
+                      boxes=np.array([[0.48, 1.1, -0.1, 0.52, 1.3, 0.1]]))
+    sfar = synth.Scene([far], *synth._bounds([far]))
+    pts, pose = _frame(sfar, (0.0, 0.03, 0.0), n=500)
+    P.frame(pts, pose)
+    assert (P.export()["queued"][:n0] == 0).all()
+    # 12 cm from where the motion trigger last fired: exactly the blocked points
+    pts, pose = _frame(sfar, (0.0, 0.12, 0.0), n=500, seed=1)
+    P.frame(pts, pose)
+    q = P.export()["queued"][:n0].astype(bool)
+    assert (q == blocked).all()
+
+
+def test_state_update_rules():
+    """Sec. 3.5 in closed form: the stored score only decreases; a decays by
+    0.75 on each conflict and recovers by 0.15 (1 - a) on each confirmation;
+    confident-accessible iff stored score < n_c and c a > 0.7."""
+    pc = oracle.PointsConfig(trig_tsdf=0.04)
+    f = np.float32
+    st = dict(score=-1, best=-1, a=1.0)
+    st = oracle.pts_state_step(pc, 5, st, 3, 7, 0.99)         # first evaluation
+    assert st == dict(score=3, best=7, a=1.0, label=oracle.ACCESSIBLE)
+    st = oracle.pts_state_step(pc, 5, st, 5, 2, 0.99)         # s = n_c: a conflict
+    assert (st["score"], st["best"], st["a"]) == (3, 7, f(0.75)) and st["label"] == oracle.ACCESSIBLE
+    st = oracle.pts_state_step(pc, 5, st, 6, 2, 0.99)         # blocked: a second conflict
+    a2 = f(f(0.75) * f(0.75))
+    assert st["a"] == a2 and st["label"] == oracle.BLOCKED    # 0.99 * 0.5625 < 0.7
+    st = oracle.pts_state_step(pc, 5, st, 1, 4, 0.99)         # confirming, strictly lower
+    a3 = f(a2 + f(f(0.15) * f(f(1.0) - a2)))
+    assert (st["score"], st["best"], st["a"]) == (1, 4, a3)
+    st = oracle.pts_state_step(pc, 5, st, 1, 9, 0.99)         # equal score keeps the direction
+    assert st["best"] == 4
+    # a point never accessible: scores n_c and above neither decay nor recover a
+    st = oracle.pts_state_step(pc, 5, dict(score=-1, best=-1, a=1.0), 5, 0, 1.0)
+    assert (st["score"], st["a"], st["label"]) == (5, 1.0, oracle.BLOCKED)
+    st = oracle.pts_state_step(pc, 5, st, 6, 1, 1.0)
+    assert (st["score"], st["a"], st["label"]) == (5, 1.0, oracle.BLOCKED)
+    # one conflict at c = 0.9 already drops c a below 0.7 (0.675)
+    st = oracle.pts_state_step(pc, 5, dict(score=2, best=1, a=1.0), 6, 0, 0.9)
+    assert st["label"] == oracle.BLOCKED and st["score"] == 2
+    # low confidence keeps an accessible score unconfident
+    st = oracle.pts_state_step(pc, 5, dict(score=-1, best=-1, a=1.0), 0, 3, 0.6)
+    assert st["label"] == oracle.BLOCKED and st["score"] == 0
+
+
+def test_neighbour_brick_trigger_and_confidence_gate():
+    dirs = synth.fibonacci_dirs(32)
+    P = oracle.PointSet(oracle.Map(_cfg()), oracle.PointsConfig(trig_tsdf=2 * V, budget=0),
+                        _tool(), dirs)
+    pts, pose = _frame(_wall(), (0.0, 0.0, 0.0), n=6000)
+    P.frame(pts, pose)
+    P.drain(10 ** 9)
+    n0 = len(P)
+    # returns from a small box above the wall's top edge (z voxels 27..29)
+    top = synth.Group(a=np.array([2.02, 0, 0.57]), b=np.array([2.02, 0, 0.57]), radius=0.1,
+                      boxes=np.array([[2.0, -0.05, 0.55, 2.04, 0.05, 0.59]]))
+    st = synth.Scene([top], *synth._bounds([top]))
+    pts, pose = _frame(st, (0.0, 0.0, 0.0), n=300)
+    P.frame(pts, pose)
+    e = P.export()
+    old = np.arange(len(e["queued"])) < n0
+    zb = np.floor_divide(e["ijk"][:, 2], 8)
+    q = e["queued"].astype(bool)
+    assert (q & old & (zb == 2)).any()             # one brick below the touched bricks
+    assert not (q & old & (zb <= 1)).any()         # two bricks away: untouched
+    # a sparse scan: isolated returns leave w = 1 (c = 1/6 < 0.2): never scored, not queued
+    P2 = oracle.PointSet(oracle.Map(_cfg()), oracle.PointsConfig(trig_tsdf=2 * V), _tool(), dirs)
+    pts, pose = _frame(_wall(), (0.0, 0.0, 0.0), n=25, seed=3)
+    P2.frame(pts, pose)
+    e2 = P2.export()
+    assert len(e2["score"]) >= 20 and (e2["queued"] == 0).all()
+    assert (e2["score"] == -1).mean() > 0.8     # (a few returns share cubes: w >= 2 there)
