@@ -338,6 +338,75 @@ af_status af_soft_best(af_ctx *ctx, const float *d_c, uint64_t n, uint32_t per_p
                        void *stream);
 
 /*
+ * The stateful layer around scoring (Sec. 3.4 normals and observation-side
+ * filter, Sec. 3.5 incremental updates and confidence). The context keeps a
+ * growing, voxel-deduplicated set of surface points (the centres of voxels
+ * that received an accepted return) and, per point, its stored best score and
+ * direction, accessibility confidence a, label, and up to 8 historical
+ * viewpoints. Each af_points_frame integrates a scan (as af_integrate_scan),
+ * adds its new points, raises the re-evaluation triggers and evaluates up to
+ * `budget` queued points in point-id order; af_points_drain evaluates more of
+ * the backlog between frames. Points are numbered in order of first
+ * observation, the points new in one frame in (z, y, x) order of their
+ * voxels. The rules:
+ *  - viewpoints: once per scan that observes a point, the sensor position is
+ *    added to its sum and, while fewer than max_views are stored, stored if
+ *    farther than view_min_dist from every stored one;
+ *  - normal: PCA over the k_nn nearest surface points (itself included) in the
+ *    voxel cube of half-width nn_radius (ties in (dz, dy, dx) order), from
+ *    the exact integer covariance of the voxel offsets, its smallest-eigenvalue
+ *    eigenvector by 8 cyclic Jacobi sweeps in single precision, facing the
+ *    mean sensor position; fewer than 3 neighbours: not evaluated;
+ *  - candidates: n . u > cos_theta_max and u . (q - s) / |q - s| > obs_dot for
+ *    some stored viewpoint q; scores as af_score (no candidate: n_c + 1);
+ *  - triggers: new points; TSDF at the voxel moved more than trig_tsdf since
+ *    the previous frame; a brick within one brick of the point's brick
+ *    overlapped by the cube of an accepted return of the frame; a sensor move
+ *    of more than trig_move since the motion trigger last fired re-queues the
+ *    points labelled AF_BLOCKED;
+ *  - evaluation: points with c = w / (w + k_c) < c_min keep their state; the
+ *    stored score only decreases (strictly lower replaces it and its
+ *    direction); an accessible stored score (< n_c) with a new score >= n_c is
+ *    a conflict (a *= a_decay), a new score < n_c confirms
+ *    (a += a_recover (1 - a)); label AF_ACCESSIBLE iff stored score < n_c and
+ *    c a > ca_min, else AF_BLOCKED (AF_UNSCORED before the first evaluation).
+ * Needs af_set_tool before the first frame. Asynchronous on `stream`; the
+ * export and stats calls synchronise.
+ */
+typedef struct {
+    uint32_t capacity;     /* maximum number of points (AF_ERR_CAPACITY latched beyond) */
+    uint32_t k_nn;         /* 10: neighbours of the normal, 3..343                      */
+    int32_t nn_radius;     /* 3: neighbour search cube half-width in voxels, 1..3        */
+    uint32_t max_views;    /* 8: stored viewpoints per point, <= 8                       */
+    float view_min_dist;   /* 0.1 m                                                      */
+    float obs_dot;         /* 0.25                                                       */
+    float trig_tsdf;       /* 2 v                                                        */
+    float trig_move;       /* 0.1 m                                                      */
+    uint32_t budget;       /* evaluations per frame                                      */
+    float k_c;             /* 5                                                          */
+    float c_min;           /* 0.2                                                        */
+    float a_decay;         /* 0.75                                                       */
+    float a_recover;       /* 0.15                                                       */
+    float ca_min;          /* 0.7                                                        */
+} af_points_config;
+
+/* Allocates the layer: 2 KB per pool brick plus 200 B per point of capacity. */
+af_status af_points_enable(af_ctx *ctx, const af_points_config *cfg);
+/* Integrate one scan and update the point layer (see above). */
+af_status af_points_frame(af_ctx *ctx, const float *d_xyz, uint32_t n, const float pose[16],
+                          void *stream);
+/* Evaluate up to max_evals queued points in id order. */
+af_status af_points_drain(af_ctx *ctx, uint32_t max_evals, void *stream);
+/* Synchronises; number of points and evaluations of the last frame / drain. */
+af_status af_points_stats(af_ctx *ctx, uint32_t *count, uint32_t *last_evals);
+/* Synchronises; the first min(cap, count) points in id order (host arrays,
+ * any may be NULL): absolute voxel (x 3), normal (x 3), label, stored score
+ * (-1: never scored), stored direction, a, queued flag, stored viewpoints. */
+af_status af_points_export(af_ctx *ctx, uint32_t cap, int32_t *h_ijk, float *h_normal,
+                           uint8_t *h_label, int16_t *h_score, int16_t *h_best, float *h_a,
+                           uint8_t *h_queued, int32_t *h_nviews, uint32_t *out_count);
+
+/*
  * Kernel timing: when enabled, every launch of the context is bracketed by
  * CUDA events recorded on the launch's own stream. Index 0 = brick
  * allocation, 1 = cube integration, 2 = weight cap + bit view, 3 = scoring,

@@ -28,7 +28,8 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_profile_read", "af_integrate_scan_noalloc", "af_batch_create", "af_batch_destroy",
            "af_batch_tick", "af_batch_set_tuning", "af_batch_get_tuning", "af_soft_seed",
            "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
-           "af_soft_start", "af_last_error")
+           "af_soft_start", "af_points_enable", "af_points_frame", "af_points_drain",
+           "af_points_stats", "af_points_export", "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
@@ -74,6 +75,14 @@ class _Profile(C.Structure):
 class _Refine(C.Structure):
     _fields_ = [("steps", C.c_uint32), ("lr_dir", C.c_float), ("lr_h", C.c_float),
                 ("h_max", C.c_float)]
+
+
+class _PointsConfig(C.Structure):
+    _fields_ = [("capacity", C.c_uint32), ("k_nn", C.c_uint32), ("nn_radius", C.c_int32),
+                ("max_views", C.c_uint32), ("view_min_dist", C.c_float), ("obs_dot", C.c_float),
+                ("trig_tsdf", C.c_float), ("trig_move", C.c_float), ("budget", C.c_uint32),
+                ("k_c", C.c_float), ("c_min", C.c_float), ("a_decay", C.c_float),
+                ("a_recover", C.c_float), ("ca_min", C.c_float)]
 
 
 class _BatchItem(C.Structure):
@@ -132,6 +141,11 @@ def load(build: bool = True) -> C.CDLL:
                                          C.POINTER(_Refine), P, P, P]),
             "af_soft_best": (C.c_int, [P, P, C.c_uint64, U32, P, P, P, P, P]),
             "af_soft_start": (C.c_int, [P, P, P, U32, P, P]),
+            "af_points_enable": (C.c_int, [P, C.POINTER(_PointsConfig)]),
+            "af_points_frame": (C.c_int, [P, P, U32, P, P]),
+            "af_points_drain": (C.c_int, [P, U32, P]),
+            "af_points_stats": (C.c_int, [P, C.POINTER(U32), C.POINTER(U32)]),
+            "af_points_export": (C.c_int, [P, U32, P, P, P, P, P, P, P, P, C.POINTER(U32)]),
             "af_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -198,6 +212,31 @@ class MapConfig:
         c.block_edge = 8
         c.domain_min[:] = [int(x) for x in self.domain_min]
         c.domain_bricks[:] = [int(x) for x in self.domain_bricks]
+        return c
+
+
+@dataclass
+class PointsConfig:
+    """The stateful point layer (Sec. 3.4, 3.5); trig_tsdf is 2 v."""
+    trig_tsdf: float
+    capacity: int = 1 << 20
+    k_nn: int = 10
+    nn_radius: int = 3
+    max_views: int = 8
+    view_min_dist: float = 0.1
+    obs_dot: float = 0.25
+    trig_move: float = 0.1
+    budget: int = 0xFFFFFFFF
+    k_c: float = 5.0
+    c_min: float = 0.2
+    a_decay: float = 0.75
+    a_recover: float = 0.15
+    ca_min: float = 0.7
+
+    def _c(self) -> _PointsConfig:
+        c = _PointsConfig()
+        for k, _ in _PointsConfig._fields_:
+            setattr(c, k, getattr(self, k))
         return c
 
 
@@ -323,6 +362,46 @@ class Map:
                                           _np_ptr(fl), C.byref(out)), self._h)
         n = int(out.value)
         return dict(key=key[:n], S=S[:n], w=w[:n], flags=fl[:n])
+
+    # ---- the stateful point layer ----
+
+    def points_enable(self, cfg: "PointsConfig"):
+        """af_points_enable."""
+        self._pc = cfg._c()
+        _check(self._lib.af_points_enable(self._h, C.byref(self._pc)), self._h)
+
+    def points_frame(self, xyz, pose, stream=None):
+        """af_points_frame: integrate a scan and update the point layer."""
+        import torch
+        n = int(xyz.shape[0])
+        p = _dev_ptr(xyz, torch.float32, (3,)) if n else C.c_void_p(0)
+        pose = np.ascontiguousarray(pose, np.float32).reshape(16)
+        _check(self._lib.af_points_frame(self._h, p, n, _np_ptr(pose), _stream_ptr(stream)),
+               self._h)
+
+    def points_drain(self, max_evals: int, stream=None):
+        """af_points_drain: evaluate up to max_evals queued points."""
+        _check(self._lib.af_points_drain(self._h, max_evals, _stream_ptr(stream)), self._h)
+
+    def points_stats(self) -> tuple:
+        """(number of points, evaluations of the last frame or drain)."""
+        n, e = C.c_uint32(), C.c_uint32()
+        _check(self._lib.af_points_stats(self._h, C.byref(n), C.byref(e)), self._h)
+        return int(n.value), int(e.value)
+
+    def points_export(self) -> dict:
+        """Every point in id order: ijk, normal, label, score, best, a, queued, nviews."""
+        n, _ = self.points_stats()
+        out = dict(ijk=np.zeros((n, 3), np.int32), normal=np.zeros((n, 3), np.float32),
+                   label=np.zeros(n, np.uint8), score=np.zeros(n, np.int16),
+                   best=np.zeros(n, np.int16), a=np.zeros(n, np.float32),
+                   queued=np.zeros(n, np.uint8), nviews=np.zeros(n, np.int32))
+        cnt = C.c_uint32()
+        _check(self._lib.af_points_export(self._h, n, *(_np_ptr(out[k]) for k in
+                                                        ("ijk", "normal", "label", "score", "best",
+                                                         "a", "queued", "nviews")),
+                                          C.byref(cnt)), self._h)
+        return out
 
     # ---- the differentiable form ----
 

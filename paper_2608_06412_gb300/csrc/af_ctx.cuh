@@ -40,6 +40,23 @@ struct af_ctx {
   float* d_table = nullptr;  // seed directions, and their host copy
   uint32_t table_cap = 0;
   std::vector<float> h_table;
+  // the stateful point layer (af_points_enable)
+  bool pts_on = false;
+  af_points_config pcfg{};
+  int32_t* d_pid = nullptr;
+  af::PtState* d_pst = nullptr;
+  float4* d_pviews = nullptr;
+  unsigned long long* d_pnew = nullptr;
+  uint32_t* d_pchg = nullptr;
+  uint32_t* d_pnear = nullptr;
+  uint32_t* d_pchglist = nullptr;
+  uint32_t* d_psel = nullptr;
+  uint32_t* d_pblock = nullptr;
+  af::PtCounters* d_pcount = nullptr;
+  int4* d_pnnoff = nullptr;
+  int pnoff = 0;
+  float q_last[3] = {0.f, 0.f, 0.f};
+  bool have_q_last = false;
   // host counters
   uint64_t scans = 0, returns_in = 0, points_in = 0;
   // kernel profiling: CUDA events around each launch on its own stream

@@ -197,6 +197,51 @@ struct RefineArgs {
   float lr_dir, lr_h, h_max;
 };
 
+// ---- the stateful layer around scoring (Sec. 3.4, 3.5) ----
+
+// One surface point (64 bytes). Its stored viewpoints live in a separate
+// array, max 8 per point.
+struct PtState {
+  int32_t x, y, z;    // box-relative voxel
+  uint32_t blk;       // pool index of its brick
+  float qsum[3];      // sum of the sensor positions of the scans that saw it
+  uint32_t nobs;      // number of such scans
+  uint32_t last_scan; // stamp of the last of them
+  float last_tsdf;    // TSDF at its voxel after the previous frame
+  float a;            // accessibility confidence
+  float n[3];         // normal of the last evaluation
+  int16_t score, best;  // stored best score (-1: never scored) and direction
+  uint8_t queued, label, nviews, pad;
+};
+
+struct PtCounters {
+  uint32_t count;  // points
+  uint32_t nnew;   // points new in this frame
+  uint32_t nchg;   // bricks overlapped by the frame's cubes
+  uint32_t nsel;   // points selected for evaluation
+  uint32_t evals;  // evaluations of the last call
+  uint32_t pad[3];
+};
+
+// Parameters of the layer as the kernels read them.
+struct PtView {
+  PtState* st;
+  float4* views;         // capacity * 8
+  int32_t* pid;          // point id per voxel of every pool brick, -1 none, -2 being created
+  unsigned long long* newkeys;
+  uint32_t* chg;         // per pool brick: stamp of the last frame whose cubes overlap it
+  uint32_t* near;        // per pool brick: stamp of the last frame with such a brick next to it
+  uint32_t* chglist;
+  uint32_t* sel;
+  uint32_t* blocksum;
+  PtCounters* C;
+  const int4* nnoff;     // neighbour offsets, nearest first, ties in (dz, dy, dx) order
+  int noff;
+  uint32_t capacity;
+  int k_nn, nn_radius, max_views;
+  float view_min_dist2, obs_dot, trig_tsdf, k_c, c_min, a_decay, a_recover, ca_min;
+};
+
 // ---- batched ticks: many maps in one set of persistent launches ----
 
 // One map's share of a batched tick, rewritten every tick. The offsets are

@@ -1,0 +1,100 @@
+"""The stateful point layer on the GPU (af_points_*) against the oracle's
+(or_pts_*), frame by frame on the same scans: point ids and voxels, normals,
+labels, stored scores and directions, accessibility confidence a, queue
+flags and stored viewpoints, all bit for bit -- under a per-frame budget
+that leaves a backlog, after draining it, and through the triggers of a
+moving sensor and a changing scene."""
+import numpy as np
+import pytest
+
+import oracle
+from parity import oracle_config, oracle_tool, to_dev
+from paper_2608_06412_gb300 import af, synth, workload
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("ijk", "normal", "label", "score", "best", "a", "queued", "nviews")
+
+
+def _compare(g, o, what):
+    assert len(g["label"]) == len(o["label"]), (what, len(g["label"]), len(o["label"]))
+    for k in FIELDS:
+        a, b = g[k], o[k]
+        if k in ("normal", "a"):
+            a, b = a.view(np.uint32), b.view(np.uint32)      # bit for bit
+        bad = np.nonzero((a != b).reshape(len(a), -1).any(1))[0]
+        assert len(bad) == 0, f"{what}: {k} differs at {len(bad)} points, first {bad[0]}: " \
+                              f"gpu {g[k][bad[0]]} oracle {o[k][bad[0]]}"
+
+
+def _pair(W, pc, caps, G=None):
+    g = af.Map(W.af_config(**caps))
+    dirs = W.dirs if G is None else synth.fibonacci_dirs(G)
+    g.set_tool(W.af_tool(), dirs)
+    g.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], **pc))
+    om = oracle.Map(oracle_config(W))
+    op = oracle.PointSet(om, oracle.PointsConfig(trig_tsdf=2 * W.params["v"],
+                                                 **{k: v for k, v in pc.items() if k != "capacity"}),
+                         oracle_tool(W), dirs)
+    return g, om, op
+
+
+def test_points_single_frame_scene_moving_sensor():
+    """The sphere / wall / slotted-plate scene from a sensor that moves 4 cm
+    per frame: new points, viewpoints, neighbourhood and motion triggers, a
+    budget of 150 evaluations per frame, then the backlog drained."""
+    W = workload.single_frame()
+    caps = dict(hash_capacity=1 << 16, pool_blocks=1 << 14, max_returns=1 << 15, max_points=1 << 12)
+    g, om, op = _pair(W, dict(budget=150, capacity=1 << 16), caps)
+    scene = W.scene
+    for f in range(8):
+        fr = synth.cone_frame(scene, 6000, 0.01, 100 + f, origin=(0.0, 0.04 * f, 0.02 * f))
+        g.points_frame(to_dev(fr.pts), fr.pose)
+        op.frame(fr.pts, fr.pose)
+        _compare(g.points_export(), op.export(), f"frame {f}")
+    g.points_drain(10 ** 6)
+    op.drain(10 ** 6)
+    ge, oe = g.points_export(), op.export()
+    _compare(ge, oe, "drained")
+    assert (ge["queued"] == 0).all()
+    assert (ge["label"] == af.ACCESSIBLE).any() and (ge["label"] == af.BLOCKED).any()
+    assert (ge["nviews"] >= 2).any() and (ge["score"] >= 0).mean() > 0.5
+    assert g.sync_status() == 0
+
+
+def test_points_pine_stream():
+    """Ten frames of the pine stream (K = 32 directions), 400 evaluations per frame."""
+    W = workload.pine_stream()
+    caps = dict(hash_capacity=1 << 18, pool_blocks=1 << 16, max_returns=1 << 15, max_points=1 << 12)
+    g, om, op = _pair(W, dict(budget=400, capacity=1 << 18), caps, G=64)
+    for f in range(10):
+        fr, _, _ = workload.pine_frame(W, f)
+        g.points_frame(to_dev(fr.pts), fr.pose)
+        op.frame(fr.pts, fr.pose)
+    _compare(g.points_export(), op.export(), "frame 9")
+    n, ev = g.points_stats()
+    assert ev == 400 and n > 10_000
+    g.points_drain(2000)
+    op.drain(2000)
+    _compare(g.points_export(), op.export(), "after a drain of 2000")
+
+
+def test_points_arguments():
+    W = workload.single_frame()
+    caps = dict(hash_capacity=1 << 14, pool_blocks=1 << 12, max_returns=1 << 12, max_points=1 << 10)
+    g = af.Map(W.af_config(**caps))
+    with pytest.raises(af.AfError) as e:
+        g.points_frame(to_dev(np.zeros((1, 3), np.float32)), np.eye(4))
+    assert e.value.status == af.ERR_STATE
+    with pytest.raises(af.AfError) as e:
+        g.points_enable(af.PointsConfig(trig_tsdf=0.04, nn_radius=4))
+    assert e.value.status == af.ERR_INVALID_ARG
+    g.points_enable(af.PointsConfig(trig_tsdf=0.04, capacity=16))
+    with pytest.raises(af.AfError) as e:
+        g.points_frame(to_dev(np.zeros((1, 3), np.float32)), np.eye(4))
+    assert e.value.status == af.ERR_STATE             # no tool yet
+    g.set_tool(W.af_tool(), W.dirs)
+    fr = synth.cone_frame(W.scene, 500, 0.01, 3)
+    g.points_frame(to_dev(fr.pts), fr.pose)          # more points than capacity
+    n, _ = g.points_stats()
+    assert n == 16 and g.sync_status() == af.ERR_CAPACITY
