@@ -53,6 +53,9 @@ def _args():
     ap.add_argument("--soft", action="store_true",
                     help="the differentiable form on the pine map after 300 frames")
     ap.add_argument("--soft-points", type=int, default=100_000)
+    ap.add_argument("--points", action="store_true",
+                    help="the stateful point layer over the pine stream")
+    ap.add_argument("--points-budget", type=int, default=16384)
     return ap.parse_args()
 
 
@@ -730,6 +733,80 @@ def run_soft(args, local):
     return out
 
 
+def run_points(args, local):
+    """The stateful point layer (Sec. 3.4, 3.5) over the pine stream: each
+    step integrates one frame and updates the point set -- new points,
+    viewpoints, triggers, up to `budget` evaluations with PCA normals and the
+    observation-side filter."""
+    import torch
+    from paper_2608_06412_gb300 import af, workload
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = workload.pine_stream()
+    nfr = args.warmup + args.steps
+    frames = _frames(W, 0, nfr)
+    g = af.Map(W.af_config(**workload.BENCH_CAPS))
+    g.set_tool(W.af_tool(), W.dirs)
+    g.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], budget=args.points_budget,
+                                    capacity=1 << 21))
+    d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    for k in range(args.warmup):
+        g.points_frame(d_xyz[k], frames[k][0].pose)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    evals = 0
+    clocks = Clocks(local)
+    clocks.start()
+    clocks.mark(True)
+    for i, k in enumerate(range(args.warmup, nfr)):
+        flush.zero_()
+        ev[i][0].record(stream)
+        g.points_frame(d_xyz[k], frames[k][0].pose)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(False)
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    # evaluations per frame, counted in a second pass over the same frames
+    g2 = af.Map(W.af_config(**workload.BENCH_CAPS))
+    g2.set_tool(W.af_tool(), W.dirs)
+    g2.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], budget=args.points_budget,
+                                     capacity=1 << 21))
+    per = []
+    for k in range(nfr):
+        g2.points_frame(d_xyz[k], frames[k][0].pose)
+        if k >= args.warmup:
+            per.append(g2.points_stats()[1])
+    evals = sum(per)
+    n, _ = g.points_stats()
+    e = g.points_export()
+    total = sum(ms)
+    out = {
+        "metric": "stateful point-layer evaluations/s (integration + point set + triggers + budgeted evaluation)",
+        "value": evals / (total / 1e3), "unit": "evaluations/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+        "data": "synthetic",
+        "config": {"workload": W.name, "budget": args.points_budget, "K": W.params["K"],
+                   "G": len(W.dirs), "l2": "flushed between steps (256 MiB write)"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "max": float(max(ms))},
+        "evaluations_per_frame": {"mean": float(np.mean(per)), "max": int(max(per))},
+        "points": n,
+        "labels": {"unscored": int((e["label"] == 0).sum()),
+                   "accessible": int((e["label"] == 1).sum()),
+                   "blocked": int((e["label"] == 2).sum()),
+                   "queued": int(e["queued"].sum())},
+        "clocks": clk,
+    }
+    g.close()
+    g2.close()
+    return out
+
+
 def main():
     args = _args()
     ws, rank, local = _dist()
@@ -739,6 +816,9 @@ def main():
         return
     if args.soft:
         print(json.dumps(run_soft(args, local)), flush=True)
+        return
+    if args.points:
+        print(json.dumps(run_points(args, local)), flush=True)
         return
     if ws > 1:
         import torch.distributed as dist

@@ -62,6 +62,30 @@ def test_points_single_frame_scene_moving_sensor():
     assert g.sync_status() == 0
 
 
+def test_points_non_default_parameters():
+    """Every parameter of the layer away from the paper's value: a 5^3
+    neighbour cube with 6 neighbours, 3 viewpoints 5 cm apart, a stricter
+    observation filter, a high confidence gate, a faster motion trigger and
+    other confidence constants; budget 200."""
+    W = workload.single_frame()
+    caps = dict(hash_capacity=1 << 16, pool_blocks=1 << 14, max_returns=1 << 15, max_points=1 << 12)
+    pc = dict(budget=200, capacity=1 << 16, k_nn=6, nn_radius=2, max_views=3, view_min_dist=0.05,
+              obs_dot=0.5, c_min=0.9, k_c=3.0, trig_move=0.05, a_decay=0.5, a_recover=0.3,
+              ca_min=0.6)
+    g, om, op = _pair(W, pc, caps)
+    for f in range(8):
+        fr = synth.cone_frame(W.scene, 6000, 0.01, 200 + f, origin=(0.0, 0.03 * f, -0.02 * f))
+        g.points_frame(to_dev(fr.pts), fr.pose)
+        op.frame(fr.pts, fr.pose)
+        _compare(g.points_export(), op.export(), f"frame {f}")
+    g.points_drain(10 ** 6)
+    op.drain(10 ** 6)
+    ge = g.points_export()
+    _compare(ge, op.export(), "drained")
+    assert ge["nviews"].max() == 3 and (ge["score"] == -1).any() and (ge["score"] >= 0).any()
+    assert g.sync_status() == 0
+
+
 def test_points_pine_stream():
     """Ten frames of the pine stream (K = 32 directions), 400 evaluations per frame."""
     W = workload.pine_stream()

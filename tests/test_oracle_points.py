@@ -4,17 +4,21 @@ and mathematics fix:
 
 * the Jacobi eigen-solver against numpy's LAPACK solver, residuals and
   orthonormality, and the diagonal case (no rotation at all);
+* normals on a voxelised sphere against a brute-force restatement (nearest
+  neighbours by sorting, float64 covariance, numpy's eigen-solver);
 * PCA normals on an axis-aligned wall equal the wall normal exactly, facing
   the sensor; points are numbered in (z, y, x) order within a frame;
 * viewpoints are stored only when farther than the minimum distance from all
-  stored ones, at most max_views;
+  stored ones, at most max_views (8, and 3 when configured so);
+* the confidence gate skips exactly the points with w / (w + k_c) < c_min;
 * every scored best direction is aligned (> obs_dot) with a stored viewpoint;
 * the budget evaluates the lowest ids first and the backlog drains in order;
 * the paper's worked example: a well-observed accessible point stays
   accessible after one conflicting evaluation (c a = 0.75) and leaves the
   accessible set after two (c a = 0.5625 < 0.7), its stored score unchanged;
 * a sensor move above trig_move re-queues blocked points, a smaller one
-  does not; returns far away queue nothing.
+  does not, and the distance is measured from where the trigger last fired;
+  returns far away queue nothing.
 Parity status: pinned.
 """
 import numpy as np
@@ -88,6 +92,45 @@ def test_wall_normals_ids_and_views():
     assert (e["nviews"] == 1).all()
 
 
+def _sphere(c=(1.5, 0.0, 0.0), r=0.3):
+    c = np.asarray(c, float)
+    g = synth.Group(a=c, b=c, radius=r * 1.01, spheres=np.array([[*c, r]]))
+    return synth.Scene([g], *synth._bounds([g]))
+
+
+def test_pca_normals_match_brute_force_eigh():
+    """Normals on a voxelised sphere against a brute-force restatement: the 10
+    nearest points of the final set in the +-3 cube (ties by dz, dy, dx), the
+    covariance in float64 and numpy's symmetric eigen-solver, the smallest
+    eigenvector turned toward the sensor."""
+    mp = oracle.Map(_cfg())
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V), _tool(), synth.fibonacci_dirs(64))
+    origin = np.zeros(3)
+    pts, pose = _frame(_sphere(), origin, n=6000)
+    P.frame(pts, pose)
+    e = P.export()
+    ijk = e["ijk"].astype(np.int64)
+    keys = {tuple(x): i for i, x in enumerate(ijk)}
+    R = 3
+    offs = [(x, y, z) for z in range(-R, R + 1) for y in range(-R, R + 1) for x in range(-R, R + 1)]
+    offs.sort(key=lambda o: (o[0] ** 2 + o[1] ** 2 + o[2] ** 2, o[2], o[1], o[0]))
+    checked = 0
+    for i in np.flatnonzero(e["score"] >= 0):
+        nb = [o for o in offs if tuple(ijk[i] + o) in keys][:10]
+        d = np.array(nb, np.float64)
+        C = (d - d.mean(0)).T @ (d - d.mean(0))
+        w, Vm = np.linalg.eigh(C)
+        if (w[1] - w[0]) < 0.05 * w[2]:
+            continue   # near-degenerate smallest pair: the direction is ill-posed
+        n = Vm[:, 0]
+        s = (ijk[i] + 0.5) * V
+        if n @ (origin - s) < 0:
+            n = -n
+        assert np.abs(e["normal"][i] - n).max() < 2e-4, (i, e["normal"][i], n)
+        checked += 1
+    assert checked > 200
+
+
 def test_view_storage_rule():
     mp = oracle.Map(_cfg())
     P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, budget=0), _tool(),
@@ -108,6 +151,15 @@ def test_view_storage_rule():
     # greedy storage: any two stored positions are > 10 cm apart, so at most
     # 3 of these 5 (storing every scan would give 5, a reversed test 1)
     assert e2["nviews"].max() == 3 and (e2["nviews"] == 3).sum() > 20
+    # max_views = 3 with more positions far apart: exactly 3 are kept
+    P3 = oracle.PointSet(oracle.Map(_cfg()),
+                         oracle.PointsConfig(trig_tsdf=2 * V, budget=0, max_views=3), _tool(),
+                         synth.fibonacci_dirs(32))
+    for k in range(6):    # 0, 12, ..., 60 cm: six storable positions
+        pts, pose = _frame(wall, (0.0, 0.12 * k, 0.0), n=3000, seed=k)
+        P3.frame(pts, pose)
+    e3 = P3.export()
+    assert e3["nviews"].max() == 3 and (e3["nviews"] == 3).sum() > 20
 
 
 def test_observation_side_filter():
@@ -211,6 +263,11 @@ def test_motion_trigger_and_locality():
     P.frame(pts, pose)
     q = P.export()["queued"][:n0].astype(bool)
     assert (q == blocked).all()
+    # 17 cm from the start but 5 cm from the last firing: nothing is re-queued
+    P.drain(10 ** 9)
+    pts, pose = _frame(sfar, (0.0, 0.17, 0.0), n=500, seed=2)
+    P.frame(pts, pose)
+    assert (P.export()["queued"][:n0] == 0).all()
 
 
 def test_state_update_rules():
@@ -272,3 +329,15 @@ def test_neighbour_brick_trigger_and_confidence_gate():
     e2 = P2.export()
     assert len(e2["score"]) >= 20 and (e2["queued"] == 0).all()
     assert (e2["score"] == -1).mean() > 0.8     # (a few returns share cubes: w >= 2 there)
+    # a dense scan with the gate at c = 0.958 (w >= 115): exactly the points
+    # below it keep no score and no normal
+    mp3 = oracle.Map(_cfg())
+    P3 = oracle.PointSet(mp3, oracle.PointsConfig(trig_tsdf=2 * V, c_min=0.958), _tool(), dirs)
+    pts, pose = _frame(_wall(), (0.0, 0.0, 0.0), n=6000)
+    P3.frame(pts, pose)
+    e3 = P3.export()
+    w = np.array([mp3.voxel(*x)[1] for x in e3["ijk"]], np.float32)
+    low = (w / (w + np.float32(5))) < np.float32(0.958)
+    assert 200 < low.sum() < len(low) - 200
+    assert (e3["score"][low] == -1).all() and (e3["normal"][low] == 0).all()
+    assert (e3["score"][~low] >= 0).mean() > 0.95
