@@ -56,6 +56,12 @@ def _args():
     ap.add_argument("--points", action="store_true",
                     help="the stateful point layer over the pine stream")
     ap.add_argument("--points-budget", type=int, default=16384)
+    ap.add_argument("--ring", action="store_true",
+                    help="--points: the paper's approach set, 180 yaw directions and a 70 degree cone")
+    ap.add_argument("--c2f", action="store_true",
+                    help="--points --ring: coarse-to-fine search (20 degrees, +-24 degrees, 0.3 m)")
+    ap.add_argument("--clamp-signed", action="store_true",
+                    help="--points: the [-tau, tau] clamp ablation (Tab. 4)")
     return ap.parse_args()
 
 
@@ -742,13 +748,24 @@ def run_points(args, local):
     from paper_2608_06412_gb300 import af, workload
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    from paper_2608_06412_gb300 import synth
     W = workload.pine_stream()
     nfr = args.warmup + args.steps
     frames = _frames(W, 0, nfr)
-    g = af.Map(W.af_config(**workload.BENCH_CAPS))
-    g.set_tool(W.af_tool(), W.dirs)
-    g.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], budget=args.points_budget,
-                                    capacity=1 << 21))
+    tool, dirs = W.af_tool(), W.dirs
+    if args.ring:
+        tool.cos_theta_max = synth.COS_70
+        dirs = synth.yaw_ring(180)
+    c2f = dict(c2f_stride=10, c2f_half=12, c2f_radius=0.3) if args.c2f else {}
+    caps = dict(workload.BENCH_CAPS, clamp_signed=int(args.clamp_signed))
+
+    def layer():
+        m = af.Map(W.af_config(**caps))
+        m.set_tool(tool, dirs)
+        m.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], budget=args.points_budget,
+                                        capacity=1 << 21, **c2f))
+        return m
+    g = layer()
     d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
     flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -771,10 +788,7 @@ def run_points(args, local):
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     # evaluations per frame, counted in a second pass over the same frames
-    g2 = af.Map(W.af_config(**workload.BENCH_CAPS))
-    g2.set_tool(W.af_tool(), W.dirs)
-    g2.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], budget=args.points_budget,
-                                     capacity=1 << 21))
+    g2 = layer()
     per = []
     for k in range(nfr):
         g2.points_frame(d_xyz[k], frames[k][0].pose)
@@ -790,8 +804,11 @@ def run_points(args, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
         "data": "synthetic",
-        "config": {"workload": W.name, "budget": args.points_budget, "K": W.params["K"],
-                   "G": len(W.dirs), "l2": "flushed between steps (256 MiB write)"},
+        "config": {"workload": W.name, "budget": args.points_budget,
+                   "directions": "yaw ring, 70 deg cone" if args.ring else "Fibonacci sphere",
+                   "G": len(dirs), "search": "coarse-to-fine" if args.c2f else "full",
+                   "clamp": "[-tau, tau]" if args.clamp_signed else "[0, tau]",
+                   "l2": "flushed between steps (256 MiB write)"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                        "max": float(max(ms))},
         "evaluations_per_frame": {"mean": float(np.mean(per)), "max": int(max(per))},
@@ -800,6 +817,7 @@ def run_points(args, local):
                    "accessible": int((e["label"] == 1).sum()),
                    "blocked": int((e["label"] == 2).sum()),
                    "queued": int(e["queued"].sum())},
+        "with_direction": int((e["best"] >= 0).sum()),
         "clocks": clk,
     }
     g.close()

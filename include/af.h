@@ -56,7 +56,8 @@ enum { AF_KERNEL_TOOL = 0, AF_KERNEL_CORRIDOR = 1 };
  */
 typedef struct {
     float voxel_size;     /* v                                                  */
-    float truncation;     /* tau; contributions are clamped to [0, tau]        */
+    float truncation;     /* tau; contributions are clamped to [0, tau]        *
+                           * ([-tau, tau] with clamp_signed)                   */
     float r_c;            /* collision threshold: occupied iff TSDF < r_c      */
     float cone_cos;       /* voxels with cos(theta) > cone_cos behind a return
                              are not updated (Sec. 3.2; 0.95)                  */
@@ -75,6 +76,9 @@ typedef struct {
     uint32_t pool_blocks;      /* bricks that can be allocated                */
     uint32_t max_returns;      /* largest n per af_integrate_scan            */
     uint32_t max_points;       /* largest m per af_frame_host                */
+    int32_t clamp_signed;      /* 0: the paper's positive clamp [0, tau];     *
+                                * 1: [-tau, tau], the ablation of Tab. 4.     *
+                                * Only the clamp changes; S may then be < 0.  */
 } af_config;
 
 /* A cylinder tool of radius r and length L whose tip (the interaction point)
@@ -181,12 +185,13 @@ af_status af_block_count(af_ctx *ctx, uint32_t *out);
  * of them (order unspecified). Brick b covers voxels
  * (domain_min + key) * 8 + (lx, ly, lz), voxel l = lx + 8 ly + 64 lz.
  *  h_key     : cap x 3 int32   brick coordinates (absolute, in bricks)
- *  h_S       : cap x 512 uint64 SDF sums in units of 2^-20 m
+ *  h_S       : cap x 512 int64  SDF sums in units of 2^-20 m (negative only
+ *              with clamp_signed)
  *  h_w       : cap x 512 uint32 weights
  *  h_flags   : cap x 512 uint8  bit0 cleared, bit1 occupied, bit2 known
  * *out_count receives the number written.
  */
-af_status af_export_blocks(af_ctx *ctx, uint32_t cap, int32_t *h_key, uint64_t *h_S,
+af_status af_export_blocks(af_ctx *ctx, uint32_t cap, int32_t *h_key, int64_t *h_S,
                            uint32_t *h_w, uint8_t *h_flags, uint32_t *out_count);
 
 /*
@@ -369,7 +374,15 @@ af_status af_soft_best(af_ctx *ctx, const float *d_c, uint64_t n, uint32_t per_p
  *    direction); an accessible stored score (< n_c) with a new score >= n_c is
  *    a conflict (a *= a_decay), a new score < n_c confirms
  *    (a += a_recover (1 - a)); label AF_ACCESSIBLE iff stored score < n_c and
- *    c a > ca_min, else AF_BLOCKED (AF_UNSCORED before the first evaluation).
+ *    c a > ca_min, else AF_BLOCKED (AF_UNSCORED before the first evaluation);
+ *  - coarse-to-fine search (Sec. 3.6; c2f_stride > 0), for a direction table
+ *    in ring order such as the paper's 180-direction yaw ring: the directions
+ *    searched are every c2f_stride-th one and those within c2f_half indices
+ *    (circularly) of a centre: the stored best direction of the nearest
+ *    other point within c2f_radius (voxel-centre distance, ties in
+ *    (dz, dy, dx) order) among those that had one when the batch began, else
+ *    the coarse set's own best; lowest-index minimum over the searched
+ *    candidates.
  * Needs af_set_tool before the first frame. Asynchronous on `stream`; the
  * export and stats calls synchronise.
  */
@@ -388,6 +401,9 @@ typedef struct {
     float a_decay;         /* 0.75                                                       */
     float a_recover;       /* 0.15                                                       */
     float ca_min;          /* 0.7                                                        */
+    uint32_t c2f_stride;   /* 0: full search; yaw ring of 180: 10 (20 degrees)           */
+    uint32_t c2f_half;     /* window half-width in directions; yaw ring: 12 (+-24 deg)   */
+    float c2f_radius;      /* neighbour radius, 0.3 m; below 32 voxels                   */
 } af_points_config;
 
 /* Allocates the layer: 2 KB per pool brick plus 200 B per point of capacity. */
@@ -438,8 +454,10 @@ af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);
  *  box_min, box_dim : the output box in absolute voxel indices; voxel
  *                     (x, y, z) is element ((z - z0) * dy + (y - y0)) * dx +
  *                     (x - x0). Contributions outside the box are not kept.
- *  d_vox   : per voxel, (S << 20) | w: S the SDF sum in units of 2^-20 m,
- *            w the weight (device memory, caller-owned, in/out).
+ *  d_vox   : per voxel, S 2^20 + w in two's complement: S the SDF sum in
+ *            units of 2^-20 m (negative only with clamp_signed; recover it
+ *            by an arithmetic shift of the word as int64 by 20), w the
+ *            weight (device memory, caller-owned, in/out).
  *  d_flags : per voxel, bit0 ray-cleared, bit1 occupied, bit2 known
  *            (device memory, caller-owned, in/out).
  * The library allocates nothing: its per-return scratch is a fixed device

@@ -50,7 +50,7 @@ class _Config(C.Structure):
                 ("clear_hi", C.c_float), ("cube_radius", C.c_int32),
                 ("clear_samples", C.c_int32), ("w_min", C.c_uint32),
                 ("w_cap", C.c_uint32), ("dom_min", C.c_int32 * 3),
-                ("dom_size", C.c_int32 * 3)]
+                ("dom_size", C.c_int32 * 3), ("clamp_signed", C.c_int32)]
 
 
 class _Tool(C.Structure):
@@ -68,7 +68,8 @@ class _PtsConfig(C.Structure):
                 ("view_min_dist", C.c_float), ("obs_dot", C.c_float), ("trig_tsdf", C.c_float),
                 ("trig_move", C.c_float), ("budget", C.c_uint32), ("k_c", C.c_float),
                 ("c_min", C.c_float), ("a_decay", C.c_float), ("a_recover", C.c_float),
-                ("ca_min", C.c_float)]
+                ("ca_min", C.c_float), ("c2f_stride", C.c_uint32), ("c2f_half", C.c_uint32),
+                ("c2f_radius", C.c_float)]
 
 
 def _load():
@@ -83,10 +84,10 @@ def _load():
         lib.or_integrate.argtypes = [P, P, C.c_int64, P]
         lib.or_get_voxel.restype = C.c_int
         lib.or_get_voxel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32,
-                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_uint32),
                                      C.POINTER(C.c_int32)]
         lib.or_set_voxel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32,
-                                     C.c_uint64, C.c_uint32, C.c_int32]
+                                     C.c_int64, C.c_uint32, C.c_int32]
         lib.or_set_voxels.argtypes = [P, C.c_int64, P, P, P, P]
         lib.or_voxel_count.restype = C.c_int64
         lib.or_voxel_count.argtypes = [P]
@@ -147,12 +148,13 @@ class Config:
     clear_hi: float = 2.25
     w_min: int = 3
     w_cap: int = 2000
+    clamp_signed: int = 0   # 1: contributions clamped to [-tau, tau] (Tab. 4 ablation)
 
     def _c(self) -> _Config:
         c = _Config()
         for k in ("v", "tau", "r_c", "cone_cos", "range_min", "range_max",
                   "clear_lo", "clear_hi", "cube_radius", "clear_samples",
-                  "w_min", "w_cap"):
+                  "w_min", "w_cap", "clamp_signed"):
             setattr(c, k, getattr(self, k))
         c.dom_min[:] = [int(x) for x in self.dom_min]
         c.dom_size[:] = [int(x) for x in self.dom_size]
@@ -200,7 +202,7 @@ class Map:
         return int(self._lib.or_integrate(self._h, _ptr(pts), len(pts), _ptr(pose)))
 
     def voxel(self, i: int, j: int, k: int):
-        S, w, cl = C.c_uint64(), C.c_uint32(), C.c_int32()
+        S, w, cl = C.c_int64(), C.c_uint32(), C.c_int32()
         self._lib.or_get_voxel(self._h, i, j, k, C.byref(S), C.byref(w), C.byref(cl))
         return int(S.value), int(w.value), int(cl.value)
 
@@ -211,7 +213,7 @@ class Map:
                    cleared: np.ndarray | None = None):
         ijk = np.ascontiguousarray(ijk, np.int32).reshape(-1, 3)
         n = len(ijk)
-        S = np.ascontiguousarray(np.broadcast_to(S, (n,)), np.uint64)
+        S = np.ascontiguousarray(np.broadcast_to(S, (n,)), np.int64)
         w = np.ascontiguousarray(np.broadcast_to(w, (n,)), np.uint32)
         cl = np.zeros(n, np.uint8) if cleared is None else \
             np.ascontiguousarray(np.broadcast_to(cleared, (n,)), np.uint8)
@@ -230,7 +232,7 @@ class Map:
         """All stored voxels, sorted by (z, y, x)."""
         n = len(self)
         ijk = np.zeros((n, 3), np.int32)
-        S = np.zeros(n, np.uint64)
+        S = np.zeros(n, np.int64)
         w = np.zeros(n, np.uint32)
         cl = np.zeros(n, np.uint8)
         occ = np.zeros(n, np.uint8)
@@ -340,6 +342,11 @@ class PointsConfig:
     a_decay: float = 0.75
     a_recover: float = 0.15
     ca_min: float = 0.7
+    # coarse-to-fine search over a ring-ordered direction table (Sec. 3.6);
+    # for the 180-direction yaw ring: stride 10 (20 deg), half 12 (+-24 deg)
+    c2f_stride: int = 0
+    c2f_half: int = 0
+    c2f_radius: float = 0.3
 
     def _c(self) -> _PtsConfig:
         c = _PtsConfig()

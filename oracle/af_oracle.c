@@ -31,7 +31,10 @@
  *  - Contributions are accumulated exactly: S += round(d * 2^20) in integers
  *    and w += 1, so the result does not depend on the order of the returns.
  *  - The weight cap of Sec. 3.6 is applied once at the end of each scan:
- *    w > w_cap => S = floor(S * w_cap / w), w = w_cap.
+ *    w > w_cap => S = floor(S * w_cap / w), w = w_cap (floor also for a
+ *    negative S of the signed ablation).
+ *  - With clamp_signed (the [-tau, tau] ablation of Tab. 4) only the clamp
+ *    changes: the cube, the cone and the accumulation are the same.
  *  - The cleared band (clear_lo*tau, clear_hi*tau] is sampled at N_s points
  *    dist_j = clear_lo*tau + j*((clear_hi - clear_lo)*tau / N_s), j = 1..N_s,
  *    along the unit vector from p toward q; the voxel holding each sample is
@@ -91,7 +94,7 @@
 
 typedef struct {
     uint64_t key; /* 0 = empty slot */
-    uint64_t S;   /* sum of quantised contributions, units of 2^-20 m */
+    int64_t S;    /* sum of quantised contributions, units of 2^-20 m */
     uint32_t w;   /* number of contributions */
     int32_t cleared;
 } or_voxel;
@@ -102,6 +105,12 @@ struct or_map {
     uint64_t cap; /* power of two */
     uint64_t count;
 };
+
+/* floor(a / b) for b > 0 (C division truncates toward zero). */
+static int64_t floor_div(int64_t a, int64_t b) {
+    const int64_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
 
 static uint64_t pack_key(int32_t ix, int32_t iy, int32_t iz) {
     /* 21 bits per axis, offset so that the packed key is never 0. */
@@ -205,7 +214,7 @@ int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16
 int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[16],
                       int32_t *voxel_out) {
     const or_config *c = &m->cfg;
-    const float v = c->v, tau = c->tau;
+    const float v = c->v, tau = c->tau, lo = c->clamp_signed ? -c->tau : 0.0f;
     const int32_t mr = c->cube_radius;
     /* sensor origin q = translation of the world_from_sensor pose */
     const float q[3] = {pose[3], pose[7], pose[11]};
@@ -255,13 +264,14 @@ int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[1
                             ((a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]) / (sqrtf(aa) * range);
                         if (cos_theta > c->cone_cos) continue; /* behind the surface */
                     }
-                    /* d = ||p_i - q|| - ||x - q||, clamped to [0, tau] */
+                    /* d = ||p_i - q|| - ||x - q||, clamped to [0, tau]
+                       ([-tau, tau] in the signed ablation) */
                     const float e[3] = {x[0] - q[0], x[1] - q[1], x[2] - q[2]};
                     const float ee = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
                     float d = range - sqrtf(ee);
-                    if (d < 0.0f) d = 0.0f;
+                    if (d < lo) d = lo;
                     if (d > tau) d = tau;
-                    const uint64_t dq = (uint64_t)rintf(d * OR_SCALE);
+                    const int64_t dq = (int64_t)rintf(d * OR_SCALE);
                     or_voxel *vx = voxel_ref(m, j[0], j[1], j[2]);
                     vx->S += dq;
                     vx->w += 1;
@@ -287,14 +297,14 @@ int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[1
     for (uint64_t k = 0; k < m->cap; ++k) {
         or_voxel *vx = &m->slot[k];
         if (vx->key && vx->w > c->w_cap) {
-            vx->S = (uint64_t)(((unsigned __int128)vx->S * c->w_cap) / vx->w);
+            vx->S = floor_div(vx->S * (int64_t)c->w_cap, (int64_t)vx->w);
             vx->w = c->w_cap;
         }
     }
     return accepted;
 }
 
-int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz, uint64_t *S,
+int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz, int64_t *S,
                  uint32_t *w, int32_t *cleared) {
     const or_voxel *vx = voxel_get(m, ix, iy, iz);
     *S = vx ? vx->S : 0;
@@ -303,7 +313,7 @@ int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz, uint64_t *
     return vx != NULL;
 }
 
-void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz, uint64_t S, uint32_t w,
+void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz, int64_t S, uint32_t w,
                   int32_t cleared) {
     or_voxel *vx = voxel_ref(m, ix, iy, iz);
     vx->S = S;
@@ -311,7 +321,7 @@ void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz, uint64_t S, uin
     vx->cleared = cleared;
 }
 
-void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const uint64_t *S,
+void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const int64_t *S,
                    const uint32_t *w, const uint8_t *cleared) {
     for (int64_t k = 0; k < n; ++k)
         or_set_voxel(m, ijk[3 * k], ijk[3 * k + 1], ijk[3 * k + 2], S[k], w[k], cleared[k]);
@@ -324,8 +334,8 @@ const or_config *or_map_config(const or_map *m) { return &m->cfg; }
 /* TSDF < r_c, with r_c on the same 2^-20 m grid as S. */
 static int occ_of(const or_map *m, const or_voxel *vx) {
     if (!vx || vx->w == 0) return 0;
-    const uint64_t rcq = (uint64_t)rintf(m->cfg.r_c * OR_SCALE);
-    return vx->S < rcq * (uint64_t)vx->w;
+    const int64_t rcq = (int64_t)rintf(m->cfg.r_c * OR_SCALE);
+    return vx->S < rcq * (int64_t)vx->w;
 }
 
 static int known_of(const or_voxel *vx) { return vx && (vx->w >= 1 || vx->cleared); }
@@ -340,7 +350,7 @@ int or_known(const or_map *m, int32_t ix, int32_t iy, int32_t iz) {
     return known_of(voxel_get(m, ix, iy, iz));
 }
 
-void or_export(const or_map *m, int32_t *ijk, uint64_t *S, uint32_t *w, uint8_t *cleared,
+void or_export(const or_map *m, int32_t *ijk, int64_t *S, uint32_t *w, uint8_t *cleared,
                uint8_t *occ, uint8_t *known) {
     uint64_t o = 0;
     for (uint64_t k = 0; k < m->cap; ++k) {
@@ -514,7 +524,7 @@ void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G, c
 /* TSDF value of a voxel as single precision data: S / (w 2^20), or tau when
  * the voxel is unobserved or outside the box. */
 static double sdf_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz) {
-    uint64_t S;
+    int64_t S;
     uint32_t w;
     int32_t cl;
     if (!in_domain(&m->cfg, ix, iy, iz)) return (double)m->cfg.tau;

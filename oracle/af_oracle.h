@@ -34,6 +34,8 @@ typedef struct {
     uint32_t w_cap;     /* weight cap with proportional rescale of S (Sec. 3.6)   */
     int32_t dom_min[3]; /* map domain: voxel indices [dom_min, dom_min+dom_size) */
     int32_t dom_size[3];
+    int32_t clamp_signed; /* 0: d clamped to [0, tau] (Sec. 3.2); 1: [-tau, tau],
+                             the ablation of Tab. 4                              */
 } or_config;
 
 typedef struct {
@@ -66,15 +68,15 @@ int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[1
 
 /* Voxel state. Absent voxels report S = 0, w = 0, cleared = 0. */
 int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz,
-                 uint64_t *S, uint32_t *w, int32_t *cleared);
+                 int64_t *S, uint32_t *w, int32_t *cleared);
 void or_set_voxel(or_map *m, int32_t ix, int32_t iy, int32_t iz,
-                  uint64_t S, uint32_t w, int32_t cleared);
-void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const uint64_t *S,
+                  int64_t S, uint32_t w, int32_t cleared);
+void or_set_voxels(or_map *m, int64_t n, const int32_t *ijk, const int64_t *S,
                    const uint32_t *w, const uint8_t *cleared);
 int64_t or_voxel_count(const or_map *m);
 const or_config *or_map_config(const or_map *m);
 /* Writes every stored voxel: ijk (count x 3), S, w, cleared, occ, known. */
-void or_export(const or_map *m, int32_t *ijk, uint64_t *S, uint32_t *w,
+void or_export(const or_map *m, int32_t *ijk, int64_t *S, uint32_t *w,
                uint8_t *cleared, uint8_t *occ, uint8_t *known);
 int or_occ(const or_map *m, int32_t ix, int32_t iy, int32_t iz);
 int or_known(const or_map *m, int32_t ix, int32_t iy, int32_t iz);
@@ -132,6 +134,15 @@ typedef struct {
     float a_decay;        /* accessibility confidence a *= a_decay on conflict (0.75)  */
     float a_recover;      /* a += a_recover (1 - a) on confirmation (0.15)             */
     float ca_min;         /* confident-accessible iff score < n_c and c a > ca_min    */
+    /* Coarse-to-fine search (Sec. 3.6) over a direction table in ring order
+     * (the yaw ring): 0 = off. The evaluated directions are the coarse set
+     * {g : g mod c2f_stride = 0} and the window of indices within c2f_half
+     * (circularly) of a centre: the best direction of the nearest other point
+     * within c2f_radius whose stored best direction was set before this
+     * batch of evaluations, else the coarse set's own best. */
+    uint32_t c2f_stride;
+    uint32_t c2f_half;
+    float c2f_radius;
 } or_pts_config;
 
 typedef struct or_pts or_pts;

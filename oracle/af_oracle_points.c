@@ -43,6 +43,14 @@
  *    point (score < n_c) that scores s >= n_c is a conflict (a *= a_decay),
  *    a score s < n_c confirms (a += a_recover (1 - a)); the label is
  *    ACCESSIBLE iff the stored score < n_c and c a > ca_min, else BLOCKED.
+ *  - Coarse-to-fine search (Sec. 3.6), for a direction table in ring order
+ *    such as the paper's yaw ring: the directions searched are every
+ *    c2f_stride-th one and those within c2f_half indices (circularly) of a
+ *    centre. The centre is the stored best direction of the nearest other
+ *    point within c2f_radius (voxel-centre distance; ties in (dz, dy, dx)
+ *    order) among the points that had one when the batch of evaluations
+ *    began; without such a point, the best of the coarse set. The result is
+ *    the lowest-index minimum over the searched candidates.
  *
  * Floating point: single precision, one rounded operation at a time, in the
  * order written (build with -ffp-contract=off).
@@ -91,6 +99,9 @@ struct or_pts {
     keymap ids;        /* voxel key -> point id */
     int32_t (*off)[3]; /* neighbour offsets, nearest first */
     int32_t noff;
+    int32_t (*c2f_off)[3]; /* coarse-to-fine neighbour ball, nearest first, origin excluded */
+    int32_t c2f_noff;
+    int16_t *snap;         /* stored best directions when the current batch began */
     float q_last[3];
     int have_q_last;
     uint32_t scan;
@@ -157,7 +168,7 @@ static int in_box(const or_config *c, int32_t x, int32_t y, int32_t z) {
 
 /* TSDF of a voxel: S / (w 2^20) in double rounded to single, tau if w = 0. */
 static float tsdf_at(const or_map *m, const int32_t i[3], uint32_t *w_out) {
-    uint64_t S = 0;
+    int64_t S = 0;
     uint32_t w = 0;
     int32_t cl;
     if (in_box(or_map_config(m), i[0], i[1], i[2])) or_get_voxel(m, i[0], i[1], i[2], &S, &w, &cl);
@@ -258,6 +269,26 @@ or_pts *or_pts_new(const or_map *m, const or_pts_config *pc, const or_tool *t, c
                 ++k;
             }
     qsort(P->off, (size_t)P->noff, sizeof(int32_t[3]), off_cmp);
+    if (pc->c2f_stride > 0) {
+        /* offsets o != 0 with |o|^2 v^2 <= radius^2, evaluated in double */
+        const double v = (double)P->mc.v, r = (double)pc->c2f_radius;
+        const int32_t Rb = (int32_t)(r / v) + 1;
+        const int32_t Wb = 2 * Rb + 1;
+        P->c2f_off = (int32_t (*)[3])malloc(sizeof(int32_t[3]) * (size_t)Wb * Wb * Wb);
+        int32_t n = 0;
+        for (int32_t z = -Rb; z <= Rb; ++z)
+            for (int32_t y = -Rb; y <= Rb; ++y)
+                for (int32_t x = -Rb; x <= Rb; ++x) {
+                    const int32_t d2 = x * x + y * y + z * z;
+                    if (d2 == 0 || (double)d2 * v * v > r * r) continue;
+                    P->c2f_off[n][0] = x;
+                    P->c2f_off[n][1] = y;
+                    P->c2f_off[n][2] = z;
+                    ++n;
+                }
+        P->c2f_noff = n;
+        qsort(P->c2f_off, (size_t)n, sizeof(int32_t[3]), off_cmp);
+    }
     P->cap = 1024;
     P->p = (or_point *)calloc((size_t)P->cap, sizeof(or_point));
     km_init(&P->ids, 1024);
@@ -277,6 +308,8 @@ void or_pts_free(or_pts *P) {
     free(P->arm);
     free(P->dirs);
     free(P->off);
+    free(P->c2f_off);
+    free(P->snap);
     free(P->p);
     km_free(&P->ids);
     free(P);
@@ -353,6 +386,29 @@ static int pca_normal(const or_pts *P, const or_point *pt, float nrm[3]) {
     return 1;
 }
 
+/* Normal filter and observation-side filter of direction g (Sec. 3.4). */
+static int is_candidate(const or_pts *P, const float nrm[3], const float (*vu)[3], int32_t nv,
+                        int32_t g) {
+    const float *u = P->dirs + 3 * g;
+    const float nu = (nrm[0] * u[0] + nrm[1] * u[1]) + nrm[2] * u[2];
+    if (!(nu > P->tool.cos_theta_max)) return 0;
+    for (int32_t k = 0; k < nv; ++k)
+        if ((u[0] * vu[k][0] + u[1] * vu[k][1]) + u[2] * vu[k][2] > P->pc.obs_dot) return 1;
+    return 0;
+}
+
+/* Stored best direction, at the start of the batch, of the nearest other
+ * point within the coarse-to-fine radius that had one; -1 if none. */
+static int32_t nearest_resolved(const or_pts *P, const or_point *pt) {
+    for (int32_t k = 0; k < P->c2f_noff; ++k) {
+        const int32_t *o = P->c2f_off[k];
+        const int64_t id = km_get(&P->ids, vkey(pt->ijk[0] + o[0], pt->ijk[1] + o[1],
+                                               pt->ijk[2] + o[2]));
+        if (id >= 0 && P->snap[id] >= 0) return P->snap[id];
+    }
+    return -1;
+}
+
 static void evaluate(or_pts *P, const or_map *m, or_point *pt) {
     const int32_t n_c = (int32_t)P->tool.n_c;
     pt->queued = 0;
@@ -374,15 +430,33 @@ static void evaluate(or_pts *P, const or_map *m, or_point *pt) {
         for (int r = 0; r < 3; ++r) vu[k][r] = d[r] / len;
     }
 
+    /* the directions searched: all, or the coarse set and a window */
+    uint8_t *in_e = (uint8_t *)malloc((size_t)P->G);
+    const int32_t stride = (int32_t)P->pc.c2f_stride;
+    for (int32_t g = 0; g < P->G; ++g) in_e[g] = stride == 0 || g % stride == 0;
+    if (stride > 0) {
+        int32_t centre = nearest_resolved(P, pt);
+        if (centre < 0) { /* no resolved neighbour: the coarse set's own best */
+            int32_t cs = 0, found = 0;
+            for (int32_t g = 0; g < P->G; g += stride) {
+                if (!is_candidate(P, nrm, vu, pt->nviews, g)) continue;
+                const int32_t sc = dir_score(P, m, pt->ijk, g);
+                if (!found || sc < cs) {
+                    cs = sc;
+                    centre = g;
+                    found = 1;
+                }
+            }
+        }
+        if (centre >= 0)
+            for (int32_t g = 0; g < P->G; ++g) {
+                const int32_t d = abs(g - centre);
+                if ((d < P->G - d ? d : P->G - d) <= (int32_t)P->pc.c2f_half) in_e[g] = 1;
+            }
+    }
     int32_t best_s = n_c + 1, best_g = -1, found = 0;
     for (int32_t g = 0; g < P->G; ++g) {
-        const float *u = P->dirs + 3 * g;
-        const float nu = (nrm[0] * u[0] + nrm[1] * u[1]) + nrm[2] * u[2];
-        if (!(nu > P->tool.cos_theta_max)) continue;
-        int seen = 0;
-        for (int32_t k = 0; k < pt->nviews && !seen; ++k)
-            if ((u[0] * vu[k][0] + u[1] * vu[k][1]) + u[2] * vu[k][2] > P->pc.obs_dot) seen = 1;
-        if (!seen) continue;
+        if (!in_e[g] || !is_candidate(P, nrm, vu, pt->nviews, g)) continue;
         const int32_t sc = dir_score(P, m, pt->ijk, g);
         if (!found || sc < best_s) {
             best_s = sc;
@@ -390,6 +464,7 @@ static void evaluate(or_pts *P, const or_map *m, or_point *pt) {
             found = 1;
         }
     }
+    free(in_e);
     if (!found) best_g = -1; /* no candidate: blocked, no direction */
 
     or_pts_state_step(&P->pc, n_c, best_s, best_g, c, &pt->score, &pt->best, &pt->a, &pt->label);
@@ -412,6 +487,11 @@ void or_pts_state_step(const or_pts_config *pc, int32_t n_c, int32_t s, int32_t 
 
 int64_t or_pts_drain(or_pts *P, const or_map *m, int64_t max) {
     int64_t done = 0;
+    if (P->pc.c2f_stride > 0) { /* neighbours' directions as they were before this batch */
+        free(P->snap);
+        P->snap = (int16_t *)malloc(sizeof(int16_t) * (size_t)(P->n > 0 ? P->n : 1));
+        for (int64_t id = 0; id < P->n; ++id) P->snap[id] = P->p[id].best;
+    }
     for (int64_t id = 0; id < P->n && done < max; ++id)
         if (P->p[id].queued) {
             evaluate(P, m, &P->p[id]);

@@ -52,7 +52,8 @@ class _Config(C.Structure):
                 ("w_min", C.c_uint32), ("w_cap", C.c_uint32), ("block_edge", C.c_uint32),
                 ("domain_min", C.c_int32 * 3), ("domain_bricks", C.c_uint32 * 3),
                 ("hash_capacity", C.c_uint32), ("pool_blocks", C.c_uint32),
-                ("max_returns", C.c_uint32), ("max_points", C.c_uint32)]
+                ("max_returns", C.c_uint32), ("max_points", C.c_uint32),
+                ("clamp_signed", C.c_int32)]
 
 
 class _Tool(C.Structure):
@@ -82,7 +83,8 @@ class _PointsConfig(C.Structure):
                 ("max_views", C.c_uint32), ("view_min_dist", C.c_float), ("obs_dot", C.c_float),
                 ("trig_tsdf", C.c_float), ("trig_move", C.c_float), ("budget", C.c_uint32),
                 ("k_c", C.c_float), ("c_min", C.c_float), ("a_decay", C.c_float),
-                ("a_recover", C.c_float), ("ca_min", C.c_float)]
+                ("a_recover", C.c_float), ("ca_min", C.c_float), ("c2f_stride", C.c_uint32),
+                ("c2f_half", C.c_uint32), ("c2f_radius", C.c_float)]
 
 
 class _BatchItem(C.Structure):
@@ -202,12 +204,13 @@ class MapConfig:
     pool_blocks: int = 1 << 15
     max_returns: int = 1 << 16
     max_points: int = 1 << 16
+    clamp_signed: int = 0     # 1: contributions clamped to [-tau, tau] (Tab. 4 ablation)
 
     def _c(self) -> _Config:
         c = _Config()
         for k in ("voxel_size", "truncation", "r_c", "cone_cos", "range_min", "range_max",
                   "clear_lo", "clear_hi", "cube_radius", "clear_samples", "w_min", "w_cap",
-                  "hash_capacity", "pool_blocks", "max_returns", "max_points"):
+                  "hash_capacity", "pool_blocks", "max_returns", "max_points", "clamp_signed"):
             setattr(c, k, getattr(self, k))
         c.block_edge = 8
         c.domain_min[:] = [int(x) for x in self.domain_min]
@@ -232,6 +235,11 @@ class PointsConfig:
     a_decay: float = 0.75
     a_recover: float = 0.15
     ca_min: float = 0.7
+    # coarse-to-fine search over a ring-ordered direction table (Sec. 3.6);
+    # for the 180-direction yaw ring: stride 10 (20 deg), half 12 (+-24 deg)
+    c2f_stride: int = 0
+    c2f_half: int = 0
+    c2f_radius: float = 0.3
 
     def _c(self) -> _PointsConfig:
         c = _PointsConfig()
@@ -354,7 +362,7 @@ class Map:
         brick keys and per-voxel S, w, flags."""
         n = self.block_count() if cap is None else min(cap, self.block_count())
         key = np.zeros((max(n, 1), 3), np.int32)
-        S = np.zeros((max(n, 1), 512), np.uint64)
+        S = np.zeros((max(n, 1), 512), np.int64)
         w = np.zeros((max(n, 1), 512), np.uint32)
         fl = np.zeros((max(n, 1), 512), np.uint8)
         out = C.c_uint32()

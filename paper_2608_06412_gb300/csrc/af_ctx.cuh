@@ -55,6 +55,9 @@ struct af_ctx {
   af::PtCounters* d_pcount = nullptr;
   int4* d_pnnoff = nullptr;
   int pnoff = 0;
+  int4* d_pc2f = nullptr;     // coarse-to-fine neighbour ball
+  int pc2f_noff = 0, pc2f_R = 0;
+  int16_t* d_psnap = nullptr;
   float q_last[3] = {0.f, 0.f, 0.f};
   bool have_q_last = false;
   // host counters

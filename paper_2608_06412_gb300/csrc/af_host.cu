@@ -277,7 +277,8 @@ static void free_all(af_ctx* c) {
   cudaFree(c->d_table);
   for (void* p : {(void*)c->d_pid, (void*)c->d_pst, (void*)c->d_pviews, (void*)c->d_pnew,
                   (void*)c->d_pchg, (void*)c->d_pnear, (void*)c->d_pchglist, (void*)c->d_psel,
-                  (void*)c->d_pblock, (void*)c->d_pcount, (void*)c->d_pnnoff})
+                  (void*)c->d_pblock, (void*)c->d_pcount, (void*)c->d_pnnoff, (void*)c->d_pc2f,
+                  (void*)c->d_psnap})
     cudaFree(p);
   cudaFreeHost(c->h_status);
 }
@@ -298,6 +299,7 @@ static af_status check_config(const af_config* c) {
   if (c->clear_samples < 0 || c->clear_samples > 64) return bad("clear_samples must be in 0..64");
   if (c->block_edge != 8) return bad("block_edge must be 8");
   if (c->w_cap < 1) return bad("w_cap must be >= 1");
+  if (c->clamp_signed != 0 && c->clamp_signed != 1) return bad("clamp_signed must be 0 or 1");
   if (c->max_returns < 1) return bad("max_returns must be >= 1");
   if ((uint64_t)c->max_returns + c->w_cap >= (1ull << af::kWBits))
     return bad("max_returns + w_cap must be below 2^20");
@@ -336,6 +338,8 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   M.w_min = cfg->w_min;
   M.w_cap = cfg->w_cap;
   M.rcq = (uint64_t)rintf(cfg->r_c * af::kScale);
+  M.clamp_signed = cfg->clamp_signed;
+  M.dlo = cfg->clamp_signed ? -cfg->truncation : 0.f;
   for (int k = 0; k < 3; ++k) {
     M.dom_vox[k] = cfg->domain_min[k] * 8;
     M.dim_vox[k] = (int)cfg->domain_bricks[k] * 8;
@@ -591,7 +595,7 @@ extern "C" af_status af_block_count(af_ctx* ctx, uint32_t* out) {
   return AF_OK;
 }
 
-extern "C" af_status af_export_blocks(af_ctx* ctx, uint32_t cap, int32_t* h_key, uint64_t* h_S,
+extern "C" af_status af_export_blocks(af_ctx* ctx, uint32_t cap, int32_t* h_key, int64_t* h_S,
                                       uint32_t* h_w, uint8_t* h_flags, uint32_t* out_count) {
   if (!ctx || !out_count) return fail(ctx, AF_ERR_INVALID_ARG, "af_export_blocks: NULL argument");
   if (cap > 0 && (!h_key || !h_S || !h_w || !h_flags))
@@ -619,7 +623,7 @@ extern "C" af_status af_export_blocks(af_ctx* ctx, uint32_t cap, int32_t* h_key,
     h_key[3 * b + 2] = (int32_t)(k >> 42) + ctx->cfg.domain_min[2];
     for (int l = 0; l < af::kBrickVox; ++l) {
       const uint64_t wd = words[(size_t)b * af::kBrickVox + l];
-      h_S[(size_t)b * af::kBrickVox + l] = wd >> af::kWBits;
+      h_S[(size_t)b * af::kBrickVox + l] = af::word_S(wd);
       h_w[(size_t)b * af::kBrickVox + l] = (uint32_t)(wd & af::kWMask);
     }
   }

@@ -304,25 +304,25 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
           if (!decided && __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range)) > cone) continue;
         }
       }
-      // d = |p - q| - |x - q|, clamped to [0, tau]
+      // d = |p - q| - |x - q|, clamped to [0, tau] ([-tau, tau] in the ablation)
       const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
       const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
       float d;
-      if (cc >= bb) {
+      if (cc >= bb && !M.clamp_signed) {
         d = 0.f;  // |x - q| >= |p - q|: the rounded difference is <= 0
       } else if (cc > 1e-20f && range - sqrt_approx(cc) > tau + range * kMargin) {
         d = tau;  // the exact difference exceeds tau
       } else {
         d = __fsub_rn(range, __fsqrt_rn(cc));
-        d = d < 0.f ? 0.f : d;
+        d = d < M.dlo ? M.dlo : d;
         d = d > tau ? tau : d;
       }
-      const unsigned long long dq = (unsigned long long)__float2uint_rn(__fmul_rn(d, kScale));
+      const long long dq = __float2ll_rn(__fmul_rn(d, kScale));
       const int bl = ((jx >> 3) - b0.x) + BA * (((jy >> 3) - b0.y) + BA * ((jz >> 3) - b0.z));
       const uint32_t blk = s_blk[t][bl];
       if (blk >= M.pool_blocks) continue;
       const int l = (jx & 7) | ((jy & 7) << 3) | ((jz & 7) << 6);
-      atomicAdd(M.vox + (size_t)blk * kBrickVox + l, (dq << kWBits) | 1ull);
+      atomicAdd(M.vox + (size_t)blk * kBrickVox + l, make_word(dq, 1ull));
     }
   }
 
@@ -365,13 +365,14 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
     const uint64_t key = M.bkey[blk];
     unsigned long long* wp = M.vox + (size_t)blk * kBrickVox + l;
     unsigned long long word = *wp;
-    unsigned long long w = word & kWMask, S = word >> kWBits;
+    unsigned long long w = word & kWMask;
+    long long S = word_S(word);
     if (w > M.w_cap) {
-      S = S * M.w_cap / w;  // S < 2^44 and w_cap < 2^20: no overflow
+      S = capped_S(S, M.w_cap, (long long)w);  // |S| < 2^40, w_cap < 2^20: no overflow
       w = M.w_cap;
-      *wp = (S << kWBits) | w;
+      *wp = make_word(S, w);
     }
-    const bool o = w >= 1 && S < M.rcq * w;
+    const bool o = w >= 1 && S < (long long)M.rcq * (long long)w;
     const bool cl = (M.cleared[blk * 16 + wi] >> lane) & 1u;
     const bool kn = w >= 1 || cl;
     const unsigned ob = __ballot_sync(0xffffffffu, o);

@@ -7,10 +7,12 @@
 //             Keys are domain-relative brick coordinates packed 21 bits per
 //             axis; all ones marks an empty slot.
 //  * pool   : bricks of 8^3 voxels. Each voxel is ONE u64 word holding
-//             (S << 20) | w, so a contribution is a single 64-bit atomic add
-//             of (round(d 2^20) << 20) | 1 and integer addition makes the sum
-//             independent of the order of the returns. w < 2^20 is guaranteed
-//             by max_returns + w_cap < 2^20 and S < 2^44 by tau <= 1 m.
+//             S 2^20 + w in two's complement (S is negative only in the
+//             signed-clamp ablation), so a contribution is a single 64-bit
+//             atomic add of round(d 2^20) 2^20 + 1 and integer addition makes
+//             the sum independent of the order of the returns. w < 2^20 is
+//             guaranteed by max_returns + w_cap < 2^20, |S| < 2^40 by
+//             tau <= 1 m; S is the arithmetic shift of the word by 20.
 //             Next to it: 512 cleared bits per brick and the brick key.
 //  * planes : the occupied and known views as dense bit planes over the map
 //             box, one bit per voxel, rows along x (64 voxels per u64 word),
@@ -55,6 +57,22 @@ struct alignas(16) HashSlot {
 };
 
 // Everything a kernel needs about the map; passed by value.
+// The signed sum S of a voxel word (arithmetic shift: exact for any sign).
+__host__ __device__ inline long long word_S(unsigned long long word) {
+  return (long long)word >> kWBits;
+}
+
+// A voxel word from S and w (w < 2^20).
+__host__ __device__ inline unsigned long long make_word(long long S, unsigned long long w) {
+  return ((unsigned long long)S << kWBits) | w;
+}
+
+// Sec. 3.6's proportional rescale S w_cap / w, rounded toward minus infinity.
+__host__ __device__ inline long long capped_S(long long S, long long w_cap, long long w) {
+  const long long a = S * w_cap, q = a / w;
+  return (a % w != 0 && a < 0) ? q - 1 : q;
+}
+
 struct MapView {
   // geometry
   float v, tau, r_c, cone_cos, range_min, range_max, clear_lo, clear_hi;
@@ -63,6 +81,8 @@ struct MapView {
   int ns;             // cleared-band samples
   uint32_t w_min, w_cap;
   uint64_t rcq;       // round(r_c 2^20)
+  int clamp_signed;   // 1: contributions clamped to [-tau, tau] (Tab. 4 ablation)
+  float dlo;          // lower clamp of d: 0, or -tau with clamp_signed
   int dom_vox[3];     // absolute voxel index of the box's min corner
   int dim_vox[3];     // box size in voxels (multiples of 8)
   int row_words;      // u64 words per plane row
@@ -240,6 +260,12 @@ struct PtView {
   uint32_t capacity;
   int k_nn, nn_radius, max_views;
   float view_min_dist2, obs_dot, trig_tsdf, k_c, c_min, a_decay, a_recover, ca_min;
+  // coarse-to-fine search (stride 0: off)
+  int c2f_stride, c2f_half;
+  int c2f_R;             // ball radius in whole voxels (<= 31)
+  const int4* c2foff;    // the ball's offsets, origin excluded, nearest first
+  int c2f_noff;
+  int16_t* snap;         // stored best directions when the batch began
 };
 
 // ---- batched ticks: many maps in one set of persistent launches ----

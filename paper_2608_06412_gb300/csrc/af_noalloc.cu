@@ -135,10 +135,10 @@ __global__ void __launch_bounds__(256) k_na_integrate(MapView M, const float4* _
     const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
     const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
     float d = __fsub_rn(range, __fsqrt_rn(cc));
-    d = d < 0.f ? 0.f : d;
+    d = d < M.dlo ? M.dlo : d;
     d = d > M.tau ? M.tau : d;
-    const unsigned long long dq = (unsigned long long)__float2uint_rn(__fmul_rn(d, kScale));
-    atomicAdd(B.vox + at, (dq << kWBits) | 1ull);
+    const long long dq = __float2ll_rn(__fmul_rn(d, kScale));
+    atomicAdd(B.vox + at, make_word(dq, 1ull));
   } else if (e < pairs + band) {
     const uint64_t f = e - pairs;
     const uint32_t k = (uint32_t)(f / M.ns);
@@ -161,14 +161,15 @@ __global__ void __launch_bounds__(256) k_na_finalize(MapView M, Box B, uint64_t 
   for (uint64_t at = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; at < count;
        at += (uint64_t)gridDim.x * blockDim.x) {
     unsigned long long word = B.vox[at];
-    unsigned long long w = word & kWMask, S = word >> kWBits;
+    unsigned long long w = word & kWMask;
+    long long S = word_S(word);
     if (w > M.w_cap) {
-      S = S * M.w_cap / w;
+      S = capped_S(S, M.w_cap, (long long)w);
       w = M.w_cap;
-      B.vox[at] = (S << kWBits) | w;
+      B.vox[at] = make_word(S, w);
     }
     const unsigned cl = B.flags[at] & 1u;
-    const unsigned occ = (w >= 1 && S < M.rcq * w) ? 1u : 0u;
+    const unsigned occ = (w >= 1 && S < (long long)M.rcq * (long long)w) ? 1u : 0u;
     const unsigned kn = (w >= 1 || cl) ? 1u : 0u;
     B.flags[at] = (uint8_t)(cl | (occ << 1) | (kn << 2));
   }
@@ -199,7 +200,8 @@ extern "C" af_status af_integrate_scan_noalloc(const af_config* cfg, const float
       !(cfg->r_c > 0.f && cfg->r_c <= 1.f) || cfg->cube_radius < 1 || cfg->cube_radius > 8 ||
       cfg->clear_samples < 0 || cfg->clear_samples > 64 || cfg->block_edge != 8 ||
       cfg->w_cap < 1 || (uint64_t)AF_NOALLOC_MAX_RETURNS + cfg->w_cap >= (1ull << kWBits) ||
-      !(cfg->range_max > cfg->range_min) || !(cfg->clear_hi >= cfg->clear_lo))
+      !(cfg->range_max > cfg->range_min) || !(cfg->clear_hi >= cfg->clear_lo) ||
+      (cfg->clamp_signed != 0 && cfg->clamp_signed != 1))
     return nfail(AF_ERR_INVALID_ARG, "af_integrate_scan_noalloc: parameter out of range");
   uint64_t count = 1;
   for (int k = 0; k < 3; ++k) {
@@ -231,6 +233,8 @@ extern "C" af_status af_integrate_scan_noalloc(const af_config* cfg, const float
   M.w_min = cfg->w_min;
   M.w_cap = cfg->w_cap;
   M.rcq = (uint64_t)rintf(cfg->r_c * kScale);
+  M.clamp_signed = cfg->clamp_signed;
+  M.dlo = cfg->clamp_signed ? -cfg->truncation : 0.f;
   for (int k = 0; k < 3; ++k) {
     M.dom_vox[k] = cfg->domain_min[k] * 8;
     M.dim_vox[k] = (int)cfg->domain_bricks[k] * 8;

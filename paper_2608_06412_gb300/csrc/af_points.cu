@@ -16,10 +16,12 @@
 //                 sensor motion for blocked points
 //  k_pts_count / k_pts_scan / k_pts_select
 //                 the first `budget` queued ids in id order
+//  k_pts_snap     (coarse-to-fine search only) the stored best directions
+//                 as they are before the batch
 //  k_pts_eval     one warp per selected point: confidence gate, nearest
 //                 neighbours, exact integer covariance, Jacobi eigenvector,
-//                 view-filtered scoring (the plain path's exact search),
-//                 state update
+//                 view-filtered scoring (the plain path's exact search, or
+//                 its coarse-to-fine form), state update
 // The integer decisions (neighbour choice, eigenvector, orientation,
 // candidate tests, gates) are taken in single precision with correctly
 // rounded operations in a fixed order, as the CPU oracle takes them.
@@ -64,7 +66,8 @@ __device__ inline int vox_slot(int x, int y, int z) { return (x & 7) | ((y & 7) 
 
 // TSDF of a voxel word: S / (w 2^20) in double rounded to single, tau if w = 0.
 __device__ inline float tsdf_word(unsigned long long word, float tau) {
-  const unsigned long long w = word & kWMask, S = word >> kWBits;
+  const unsigned long long w = word & kWMask;
+  const long long S = word_S(word);
   return w ? __double2float_rn((double)S / ((double)w * 1048576.0)) : tau;
 }
 
@@ -331,7 +334,85 @@ __device__ inline void jacobi_min(float a[3][3], float out[3]) {
   for (int i = 0; i < 3; ++i) out[i] = v[i][j];
 }
 
+// Stored best directions before a batch of evaluations (coarse-to-fine).
+__global__ void __launch_bounds__(256) k_pts_snap(PtView V) {
+  const uint32_t n = min(V.C->count, V.capacity);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    V.snap[i] = V.st[i].best;
+}
+
+// Coarse-to-fine direction subsets over a ring-ordered table.
+struct CoarseFilter {
+  const NormalViewFilter& F;
+  int stride;
+  __device__ bool operator()(const ToolView& T, int g) const {
+    return g < T.G && g % stride == 0 && F(T, g);
+  }
+};
+struct WindowFilter {
+  const NormalViewFilter& F;
+  int centre, half;
+  __device__ bool operator()(const ToolView& T, int g) const {
+    if (g >= T.G) return false;
+    const int d = abs(g - centre);
+    return min(d, T.G - d) <= half && F(T, g);
+  }
+};
+
+// Lowest-index minimum of two (score, index) results; index -1 = none.
+__device__ inline int2 better(int2 a, int2 b) {
+  if (b.y < 0) return a;
+  if (a.y < 0) return b;
+  return (b.x < a.x || (b.x == a.x && b.y < a.y)) ? b : a;
+}
+
+constexpr int kC2FTab = 729;  // bricks a ball of radius <= 31 voxels can span (9^3)
+
+// Stored best direction (before the batch) of the nearest other point in
+// the coarse-to-fine ball that had one; -1 if none. tb: this warp's table of
+// the ball's bricks.
+__device__ int nearest_resolved(const MapView& M, const PtView& V, const PtState& st, uint32_t* tb,
+                                int lane) {
+  const int R = V.c2f_R;
+  const int b0x = (st.x - R) >> 3, b0y = (st.y - R) >> 3, b0z = (st.z - R) >> 3;
+  const int nx = ((st.x + R) >> 3) - b0x + 1, ny = ((st.y + R) >> 3) - b0y + 1,
+            nz = ((st.z + R) >> 3) - b0z + 1;
+  for (int k = lane; k < nx * ny * nz; k += 32) {
+    const int bx = b0x + k % nx, by = b0y + (k / nx) % ny, bz = b0z + k / (nx * ny);
+    uint32_t b = kNoBlock;
+    if (bx >= 0 && by >= 0 && bz >= 0 && bx < (M.dim_vox[0] >> 3) && by < (M.dim_vox[1] >> 3) &&
+        bz < (M.dim_vox[2] >> 3))
+      b = lookup_brick(M, pack_brick(bx, by, bz));
+    tb[k] = b;
+  }
+  __syncwarp();
+  int res = -1;
+  for (int c0 = 0; c0 < V.c2f_noff; c0 += 32) {
+    const int j = c0 + lane;
+    int16_t b = -1;
+    if (j < V.c2f_noff) {
+      const int4 o = __ldg(V.c2foff + j);
+      const int x = st.x + o.x, y = st.y + o.y, z = st.z + o.z;
+      if (box_rel(M, x, y, z)) {
+        const uint32_t bb = tb[((x >> 3) - b0x) + nx * (((y >> 3) - b0y) + ny * ((z >> 3) - b0z))];
+        if (bb != kNoBlock) {
+          const int32_t id = __ldcg(V.pid + (size_t)bb * kBrickVox + vox_slot(x, y, z));
+          if (id >= 0) b = __ldcg(V.snap + id);
+        }
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, b >= 0);
+    if (bal) {
+      res = __shfl_sync(0xffffffffu, (int)b, __ffs(bal) - 1);
+      break;
+    }
+  }
+  __syncwarp();  // the table is rewritten for the warp's next point
+  return res;
+}
+
 __global__ void __launch_bounds__(128) k_pts_eval(MapView M, ToolView T, PtView V) {
+  __shared__ uint32_t s_c2f[4][kC2FTab];
   const int lane = threadIdx.x & 31;
   const uint32_t nsel = V.C->nsel;
   const uint32_t wstride = gridDim.x * (blockDim.x >> 5);
@@ -448,12 +529,21 @@ __global__ void __launch_bounds__(128) k_pts_eval(MapView M, ToolView T, PtView 
                       P.py >= T.reach[1] && P.py + T.reach[1] < M.dim_vox[1] &&
                       P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
     int2 res;
-    if (fast) {
-      P.row = (P.pz * M.dim_vox[1] + P.py) * M.row_words;
-      res = best_direction<true>(M, T, P, F, lane);
+    P.row = fast ? (P.pz * M.dim_vox[1] + P.py) * M.row_words : 0;
+    if (V.c2f_stride == 0) {
+      res = fast ? best_direction<true>(M, T, P, F, lane) : best_direction<false>(M, T, P, F, lane);
     } else {
-      P.row = 0;
-      res = best_direction<false>(M, T, P, F, lane);
+      // coarse set, then the window around the nearest resolved neighbour's
+      // direction (else around the coarse best); lowest-index minimum of both
+      const int nb = nearest_resolved(M, V, st, s_c2f[threadIdx.x >> 5], lane);
+      const CoarseFilter Fc{F, V.c2f_stride};
+      res = fast ? best_direction<true>(M, T, P, Fc, lane) : best_direction<false>(M, T, P, Fc, lane);
+      const int centre = nb >= 0 ? nb : res.y;
+      if (centre >= 0) {
+        const WindowFilter Fw{F, centre, V.c2f_half};
+        res = better(res, fast ? best_direction<true>(M, T, P, Fw, lane)
+                               : best_direction<false>(M, T, P, Fw, lane));
+      }
     }
     const int nc = T.n_c;
     const int sc = res.y >= 0 ? res.x : nc + 1;
@@ -536,6 +626,12 @@ PtView pt_view(af_ctx* ctx) {
   V.a_decay = c.a_decay;
   V.a_recover = c.a_recover;
   V.ca_min = c.ca_min;
+  V.c2f_stride = (int)c.c2f_stride;
+  V.c2f_half = (int)c.c2f_half;
+  V.c2f_R = ctx->pc2f_R;
+  V.c2foff = ctx->d_pc2f;
+  V.c2f_noff = ctx->pc2f_noff;
+  V.snap = ctx->d_psnap;
   return V;
 }
 
@@ -545,6 +641,7 @@ af_status select_and_eval(af_ctx* ctx, uint32_t budget, cudaStream_t s) {
   k_pts_count<<<nblocks, kSelBlock, 0, s>>>(V);
   k_pts_scan<<<1, 1024, 0, s>>>(V, nblocks, budget);
   k_pts_select<<<nblocks, kSelBlock, 0, s>>>(V, budget);
+  if (V.c2f_stride > 0) k_pts_snap<<<grid_cap(ctx->pcfg.capacity, 256, ctx->num_sms, 8), 256, 0, s>>>(V);
   k_pts_eval<<<(unsigned)ctx->num_sms * 8, 128, 0, s>>>(ctx->M, ctx->T, V);
   PT_CUDA(ctx, cudaGetLastError());
   return AF_OK;
@@ -566,6 +663,32 @@ extern "C" af_status af_points_enable(af_ctx* ctx, const af_points_config* cfg) 
   if (c.capacity < 1 || c.capacity > (1u << 30) || c.k_nn < 3 || c.k_nn > 343 || c.nn_radius < 1 ||
       c.nn_radius > 3 || c.max_views > 8 || !(c.k_c > 0.f) || c.view_min_dist < 0.f)
     return af::pfail(ctx, AF_ERR_INVALID_ARG, "af_points_enable: parameter out of range");
+  // coarse-to-fine ball: offsets o != 0 with |o|^2 v^2 <= radius^2 in double
+  std::vector<int4> ball;
+  int c2fR = 0;
+  if (c.c2f_stride > 0) {
+    const double v = (double)ctx->cfg.voxel_size, r = (double)c.c2f_radius;
+    if (!(c.c2f_radius > 0.f) || !std::isfinite(c.c2f_radius) || r / v >= 32.0 || c.c2f_half > 4096)
+      return af::pfail(ctx, AF_ERR_INVALID_ARG,
+                       "af_points_enable: coarse-to-fine radius must be in (0, 32 v), half <= 4096");
+    const int Rb = (int)(r / v) + 1;
+    for (int z = -Rb; z <= Rb; ++z)
+      for (int y = -Rb; y <= Rb; ++y)
+        for (int x = -Rb; x <= Rb; ++x) {
+          const int d2 = x * x + y * y + z * z;
+          if (d2 == 0 || (double)d2 * v * v > r * r) continue;
+          ball.push_back(make_int4(x, y, z, d2));
+          c2fR = std::max(c2fR, std::max(std::abs(x), std::max(std::abs(y), std::abs(z))));
+        }
+    std::sort(ball.begin(), ball.end(), [](const int4& a, const int4& b) {
+      if (a.w != b.w) return a.w < b.w;
+      if (a.z != b.z) return a.z < b.z;
+      if (a.y != b.y) return a.y < b.y;
+      return a.x < b.x;
+    });
+    if (c2fR > 31)
+      return af::pfail(ctx, AF_ERR_INVALID_ARG, "af_points_enable: coarse-to-fine ball beyond 31 voxels");
+  }
   ctx->pcfg = c;
   const size_t B = ctx->cfg.pool_blocks, P = c.capacity, R = ctx->cfg.max_returns;
   const size_t nblocks = (P + 1023) / 1024;
@@ -599,8 +722,16 @@ extern "C" af_status af_points_enable(af_ctx* ctx, const af_points_config* cfg) 
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_pnnoff, off.size() * sizeof(int4));
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->d_pnnoff, off.data(), off.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !ball.empty()) {
+    e = cudaMalloc((void**)&ctx->d_pc2f, ball.size() * sizeof(int4));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ctx->d_pc2f, ball.data(), ball.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_psnap, P * sizeof(int16_t), 0xFF);
+  }
   if (e != cudaSuccess)
     return af::pfail(ctx, AF_ERR_CUDA, "af_points_enable: allocation failed: %s", cudaGetErrorString(e));
+  ctx->pc2f_noff = (int)ball.size();
+  ctx->pc2f_R = c2fR;
   ctx->pnoff = (int)off.size();
   ctx->pts_on = true;
   ctx->have_q_last = false;

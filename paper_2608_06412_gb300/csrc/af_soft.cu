@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) k_dense_view(MapView M, float* __restrict
                  bz = (size_t)(key >> 42) * 8;
     for (int l = threadIdx.x; l < kBrickVox; l += blockDim.x) {
       const unsigned long long word = __ldcg(M.vox + (size_t)b * kBrickVox + l);
-      const unsigned long long w = word & kWMask, S = word >> kWBits;
+      const unsigned long long w = word & kWMask;
+      const long long S = word_S(word);
       const float d = w ? __double2float_rn((double)S / ((double)w * 1048576.0)) : M.tau;
       dense[((bz + (l >> 6)) * Y + by + ((l >> 3) & 7)) * X + bx + (l & 7)] = d;
     }

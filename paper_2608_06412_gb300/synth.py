@@ -95,6 +95,20 @@ def fibonacci_hemisphere(K: int, cos_max: float = 0.0) -> np.ndarray:
     return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1).astype(np.float32)
 
 
+def yaw_ring(D: int = 180, pitch: float = 0.0) -> np.ndarray:
+    """The paper's approach set (Sec. 3.4): D yaw angles psi_d = 2 pi d / D
+    at a fixed pitch (0: horizontal), u_d = (cos p cos psi, cos p sin psi,
+    sin p), in yaw order. Computed in double, rounded to float32."""
+    psi = 2.0 * math.pi * np.arange(D, dtype=np.float64) / D
+    cp, sp = math.cos(pitch), math.sin(pitch)
+    return np.stack([cp * np.cos(psi), cp * np.sin(psi), np.full(D, sp)],
+                    axis=1).astype(np.float32)
+
+
+# cos 70 degrees: the normal cone of the paper's approach set (Sec. 3.4)
+COS_70 = float(np.float32(math.cos(math.radians(70.0))))
+
+
 def halton(index: np.ndarray, base: int) -> np.ndarray:
     """Radical inverse of integer `index` in `base` (van der Corput)."""
     index = np.asarray(index, dtype=np.int64).copy()

@@ -33,12 +33,14 @@ class Workload:
     def af_config(self, **caps):
         from .af import MapConfig
         p = self.params
-        return MapConfig(voxel_size=p["v"], truncation=p["tau"], r_c=p["r_c"],
-                         cube_radius=p["cube_radius"], clear_samples=p["clear_samples"],
-                         domain_min=self.dom_min, domain_bricks=self.dom_bricks,
-                         cone_cos=p["cone_cos"], range_min=p["range_min"],
-                         range_max=p["range_max"], clear_lo=p["clear_lo"],
-                         clear_hi=p["clear_hi"], w_min=p["w_min"], w_cap=p["w_cap"], **caps)
+        kw = dict(voxel_size=p["v"], truncation=p["tau"], r_c=p["r_c"],
+                  cube_radius=p["cube_radius"], clear_samples=p["clear_samples"],
+                  domain_min=self.dom_min, domain_bricks=self.dom_bricks,
+                  cone_cos=p["cone_cos"], range_min=p["range_min"],
+                  range_max=p["range_max"], clear_lo=p["clear_lo"],
+                  clear_hi=p["clear_hi"], w_min=p["w_min"], w_cap=p["w_cap"])
+        kw.update(caps)     # capacities, and overrides of the above
+        return MapConfig(**kw)
 
     def af_tool(self):
         from .af import ToolConfig

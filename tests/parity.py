@@ -18,7 +18,8 @@ def oracle_config(W: Workload, **over) -> oracle.Config:
                          dom_size=tuple(8 * b for b in W.dom_bricks),
                          cone_cos=p["cone_cos"], range_min=p["range_min"],
                          range_max=p["range_max"], clear_lo=p["clear_lo"],
-                         clear_hi=p["clear_hi"], w_min=p["w_min"], w_cap=p["w_cap"])
+                         clear_hi=p["clear_hi"], w_min=p["w_min"], w_cap=p["w_cap"],
+                         clamp_signed=int(p.get("clamp_signed", 0)))
 
 
 def oracle_tool(W: Workload, **over) -> oracle.Tool:

@@ -198,3 +198,59 @@ def test_cube_size_follows_truncation(m, updated):
     mp.integrate(np.array([[64.5 * v, 0, 0]], np.float32), _pose([0.0, v / 2, v / 2]))
     e = mp.export()
     assert int((e["w"] == 1).sum()) == updated
+
+
+def _sphere_cap_map(clamp_signed, w_cap=2000, noise=0.0):
+    rng = np.random.default_rng(7)
+    q = np.array([0.3, -0.2, 0.1])
+    R = 1.7
+    d = rng.normal(size=(3000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d[d[:, 0] > 0.3]
+    pts = ((R + noise * rng.normal(size=(len(d), 1))) * d).astype(np.float32)
+    mp = oracle.Map(_cfg(0.02, 0.06, 3, 8, clamp_signed=clamp_signed, w_cap=w_cap))
+    mp.integrate(pts, _pose(q))
+    return mp, q, R
+
+
+def test_signed_clamp_is_the_signed_distance():
+    """The [-tau, tau] ablation (Tab. 4) on the concentric sphere: S/w is the
+    analytic R - |x - q| clamped to [-tau, tau], negative behind the surface
+    (where the cone leaves voxels to neighbouring returns), and wherever
+    that distance is >= 0 the map equals the [0, tau] map exactly."""
+    tau = 0.06
+    mp, q, R = _sphere_cap_map(1)
+    e = mp.export()
+    has = e["w"] > 0
+    centre = (e["ijk"][has] + 0.5) * np.float64(np.float32(0.02))
+    sdf = np.clip(R - np.linalg.norm(centre - q, axis=1), -tau, tau)
+    got = e["S"][has].astype(np.float64) / e["w"][has] / 2.0 ** 20
+    assert np.max(np.abs(got - sdf)) < 1e-5
+    assert (sdf == -tau).sum() > 100 and (sdf < -0.02).sum() > 1000
+    e0 = _sphere_cap_map(0)[0].export()
+    assert (e0["ijk"] == e["ijk"]).all() and (e0["w"] == e["w"]).all()
+    ahead = has.copy()
+    ahead[has] = sdf > 1e-4
+    assert (e0["S"][ahead] == e["S"][ahead]).all()
+    behind = has.copy()
+    behind[has] = sdf < -1e-4
+    assert (e0["S"][behind] == 0).all() and (e["S"][behind] < 0).all()
+    # occupancy follows the sign: every voxel behind the surface is occupied
+    assert all(mp.occ(*x) for x in e["ijk"][behind][:500])
+
+
+def test_signed_clamp_cap_floors_negative_sums():
+    """Sec. 3.6's proportional rescale of a negative sum rounds toward minus
+    infinity: S' w <= S w_cap < (S' + 1) w."""
+    big = _sphere_cap_map(1, noise=0.03)[0].export()
+    small = _sphere_cap_map(1, w_cap=3, noise=0.03)[0].export()
+    assert (big["ijk"] == small["ijk"]).all()
+    over = big["w"] > 3
+    S, w = big["S"][over].astype(object), big["w"][over].astype(object)
+    Sc = small["S"][over].astype(object)
+    assert (small["w"][over] == 3).all()
+    neg = np.array([s < 0 for s in S])
+    inexact = np.array([(s * 3) % int(x) != 0 for s, x in zip(S, w)])
+    assert (neg & inexact).sum() > 1000      # truncation would differ there
+    for s, x, sc in zip(S, w, Sc):
+        assert sc * x <= s * 3 < (sc + 1) * x

@@ -341,3 +341,96 @@ def test_neighbour_brick_trigger_and_confidence_gate():
     assert 200 < low.sum() < len(low) - 200
     assert (e3["score"][low] == -1).all() and (e3["normal"][low] == 0).all()
     assert (e3["score"][~low] >= 0).mean() > 0.95
+
+
+def _slotted_scene():
+    g = synth.Group(a=np.array([2.02, 0, 0]), b=np.array([2.02, 0, 0]), radius=0.8,
+                    boxes=np.array([[2.0, -0.5, -0.5, 2.04, -0.01, 0.5],
+                                    [2.0, 0.01, -0.5, 2.04, 0.5, 0.5],
+                                    [2.3, -0.5, -0.5, 2.34, 0.5, 0.5]]))
+    return synth.Scene([g], *synth._bounds([g]))
+
+
+def _c2f_expected(mp, tool, dirs, e, ids, snap, stride, half, radius):
+    """Brute force of the coarse-to-fine rule from the full per-direction
+    score table of the plain scorer: coarse set, centre (nearest other
+    point with a direction in `snap`, else the coarse best), window, then the
+    lowest-index minimum over the union."""
+    G = len(dirs)
+    centres = ((e["ijk"][ids].astype(np.float32) + np.float32(0.5)) * np.float32(V))
+    _, _, ds = mp.score(tool, dirs, centres, e["normal"][ids], dir_scores=True)
+    res_ijk = e["ijk"][snap >= 0].astype(np.int64)
+    res_best = snap[snap >= 0]
+    out = []
+    for k, i in enumerate(ids):
+        sc = ds[k]
+        d = res_ijk - e["ijk"][i]
+        d2 = (d ** 2).sum(1)
+        ok = (d2 > 0) & (d2 * float(np.float32(V)) ** 2 <= float(np.float32(radius)) ** 2)
+        centre = -1
+        if ok.any():
+            j = np.lexsort((d[ok, 0], d[ok, 1], d[ok, 2], d2[ok]))[0]
+            centre = int(res_best[ok][j])
+        coarse = np.arange(0, G, stride)
+        if centre < 0:
+            cs = [(sc[g], g) for g in coarse if sc[g] >= 0]
+            centre = min(cs)[1] if cs else -1
+        inE = np.zeros(G, bool)
+        inE[coarse] = True
+        if centre >= 0:
+            dd = np.abs(np.arange(G) - centre)
+            inE |= np.minimum(dd, G - dd) <= half
+        cand = [(sc[g], g) for g in range(G) if inE[g] and sc[g] >= 0]
+        out.append(min(cand) if cand else (tool.n_c + 1, -1))
+    return out
+
+
+def test_coarse_to_fine_search_brute_force():
+    """Sec. 3.6's coarse-to-fine search on the paper's yaw ring (D = 180,
+    70 degree cone; 20 degree coarse stride, +-24 degree window, 0.3 m)
+    against a brute force over the plain scorer's per-direction scores, for
+    a first batch (no resolved neighbours: windows around the coarse bests)
+    and a second (windows around neighbours' directions). The observation
+    filter is disabled so the plain scorer sees the same candidates."""
+    dirs = synth.yaw_ring(180)
+    tool = _tool(cos_theta_max=synth.COS_70, corr_length=1.0)
+    mp = oracle.Map(_cfg())
+    pc = oracle.PointsConfig(trig_tsdf=2 * V, budget=0, obs_dot=-2.0, c2f_stride=10, c2f_half=12,
+                             c2f_radius=0.3)
+    P = oracle.PointSet(mp, pc, tool, dirs)
+    pts, pose = _frame(_slotted_scene(), (0.0, 0.0, 0.0), n=6000)
+    P.frame(pts, pose)
+    before = P.export()
+    checked = 0
+    for batch in (400, 10 ** 9):
+        P.drain(batch)
+        after = P.export()
+        ids = np.flatnonzero((before["score"] < 0) & (after["score"] >= 0))
+        assert len(ids) > 100
+        exp = _c2f_expected(mp, tool, dirs, after, ids, before["best"], 10, 12, 0.3)
+        got = list(zip(after["score"][ids].tolist(), after["best"][ids].tolist()))
+        assert got == [(int(s), int(g)) for s, g in exp]
+        checked += len(ids)
+        before = after
+    assert checked > 1000
+    labels = after["label"]
+    assert (labels == oracle.ACCESSIBLE).sum() > 50 and (labels == oracle.BLOCKED).sum() > 50
+
+
+@pytest.mark.parametrize("stride,half", [(1, 0), (10, 90)])
+def test_coarse_to_fine_degenerate_cases_are_the_full_search(stride, half):
+    """A stride of 1, or a window of half the ring, searches every direction:
+    the same state as the full search."""
+    dirs = synth.yaw_ring(180)
+    tool = _tool(cos_theta_max=synth.COS_70, corr_length=1.0)
+    res = []
+    for c2f in (dict(), dict(c2f_stride=stride, c2f_half=half, c2f_radius=0.3)):
+        P = oracle.PointSet(oracle.Map(_cfg()), oracle.PointsConfig(trig_tsdf=2 * V, budget=1500,
+                                                                    **c2f), tool, dirs)
+        for k in range(2):
+            pts, pose = _frame(_slotted_scene(), (0.0, 0.05 * k, 0.0), n=4000, seed=k)
+            P.frame(pts, pose)
+        res.append(P.export())
+    for key in ("score", "best", "label", "a"):
+        assert (res[0][key] == res[1][key]).all(), key
+    assert (res[0]["score"] >= 0).sum() > 1000

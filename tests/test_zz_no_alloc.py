@@ -26,17 +26,18 @@ def _densify(blocks, box_min, box_dim):
     at = (ijk[:, 2] * by + ijk[:, 1]) * bx + ijk[:, 0]
     S = blocks["S"].reshape(-1)
     w = blocks["w"].reshape(-1)
-    vox[at[inside]] = (S[inside] << np.uint64(20)) | w[inside].astype(np.uint64)
+    vox[at[inside]] = ((S[inside].astype(np.int64) << 20) |
+                       w[inside].astype(np.int64)).view(np.uint64)
     flags[at[inside]] = blocks["flags"].reshape(-1)[inside]
     return vox, flags
 
 
-@pytest.mark.parametrize("sub_box", [False, True])
-def test_noalloc_matches_map_path_on_consecutive_scans(sub_box):
+@pytest.mark.parametrize("sub_box,clamp_signed", [(False, 0), (True, 0), (True, 1)])
+def test_noalloc_matches_map_path_on_consecutive_scans(sub_box, clamp_signed):
     import torch
     W = workload.single_frame()
     fr, _, _ = workload.single_frame_inputs(W)
-    cfg = W.af_config()
+    cfg = W.af_config(clamp_signed=clamp_signed, w_cap=3 if clamp_signed else 2000)
     # scan A in the world frame; scan B seen from a rotated, shifted sensor
     a = fr.pts[:10000]
     R = np.array([[0.0, -1, 0], [1, 0, 0], [0, 0, 1]])
