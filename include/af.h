@@ -136,6 +136,23 @@ af_status af_integrate_scan(af_ctx *ctx, const float *d_xyz, uint32_t n,
                             const float pose[16], void *stream);
 
 /*
+ * Projective integration, the ablation of Tab. 3 (Sec. 3.2): the same
+ * arguments and return acceptance as af_integrate_scan, but the accepted
+ * returns only build a range image -- the nearest range in each cell of a
+ * bins x bins octahedral map of sensor-frame directions ((u, w) =
+ * (d_x, d_y) / (|d_x| + |d_y| + |d_z|), the lower hemisphere folded onto the
+ * corners; 812 gives the mean solid angle of a 0.25 x 0.25 degree bin) --
+ * and every voxel x of the bricks their cubes overlap takes
+ * d = (range of the cell of R^T (x - q)) - |x - q|, skipped if that cell is
+ * empty or d < -tau, clamped as the map clamps. No cone, no cleared band;
+ * the weight cap and the view rebuild as af_integrate_scan. 2 <= bins <= 8192;
+ * the range image (bins^2 x 4 bytes) is allocated on first use and kept.
+ * Asynchronous on `stream`.
+ */
+af_status af_integrate_scan_projective(af_ctx *ctx, const float *d_xyz, uint32_t n,
+                                       const float pose[16], uint32_t bins, void *stream);
+
+/*
  * Sets the tool and the approach-direction table (Sec. 3.4, 3.6): for each
  * of the G unit directions (h_dirs: host G x 3 float32, world frame) the
  * library rasterises the tool and corridor kernels and the three arm-path

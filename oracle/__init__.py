@@ -82,6 +82,10 @@ def _load():
         lib.or_map_free.argtypes = [P]
         lib.or_integrate.restype = C.c_int64
         lib.or_integrate.argtypes = [P, P, C.c_int64, P]
+        lib.or_integrate_projective.restype = C.c_int64
+        lib.or_integrate_projective.argtypes = [P, P, C.c_int64, P, C.c_int32]
+        lib.or_octa_bin.restype = C.c_int32
+        lib.or_octa_bin.argtypes = [P, C.c_int32]
         lib.or_get_voxel.restype = C.c_int
         lib.or_get_voxel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32,
                                      C.POINTER(C.c_int64), C.POINTER(C.c_uint32),
@@ -200,6 +204,16 @@ class Map:
         pose = np.eye(4, dtype=np.float32) if pose is None else \
             np.ascontiguousarray(pose, dtype=np.float32).reshape(4, 4)
         return int(self._lib.or_integrate(self._h, _ptr(pts), len(pts), _ptr(pose)))
+
+    def integrate_projective(self, pts: np.ndarray, pose: np.ndarray | None = None,
+                             bins: int = 812) -> int:
+        """Projective integration (the ablation of Tab. 3) over a bins x bins
+        octahedral range image."""
+        pts = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 3)
+        pose = np.eye(4, dtype=np.float32) if pose is None else \
+            np.ascontiguousarray(pose, dtype=np.float32).reshape(4, 4)
+        return int(self._lib.or_integrate_projective(self._h, _ptr(pts), len(pts), _ptr(pose),
+                                                     int(bins)))
 
     def voxel(self, i: int, j: int, k: int):
         S, w, cl = C.c_int64(), C.c_uint32(), C.c_int32()
@@ -394,6 +408,13 @@ class PointSet:
                                                ("ijk", "normal", "label", "score", "best", "a",
                                                 "queued", "nviews")))
         return out
+
+
+def octa_bin(d, bins: int) -> int:
+    """Octahedral range-image cell of a sensor-frame direction."""
+    lib = _load()
+    d = np.ascontiguousarray(d, np.float32).reshape(3)
+    return int(lib.or_octa_bin(_ptr(d), int(bins)))
 
 
 def jacobi3(A: np.ndarray, sweeps: int = 8):

@@ -112,6 +112,11 @@ static int64_t floor_div(int64_t a, int64_t b) {
     return (a % b != 0 && a < 0) ? q - 1 : q;
 }
 
+static uint64_t pack_key(int32_t ix, int32_t iy, int32_t iz);
+
+/* Weight cap with proportional rescale of the sum (Sec. 3.6), once per scan. */
+static void apply_cap(or_map *m);
+
 static uint64_t pack_key(int32_t ix, int32_t iy, int32_t iz) {
     /* 21 bits per axis, offset so that the packed key is never 0. */
     uint64_t x = (uint64_t)(uint32_t)(ix + (1 << 20)) & 0x1FFFFFu;
@@ -190,6 +195,17 @@ void or_map_free(or_map *m) {
     if (!m) return;
     free(m->slot);
     free(m);
+}
+
+static void apply_cap(or_map *m) {
+    const or_config *c = &m->cfg;
+    for (uint64_t k = 0; k < m->cap; ++k) {
+        or_voxel *vx = &m->slot[k];
+        if (vx->key && vx->w > c->w_cap) {
+            vx->S = floor_div(vx->S * (int64_t)c->w_cap, (int64_t)vx->w);
+            vx->w = c->w_cap;
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -293,14 +309,116 @@ int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[1
         }
     }
 
-    /* weight cap with proportional rescale of the sum (Sec. 3.6) */
-    for (uint64_t k = 0; k < m->cap; ++k) {
-        or_voxel *vx = &m->slot[k];
-        if (vx->key && vx->w > c->w_cap) {
-            vx->S = floor_div(vx->S * (int64_t)c->w_cap, (int64_t)vx->w);
-            vx->w = c->w_cap;
+    apply_cap(m);
+    return accepted;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Projective integration: the ablation of Tab. 3 (Sec. 3.2).                */
+/* ------------------------------------------------------------------------- */
+
+/* Bin of a sensor-frame direction in an N x N octahedral map of the sphere:
+ * (u, w) = (d_x, d_y) / (|d_x| + |d_y| + |d_z|), the lower hemisphere folded
+ * onto the corners, then N equal cells per axis over [-1, 1]. */
+static int32_t octa_bin(const float d[3], int32_t N) {
+    const float s = (fabsf(d[0]) + fabsf(d[1])) + fabsf(d[2]);
+    float u = d[0] / s, w = d[1] / s;
+    if (d[2] < 0.0f) {
+        const float uu = (1.0f - fabsf(w)) * (u >= 0.0f ? 1.0f : -1.0f);
+        const float ww = (1.0f - fabsf(u)) * (w >= 0.0f ? 1.0f : -1.0f);
+        u = uu;
+        w = ww;
+    }
+    const float h = (float)N * 0.5f;
+    int32_t bu = (int32_t)floorf((u + 1.0f) * h), bw = (int32_t)floorf((w + 1.0f) * h);
+    bu = bu < 0 ? 0 : (bu >= N ? N - 1 : bu);
+    bw = bw < 0 ? 0 : (bw >= N ? N - 1 : bw);
+    return bw * N + bu;
+}
+
+int32_t or_octa_bin(const float d[3], int32_t bins) { return octa_bin(d, bins); }
+
+static int brick_cmp(const void *x, const void *y) {
+    const uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+    return a < b ? -1 : (a > b);
+}
+
+int64_t or_integrate_projective(or_map *m, const float *pts, int64_t n, const float pose[16],
+                                int32_t bins) {
+    const or_config *c = &m->cfg;
+    const float v = c->v, tau = c->tau, lo = c->clamp_signed ? -c->tau : 0.0f;
+    const int32_t mr = c->cube_radius;
+    const float q[3] = {pose[3], pose[7], pose[11]};
+    const int64_t N2 = (int64_t)bins * bins;
+    float *img = (float *)malloc(sizeof(float) * (size_t)N2);
+    uint8_t *hit = (uint8_t *)calloc((size_t)N2, 1);
+    const int32_t nb = (2 * mr + 7) / 8 + 1; /* bricks a cube spans per axis, at most */
+    uint64_t *bricks = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n * nb * nb * nb + 1));
+    int64_t nbr = 0, accepted = 0;
+
+    /* the returns accepted by the scan-centric rules: range image and bricks */
+    for (int64_t k = 0; k < n; ++k) {
+        const float *ps = pts + 3 * k;
+        if (!isfinite(ps[0]) || !isfinite(ps[1]) || !isfinite(ps[2])) continue;
+        float p[3];
+        for (int r = 0; r < 3; ++r)
+            p[r] = ((pose[4 * r + 0] * ps[0] + pose[4 * r + 1] * ps[1]) + pose[4 * r + 2] * ps[2]) +
+                   pose[4 * r + 3];
+        const float b[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+        const float range = sqrtf((b[0] * b[0] + b[1] * b[1]) + b[2] * b[2]);
+        if (!(range >= c->range_min && range <= c->range_max)) continue;
+        int32_t ip[3];
+        if (!voxel_index(p[0], v, &ip[0]) || !voxel_index(p[1], v, &ip[1]) ||
+            !voxel_index(p[2], v, &ip[2]))
+            continue;
+        if (!in_domain(c, ip[0] - mr, ip[1] - mr, ip[2] - mr) ||
+            !in_domain(c, ip[0] + mr, ip[1] + mr, ip[2] + mr))
+            continue;
+        accepted++;
+        /* the return's range in the bin of its sensor-frame direction (the nearest wins) */
+        if (ps[0] != 0.0f || ps[1] != 0.0f || ps[2] != 0.0f) {
+            const int32_t bin = octa_bin(ps, bins);
+            if (!hit[bin] || range < img[bin]) img[bin] = range;
+            hit[bin] = 1;
+        }
+        for (int32_t bz = floor_div(ip[2] - mr, 8); bz <= floor_div(ip[2] + mr, 8); ++bz)
+            for (int32_t by = floor_div(ip[1] - mr, 8); by <= floor_div(ip[1] + mr, 8); ++by)
+                for (int32_t bx = floor_div(ip[0] - mr, 8); bx <= floor_div(ip[0] + mr, 8); ++bx)
+                    bricks[nbr++] = pack_key(bx, by, bz);
+    }
+    qsort(bricks, (size_t)nbr, sizeof(uint64_t), brick_cmp);
+
+    /* every voxel of those bricks looks its range up through its own bin */
+    for (int64_t k = 0; k < nbr; ++k) {
+        if (k > 0 && bricks[k] == bricks[k - 1]) continue;
+        int32_t bx, by, bz;
+        unpack_key(bricks[k], &bx, &by, &bz);
+        for (int32_t l = 0; l < 512; ++l) {
+            const int32_t j[3] = {8 * bx + (l & 7), 8 * by + ((l >> 3) & 7), 8 * bz + (l >> 6)};
+            if (!in_domain(c, j[0], j[1], j[2])) continue;
+            const float e[3] = {voxel_centre(j[0], v) - q[0], voxel_centre(j[1], v) - q[1],
+                                voxel_centre(j[2], v) - q[2]};
+            /* sensor-frame direction R^T e */
+            float xs[3];
+            for (int r = 0; r < 3; ++r)
+                xs[r] = (pose[r] * e[0] + pose[4 + r] * e[1]) + pose[8 + r] * e[2];
+            if (xs[0] == 0.0f && xs[1] == 0.0f && xs[2] == 0.0f) continue;
+            const int32_t bin = octa_bin(xs, bins);
+            if (!hit[bin]) continue; /* an empty bin: no observation */
+            const float dist = sqrtf((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]);
+            float d = img[bin] - dist;
+            if (d < -tau) continue; /* beyond the truncation behind the surface */
+            if (d < lo) d = lo;
+            if (d > tau) d = tau;
+            or_voxel *vx = voxel_ref(m, j[0], j[1], j[2]);
+            vx->S += (int64_t)rintf(d * OR_SCALE);
+            vx->w += 1;
         }
     }
+    apply_cap(m);
+    free(img);
+    free(hit);
+    free(bricks);
     return accepted;
 }
 

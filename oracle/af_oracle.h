@@ -61,6 +61,16 @@ void or_map_free(or_map *m);
  * Sec. 3.6 weight cap). pts: n x 3 floats in the sensor frame; pose: 4x4
  * row-major world_from_sensor. Returns the number of accepted returns. */
 int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16]);
+/* Projective integration, the ablation of Tab. 3: the returns accepted by the
+ * scan-centric rules fill a range image over bins x bins octahedral direction
+ * cells (the nearest return per cell); every voxel of the 8^3 bricks that
+ * their cubes overlap takes d = (range in its own cell) - |x - q|, skipped
+ * if the cell is empty or d < -tau, clamped as the scan-centric path clamps;
+ * no cone and no cleared band. Returns the accepted returns. */
+int64_t or_integrate_projective(or_map *m, const float *pts, int64_t n, const float pose[16],
+                                int32_t bins);
+/* The octahedral cell (row-major, bins x bins) of direction d (exposed for its pins). */
+int32_t or_octa_bin(const float d[3], int32_t bins);
 /* The same, also writing the voxel of every accepted return to voxel_out
  * (n x 3, INT32_MIN for dropped returns) when it is not NULL. */
 int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[16],

@@ -29,7 +29,8 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_batch_tick", "af_batch_set_tuning", "af_batch_get_tuning", "af_soft_seed",
            "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
            "af_soft_start", "af_points_enable", "af_points_frame", "af_points_drain",
-           "af_points_stats", "af_points_export", "af_last_error")
+           "af_points_stats", "af_points_export", "af_integrate_scan_projective",
+           "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
@@ -115,6 +116,7 @@ def load(build: bool = True) -> C.CDLL:
             "af_create": (C.c_int, [C.POINTER(_Config), C.POINTER(P)]),
             "af_destroy": (C.c_int, [P]),
             "af_integrate_scan": (C.c_int, [P, P, U32, P, P]),
+            "af_integrate_scan_projective": (C.c_int, [P, P, U32, P, U32, P]),
             "af_set_tool": (C.c_int, [P, C.POINTER(_Tool), P, U32]),
             "af_score": (C.c_int, [P, P, P, U32, P, P, P]),
             "af_frame_host": (C.c_int, [P, P, U32, P, P, P, U32, P, P, P]),
@@ -301,6 +303,16 @@ class Map:
         pose = np.ascontiguousarray(pose, np.float32).reshape(16)
         _check(self._lib.af_integrate_scan(self._h, p, n, _np_ptr(pose), _stream_ptr(stream)),
                self._h)
+
+    def integrate_scan_projective(self, xyz, pose, bins: int = 812, stream=None):
+        """af_integrate_scan_projective: the projective ablation of Tab. 3 over
+        a bins x bins octahedral range image."""
+        import torch
+        n = int(xyz.shape[0])
+        p = _dev_ptr(xyz, torch.float32, (3,)) if n else C.c_void_p(0)
+        pose = np.ascontiguousarray(pose, np.float32).reshape(16)
+        _check(self._lib.af_integrate_scan_projective(self._h, p, n, _np_ptr(pose), int(bins),
+                                                      _stream_ptr(stream)), self._h)
 
     def set_tool(self, tool: ToolConfig, dirs: np.ndarray):
         """af_set_tool: rasterise the tool/corridor kernels for G directions."""

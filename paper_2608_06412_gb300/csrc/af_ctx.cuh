@@ -58,6 +58,9 @@ struct af_ctx {
   int4* d_pc2f = nullptr;     // coarse-to-fine neighbour ball
   int pc2f_noff = 0, pc2f_R = 0;
   int16_t* d_psnap = nullptr;
+  // the projective ablation's range image (af_integrate_scan_projective)
+  unsigned* d_img = nullptr;
+  size_t img_cap = 0;
   float q_last[3] = {0.f, 0.f, 0.f};
   bool have_q_last = false;
   // host counters

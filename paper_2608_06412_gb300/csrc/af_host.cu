@@ -275,6 +275,7 @@ static void free_all(af_ctx* c) {
   cudaFree(c->d_dense);
   cudaFree(c->d_cells);
   cudaFree(c->d_table);
+  cudaFree(c->d_img);
   for (void* p : {(void*)c->d_pid, (void*)c->d_pst, (void*)c->d_pviews, (void*)c->d_pnew,
                   (void*)c->d_pchg, (void*)c->d_pnear, (void*)c->d_pchglist, (void*)c->d_psel,
                   (void*)c->d_pblock, (void*)c->d_pcount, (void*)c->d_pnnoff, (void*)c->d_pc2f,

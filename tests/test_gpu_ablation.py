@@ -9,6 +9,9 @@
 * The coarse-to-fine search of Sec. 3.6 (20 degree coarse stride, +-24
   degree window around the nearest resolved neighbour's direction within
   0.3 m) in the stateful layer, frame by frame and after draining.
+* Projective integration, the ablation of Tab. 3: maps bit for bit over an
+  octahedral range image, single scans and a rotating stream, both clamps,
+  and labels on the projective map.
 """
 import numpy as np
 import pytest
@@ -217,3 +220,51 @@ def test_coarse_to_fine_pine_stream():
     ge = g.points_export()
     _same_points(ge, op.export(), "after a drain of 3000")
     assert (ge["best"] >= 0).sum() > 1000
+
+
+@pytest.mark.parametrize("clamp_signed,bins", [(0, 812), (1, 812), (0, 97)])
+def test_projective_single_frame_bit_exact(clamp_signed, bins):
+    import torch
+    W = workload.single_frame()
+    fr, pts, nrm = workload.single_frame_inputs(W)
+    g = gpu_map(W, clamp_signed=clamp_signed)
+    g.integrate_scan_projective(to_dev(fr.pts), fr.pose, bins)
+    o = oracle.Map(oracle_config(W, clamp_signed=clamp_signed))
+    o.integrate_projective(fr.pts, fr.pose, bins)
+    torch.cuda.synchronize()
+    assert g.sync_status() == 0
+    gv = gpu_voxels(g)
+    assert_maps_equal(gv, oracle_voxels(o))
+    assert len(gv["w"]) > 10000 and (gv["cleared"] == 0).all()
+
+
+def test_projective_stream_and_labels():
+    """Eight pine-stream frames (the sensor orbits, so every pose rotates),
+    then scoring on the projective map."""
+    import torch
+    W = workload.pine_stream()
+    g = gpu_map(W, **PINE_CAPS)
+    o = oracle.Map(oracle_config(W))
+    for f in range(8):
+        fr, pts, nrm = workload.pine_frame(W, f)
+        g.integrate_scan_projective(to_dev(fr.pts), fr.pose)
+        o.integrate_projective(fr.pts, fr.pose)
+    torch.cuda.synchronize()
+    assert g.sync_status() == 0
+    assert_maps_equal(gpu_voxels(g), oracle_voxels(o))
+    g.set_tool(W.af_tool(), W.dirs)
+    sel = np.random.default_rng(3).choice(len(pts), min(2000, len(pts)), replace=False)
+    lab, best = g.score(to_dev(pts[sel].astype(np.float32)), to_dev(nrm[sel].astype(np.float32)))
+    torch.cuda.synchronize()
+    ol, ob = o.score(oracle_tool(W), W.dirs, pts[sel], nrm[sel])
+    assert (lab.cpu().numpy() == ol).all() and (best.cpu().numpy() == ob).all()
+
+
+def test_projective_arguments():
+    W = workload.single_frame()
+    g = gpu_map(W)
+    with pytest.raises(af.AfError) as e:
+        g.integrate_scan_projective(to_dev(np.zeros((4, 3), np.float32)), np.eye(4), 1)
+    assert e.value.status == af.ERR_INVALID_ARG
+    g.integrate_scan_projective(to_dev(np.zeros((0, 3), np.float32)), np.eye(4), 64)
+    assert g.sync_status() == 0 and len(gpu_voxels(g)["w"]) == 0

@@ -254,3 +254,107 @@ def test_signed_clamp_cap_floors_negative_sums():
     assert (neg & inexact).sum() > 1000      # truncation would differ there
     for s, x, sc in zip(S, w, Sc):
         assert sc * x <= s * 3 < (sc + 1) * x
+
+
+@pytest.mark.parametrize("N", [8, 61, 812])
+def test_octahedral_cells_round_trip(N):
+    """The projective ablation's range-image cells: the direction of every
+    sampled cell centre, built by inverting the octahedral fold, falls in
+    that cell (both hemispheres, every octant)."""
+    rng = np.random.default_rng(N)
+    cells = rng.integers(0, N, size=(400, 2))
+    cells[:4] = [[0, 0], [N - 1, N - 1], [0, N - 1], [N - 1, 0]]
+    for bu, bw in cells:
+        U = (bu + 0.5) / N * 2 - 1
+        W = (bw + 0.5) / N * 2 - 1
+        if abs(U) + abs(W) <= 1:
+            d = (U, W, 1 - abs(U) - abs(W))
+        else:   # the lower hemisphere, unfolded
+            u = (1 - abs(W)) * math.copysign(1, U)
+            w = (1 - abs(U)) * math.copysign(1, W)
+            d = (u, w, -(1 - abs(u) - abs(w)))
+        d = np.array(d) * rng.uniform(0.5, 40.0)          # any length
+        assert oracle.octa_bin(d, N) == bw * N + bu, (bu, bw, d)
+
+
+def test_projective_concentric_sphere():
+    """Tab. 3's projective lookup with every return at range R from a rotated
+    sensor: each updated voxel holds clamp(R - |x - q|, 0, tau) exactly once;
+    the updated set is every voxel of the returns' cube bricks whose own
+    direction cell holds a return and whose distance is not below -tau."""
+    rng = np.random.default_rng(11)
+    v, tau, R, N = 0.02, 0.06, 1.2, 24
+    c, s = math.cos(0.7), math.sin(0.7)
+    Rz = np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])
+    q = np.array([0.31, -0.17, 0.05])
+    d = rng.normal(size=(4000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d[d[:, 0] > 0.5]
+    ps = (R * d).astype(np.float32)                        # sensor frame
+    pose = _pose(q, Rz)
+    mp = oracle.Map(_cfg(v, tau, 3, 8))
+    assert mp.integrate_projective(ps, pose, N) == len(ps)
+    e = mp.export()
+    assert (e["w"] == 1).all() and (e["cleared"] == 0).all()
+    vf = np.float32(v)
+    centre = (e["ijk"] + 0.5) * np.float64(vf)
+    sdf = R - np.linalg.norm(centre - q, axis=1)
+    got = e["S"].astype(np.float64) / 2.0 ** 20
+    assert np.max(np.abs(got - np.clip(sdf, 0.0, tau))) < 1e-5
+    assert (sdf >= -tau - 1e-5).all() and (sdf < 0).sum() > 100 and (sdf > tau).sum() > 100
+    # brute force of the updated set
+    hit = {oracle.octa_bin(p, N) for p in ps}
+    P32 = pose.astype(np.float32)
+    world = (ps.astype(np.float64) @ Rz.T + q)
+    ip = np.floor(world / v).astype(int)
+    bricks = set()
+    for i in ip:
+        for bz in range((i[2] - 3) // 8, (i[2] + 3) // 8 + 1):
+            for by in range((i[1] - 3) // 8, (i[1] + 3) // 8 + 1):
+                for bx in range((i[0] - 3) // 8, (i[0] + 3) // 8 + 1):
+                    bricks.add((bx, by, bz))
+    want = set()
+    for bx, by, bz in bricks:
+        l = np.arange(512)
+        j = np.stack([8 * bx + (l & 7), 8 * by + ((l >> 3) & 7), 8 * bz + (l >> 6)], 1)
+        xc = ((j.astype(np.float32) + np.float32(0.5)) * vf)
+        ev = (xc - P32[:3, 3]).astype(np.float32)
+        xs = ev.astype(np.float64) @ Rz                    # R^T e (cell decisions are far from edges)
+        dist = np.linalg.norm(xc.astype(np.float64) - q, axis=1)
+        for k in range(512):
+            if oracle.octa_bin(xs[k], N) in hit and R - dist[k] >= -tau + 1e-4:
+                want.add(tuple(j[k]))
+            elif oracle.octa_bin(xs[k], N) in hit and R - dist[k] > -tau - 1e-4:
+                want.add(None)                              # too close to the cut to judge
+    got_set = {tuple(x) for x in e["ijk"]}
+    want.discard(None)
+    assert want <= got_set and len(got_set - want) < 0.01 * len(got_set)
+
+
+def test_projective_erodes_thin_structures():
+    """The failure mode of Sec. 3.2 behind Tab. 3: a 3 cm pole 1 m in front
+    of a wall, sparse returns. Pole voxels whose own direction cell holds a
+    wall return take free-space distances, so the projective map keeps far
+    fewer occupied pole voxels than the scan-centric map of the same scan."""
+    from paper_2608_06412_gb300 import synth
+    v, tau = 0.02, 0.06
+    pole = synth.Group(a=np.array([2.0, 0, -0.5]), b=np.array([2.0, 0, 0.5]), radius=0.05,
+                       cylinders=np.array([[2.0, 0, -0.5, 2.0, 0, 0.5, 0.015]]))
+    wall = synth.Group(a=np.array([3.02, 0, 0]), b=np.array([3.02, 0, 0]), radius=1.2,
+                       boxes=np.array([[3.0, -0.8, -0.8, 3.04, 0.8, 0.8]]))
+    scene = synth.Scene([pole, wall], *synth._bounds([pole, wall]))
+    fr = synth.cone_frame(scene, 20000, 0.0, 5, origin=(0.0, 0.0, 0.0))
+    cfg = _cfg(v, tau, 3, 8)
+    a = oracle.Map(cfg)
+    a.integrate(fr.pts, fr.pose)
+    b = oracle.Map(cfg)
+    b.integrate_projective(fr.pts, fr.pose, 812)
+
+    def pole_occ(mp):
+        e = mp.export()
+        c = (e["ijk"] + 0.5) * v
+        near = (np.hypot(c[:, 0] - 2.0, c[:, 1]) < 0.03) & (np.abs(c[:, 2]) < 0.4)
+        return int((e["occ"][near] == 1).sum())
+
+    sc, pj = pole_occ(a), pole_occ(b)
+    assert sc > 50 and pj < 0.5 * sc, (sc, pj)
