@@ -177,6 +177,18 @@ af_status af_score(af_ctx *ctx, const float *d_pts, const float *d_normals, uint
                    uint8_t *d_label, int16_t *d_best, void *stream);
 
 /*
+ * Work sharing of af_score (and af_frame_host): a point whose search takes
+ * more than `budget` candidate directions past the arm screen hands the rest
+ * of its directions to a second kernel that searches them one warp per
+ * (point, direction); the labels and best directions are identical to the
+ * single-pass search for every budget. budget = -1: single pass, one warp
+ * per point; 0 .. 4096: the hand-off threshold (default 8). The hand-off
+ * records take 12 bytes per point, allocated for max_points at af_create and
+ * grown (synchronously) for larger m. Adds two launches per af_score call.
+ */
+af_status af_set_score_split(af_ctx *ctx, int32_t budget);
+
+/*
  * One whole frame from host buffers: copies the scan and the points to the
  * device, integrates, scores, copies labels and best directions back, and
  * waits for `stream`. Sizes are bounded by max_returns / max_points. Returns
@@ -446,7 +458,9 @@ af_status af_points_export(af_ctx *ctx, uint32_t cap, int32_t *h_ijk, float *h_n
  * 4 = SDF view build, 5 = soft clearance, 6 = its adjoint, 7 = refinement,
  * 8 = seeding (af_soft_seed, af_soft_start), 9 = per-point best.
  * af_profile_read synchronises, sums the elapsed times of the recorded
- * launches (milliseconds) and, if `reset`, forgets them.
+ * launches (milliseconds) and, if `reset`, forgets them. launches[] counts
+ * kernels: an af_score call with work sharing on is three (k_score,
+ * k_score_split, k_score_finish) timed as one bracket.
  */
 typedef struct {
     uint64_t launches[10];

@@ -30,7 +30,7 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
            "af_soft_start", "af_points_enable", "af_points_frame", "af_points_drain",
            "af_points_stats", "af_points_export", "af_integrate_scan_projective",
-           "af_last_error")
+           "af_set_score_split", "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
@@ -117,6 +117,7 @@ def load(build: bool = True) -> C.CDLL:
             "af_destroy": (C.c_int, [P]),
             "af_integrate_scan": (C.c_int, [P, P, U32, P, P]),
             "af_integrate_scan_projective": (C.c_int, [P, P, U32, P, U32, P]),
+            "af_set_score_split": (C.c_int, [P, C.c_int32]),
             "af_set_tool": (C.c_int, [P, C.POINTER(_Tool), P, U32]),
             "af_score": (C.c_int, [P, P, P, U32, P, P, P]),
             "af_frame_host": (C.c_int, [P, P, U32, P, P, P, U32, P, P, P]),
@@ -313,6 +314,11 @@ class Map:
         pose = np.ascontiguousarray(pose, np.float32).reshape(16)
         _check(self._lib.af_integrate_scan_projective(self._h, p, n, _np_ptr(pose), int(bins),
                                                       _stream_ptr(stream)), self._h)
+
+    def set_score_split(self, budget: int):
+        """af_set_score_split: -1 single pass; otherwise hand a point's directions
+        beyond `budget` searched ones to per-direction warps (same results)."""
+        _check(self._lib.af_set_score_split(self._h, int(budget)), self._h)
 
     def set_tool(self, tool: ToolConfig, dirs: np.ndarray):
         """af_set_tool: rasterise the tool/corridor kernels for G directions."""

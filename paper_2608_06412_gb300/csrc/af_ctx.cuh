@@ -58,6 +58,12 @@ struct af_ctx {
   int4* d_pc2f = nullptr;     // coarse-to-fine neighbour ball
   int pc2f_noff = 0, pc2f_R = 0;
   int16_t* d_psnap = nullptr;
+  // work sharing of af_score (af_set_score_split)
+  int2* d_over = nullptr;
+  uint32_t* d_sres = nullptr;
+  uint32_t* d_scount = nullptr;
+  uint32_t split_cap = 0;
+  int score_budget = 8;
   // the projective ablation's range image (af_integrate_scan_projective)
   unsigned* d_img = nullptr;
   size_t img_cap = 0;
@@ -70,6 +76,7 @@ struct af_ctx {
   struct ProfRec {
     int kernel;
     cudaEvent_t a, b;
+    int kernels;  // kernel launches inside the bracket
   };
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_free;

@@ -22,7 +22,7 @@ cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], cons
 cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream);
 cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts,
                          const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
-                         cudaStream_t stream);
+                         const ScoreSplit& S, int num_sms, cudaStream_t stream);
 cudaError_t launch_export_flags(const MapView& M, uint32_t count, uint8_t* d_flags,
                                 cudaStream_t stream);
 cudaError_t launch_views(const MapView& M, int num_sms, bool fill, float* dense, float4* cells,
@@ -63,9 +63,9 @@ cudaEvent_t take_event(af_ctx* c) {
 
 // Runs `launch` on `s`, bracketed by events when profiling is on.
 template <class F>
-cudaError_t timed(af_ctx* c, int kernel, cudaStream_t s, F&& launch) {
+cudaError_t timed(af_ctx* c, int kernel, cudaStream_t s, F&& launch, int kernels = 1) {
   if (!c->prof_on) return launch();
-  af_ctx::ProfRec r{kernel, take_event(c), take_event(c)};
+  af_ctx::ProfRec r{kernel, take_event(c), take_event(c), kernels};
   cudaEventRecord(r.a, s);
   const cudaError_t e = launch();
   cudaEventRecord(r.b, s);
@@ -272,6 +272,9 @@ static void free_all(af_ctx* c) {
   cudaFree(c->d_nrm);
   cudaFree(c->d_label);
   cudaFree(c->d_best);
+  cudaFree(c->d_over);
+  cudaFree(c->d_sres);
+  cudaFree(c->d_scount);
   cudaFree(c->d_dense);
   cudaFree(c->d_cells);
   cudaFree(c->d_table);
@@ -381,6 +384,10 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   if (st == AF_OK) st = alloc((void**)&c->d_nrm, Pm * 12, 0);
   if (st == AF_OK) st = alloc((void**)&c->d_label, Pm, 0);
   if (st == AF_OK) st = alloc((void**)&c->d_best, Pm * 2, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_over, Pm * sizeof(int2), 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_sres, Pm * 4, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_scount, 4, 0);
+  c->split_cap = (uint32_t)Pm;
   if (st == AF_OK && cudaMallocHost((void**)&c->h_status, 64) != cudaSuccess)
     st = fail(c, AF_ERR_CUDA, "pinned allocation failed");
   int dev = 0;
@@ -522,12 +529,31 @@ extern "C" af_status af_score(af_ctx* ctx, const float* d_pts, const float* d_no
     return fail(ctx, AF_ERR_INVALID_ARG, "af_score: NULL buffer");
   if (m > (1u << 31)) return fail(ctx, AF_ERR_INVALID_ARG, "af_score: m too large");
   cudaStream_t s = (cudaStream_t)stream;
+  if (ctx->score_budget >= 0 && m > ctx->split_cap) {  // hand-off records for every point
+    cudaFree(ctx->d_over);
+    cudaFree(ctx->d_sres);
+    ctx->d_over = nullptr;
+    ctx->d_sres = nullptr;
+    ctx->split_cap = 0;
+    AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_over, (size_t)m * sizeof(int2)));
+    AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_sres, (size_t)m * 4));
+    ctx->split_cap = m;
+  }
+  const af::ScoreSplit S{ctx->d_over, ctx->d_sres, ctx->d_scount, ctx->score_budget};
   if (m > 0)
     AF_CUDA(ctx, timed(ctx, 3, s, [&] {
-              return af::launch_score(ctx->M, ctx->T, d_pts, d_normals, m, d_label, d_best, s);
-            }));
+              return af::launch_score(ctx->M, ctx->T, d_pts, d_normals, m, d_label, d_best, S,
+                                      ctx->num_sms, s);
+            }, S.budget >= 0 ? 3 : 1));
   ctx->last_stream = s;
   ctx->points_in += m;
+  return AF_OK;
+}
+
+extern "C" af_status af_set_score_split(af_ctx* ctx, int32_t budget) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_set_score_split: NULL context");
+  if (budget < -1 || budget > 4096) return fail(ctx, AF_ERR_INVALID_ARG, "af_set_score_split: budget must be in -1..4096");
+  ctx->score_budget = budget;
   return AF_OK;
 }
 
@@ -644,7 +670,7 @@ extern "C" af_status af_profile_read(af_ctx* ctx, af_profile* out, int reset) {
   for (const auto& r : ctx->prof) {
     float ms = 0.f;
     AF_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
-    out->launches[r.kernel] += 1;
+    out->launches[r.kernel] += r.kernels;
     out->ms[r.kernel] += ms;
   }
   if (reset) {

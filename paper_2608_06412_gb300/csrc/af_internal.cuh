@@ -105,6 +105,16 @@ struct MapView {
 };
 
 // Tool tables on the device (built by af_set_tool).
+// Work sharing of the plain scorer: points whose search uses up its budget
+// hand their remaining directions to a second kernel (one warp per
+// (point, direction)), which folds them into a packed lowest-index minimum.
+struct ScoreSplit {
+  int2* over;        // (point, first direction not yet searched)
+  uint32_t* res;     // packed (score << 16 | direction) of the search so far
+  uint32_t* count;   // points handed off
+  int budget;        // directions past the arm screen before a hand-off; < 0: never
+};
+
 struct ToolView {
   const float* dirs;      // G x 3 unit directions
   const short4* runs;     // x-runs (dx0, len, dy, dz), len in 1..64

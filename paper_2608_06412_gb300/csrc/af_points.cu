@@ -367,12 +367,35 @@ __device__ inline int2 better(int2 a, int2 b) {
 }
 
 constexpr int kC2FTab = 729;  // bricks a ball of radius <= 31 voxels can span (9^3)
+constexpr int kC2FNear = 64;  // ball offsets probed directly before the brick table
 
 // Stored best direction (before the batch) of the nearest other point in
 // the coarse-to-fine ball that had one; -1 if none. tb: this warp's table of
 // the ball's bricks.
 __device__ int nearest_resolved(const MapView& M, const PtView& V, const PtState& st, uint32_t* tb,
                                 int lane) {
+  // the nearest offsets first, one hash probe per lane: most points have a
+  // resolved neighbour within a voxel or two
+  const int near = min(V.c2f_noff, kC2FNear);
+  for (int c0 = 0; c0 < near; c0 += 32) {
+    const int j = c0 + lane;
+    int16_t b = -1;
+    if (j < near) {
+      const int4 o = __ldg(V.c2foff + j);
+      const int x = st.x + o.x, y = st.y + o.y, z = st.z + o.z;
+      if (box_rel(M, x, y, z)) {
+        const uint32_t bb = lookup_brick(M, pack_brick(x >> 3, y >> 3, z >> 3));
+        if (bb != kNoBlock) {
+          const int32_t id = __ldcg(V.pid + (size_t)bb * kBrickVox + vox_slot(x, y, z));
+          if (id >= 0) b = __ldcg(V.snap + id);
+        }
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, b >= 0);
+    if (bal) return __shfl_sync(0xffffffffu, (int)b, __ffs(bal) - 1);
+  }
+  if (near == V.c2f_noff) return -1;
+  // the rest of the ball through a table of its bricks
   const int R = V.c2f_R;
   const int b0x = (st.x - R) >> 3, b0y = (st.y - R) >> 3, b0z = (st.z - R) >> 3;
   const int nx = ((st.x + R) >> 3) - b0x + 1, ny = ((st.y + R) >> 3) - b0y + 1,
@@ -387,7 +410,7 @@ __device__ int nearest_resolved(const MapView& M, const PtView& V, const PtState
   }
   __syncwarp();
   int res = -1;
-  for (int c0 = 0; c0 < V.c2f_noff; c0 += 32) {
+  for (int c0 = near; c0 < V.c2f_noff; c0 += 32) {
     const int j = c0 + lane;
     int16_t b = -1;
     if (j < V.c2f_noff) {

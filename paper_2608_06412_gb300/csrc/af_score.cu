@@ -15,16 +15,27 @@
 // candidate would (the score to beat only shrinks; ties keep the lower
 // index).
 //
+// Work sharing (ScoreSplit): a point whose search takes more than `budget`
+// directions past the arm screen stops there and hands the rest of its
+// directions to k_score_split, where one warp takes each (point, direction)
+// item, prunes it against the point's packed best so far (read at the start
+// of the item; the best only ever decreases) and folds its exact score in
+// with atomicMin. The packed lowest-index minimum is the result of the full
+// search whatever the order the items run in; k_score_finish writes it out.
+// The split bounds the span of the launch by the heaviest direction instead
+// of the heaviest point.
+//
 // The device functions live in af_score.cuh.
 #include "af_score.cuh"
 
 namespace af {
 
 // Scores point pi with the whole warp (all 32 lanes call this together).
+template <bool SPLIT>
 __device__ void score_point(const MapView& M, const ToolView& T, const float* __restrict__ pts,
                             const float* __restrict__ nrm, uint32_t pi,
                             uint8_t* __restrict__ label, int16_t* __restrict__ best_out,
-                            int lane) {
+                            int lane, const ScoreSplit& S) {
   const float s0 = pts[3 * pi], s1 = pts[3 * pi + 1], s2 = pts[3 * pi + 2];
   const float n0 = nrm[3 * pi], n1 = nrm[3 * pi + 1], n2 = nrm[3 * pi + 2];
 
@@ -64,38 +75,131 @@ __device__ void score_point(const MapView& M, const ToolView& T, const float* __
                     P.py >= T.reach[1] && P.py + T.reach[1] < M.dim_vox[1] &&
                     P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
   int2 res;
-  if (fast) {
-    P.row = (P.pz * M.dim_vox[1] + P.py) * M.row_words;
-    res = best_direction<true>(M, T, P, NormalFilter{n0, n1, n2}, lane);
-  } else {
-    P.row = 0;
-    res = best_direction<false>(M, T, P, NormalFilter{n0, n1, n2}, lane);
-  }
+  int next = -1;
+  P.row = fast ? (P.pz * M.dim_vox[1] + P.py) * M.row_words : 0;
+  const NormalFilter F{n0, n1, n2};
+  if (!SPLIT)
+    res = fast ? best_direction<true>(M, T, P, F, lane) : best_direction<false>(M, T, P, F, lane);
+  else
+    res = fast ? best_direction_budget<true>(M, T, P, F, lane, S.budget, &next)
+               : best_direction_budget<false>(M, T, P, F, lane, S.budget, &next);
 
   if (lane == 0) {
-    label[pi] = (res.y >= 0 && res.x < T.n_c) ? 1 : 2;
-    best_out[pi] = (int16_t)res.y;
+    if (next < 0) {
+      label[pi] = (res.y >= 0 && res.x < T.n_c) ? 1 : 2;
+      best_out[pi] = (int16_t)res.y;
+    } else {  // hand the directions from `next` on to k_score_split
+      const uint32_t o = atomicAdd(S.count, 1u);
+      S.over[o] = make_int2((int)pi, next);
+      S.res[o] = pack_result(res);
+    }
     atomicAdd(&M.ctl->points_scored, 1ull);
     atomicAdd(&M.ctl->tests, (unsigned long long)ncand);
   }
 }
 
-template <int WARPS>
+template <int WARPS, bool SPLIT>
 __global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
     k_score(MapView M, ToolView T, const float* __restrict__ pts, const float* __restrict__ nrm,
-            uint32_t m, uint8_t* __restrict__ label, int16_t* __restrict__ best_out) {
+            uint32_t m, uint8_t* __restrict__ label, int16_t* __restrict__ best_out,
+            ScoreSplit S) {
   const uint32_t pi = blockIdx.x * WARPS + (threadIdx.x >> 5);
   if (pi >= m) return;  // whole warp
-  score_point(M, T, pts, nrm, pi, label, best_out, threadIdx.x & 31);
+  score_point<SPLIT>(M, T, pts, nrm, pi, label, best_out, threadIdx.x & 31, S);
+}
+
+// One (point, direction) item of a handed-off search; the whole warp.
+template <bool FAST>
+__device__ void split_item(const MapView& M, const ToolView& T, const Pt& P, int g, uint32_t* res,
+                           int lane) {
+  const int nc = T.n_c;
+  const uint32_t cur = __ldcg(res);
+  const int bs = (int)(cur >> 16), bg = (int)(cur & 0xFFFFu);  // bg 0xFFFF: none yet
+  bool arm_ok = false;
+  if (lane == 0) arm_ok = arm_clear<FAST>(M, T, g, P);
+  arm_ok = __shfl_sync(0xffffffffu, arm_ok, 0);
+  uint32_t mine;
+  if (!arm_ok) {
+    if (bs <= nc) return;  // blocked (n_c + 1) cannot beat an unblocked best
+    mine = pack_result(make_int2(nc + 1, g));
+  } else {
+    // counts below `sat` may improve the best; `exact` counts up to n_c
+    const bool exact = bs > nc || (g < bg && bs == nc);
+    const int sat = exact ? nc : (g < bg ? bs + 1 : bs);
+    if (!exact && sat == 0) return;
+    const int c = tool_count<FAST>(M, T, g, P, sat, lane);
+    if (!exact && c >= sat) return;
+    mine = corridor_blocked<FAST>(M, T, g, P, lane) ? pack_result(make_int2(nc + 1, g))
+                                                   : pack_result(make_int2(min(c, nc), g));
+  }
+  if (lane == 0 && mine < cur) atomicMin(res, mine);
+}
+
+__global__ void __launch_bounds__(128, 16)
+    k_score_split(MapView M, ToolView T, const float* __restrict__ pts,
+                  const float* __restrict__ nrm, ScoreSplit S) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t items = (uint64_t)__ldcg(S.count) * (uint64_t)T.G;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t it = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nw) {
+    const uint32_t o = (uint32_t)(it / (uint64_t)T.G);
+    const int g = (int)(it - (uint64_t)o * T.G);
+    const int2 ov = __ldcg(S.over + o);
+    if (g < ov.y) continue;
+    const uint32_t pi = (uint32_t)ov.x;
+    if (!candidate(T, g, nrm[3 * pi], nrm[3 * pi + 1], nrm[3 * pi + 2])) continue;
+    // the point passed the gate in k_score, so its voxel is inside the box
+    int i0, i1, i2;
+    voxel_index(pts[3 * pi], M, &i0);
+    voxel_index(pts[3 * pi + 1], M, &i1);
+    voxel_index(pts[3 * pi + 2], M, &i2);
+    Pt P;
+    P.px = i0 - M.dom_vox[0];
+    P.py = i1 - M.dom_vox[1];
+    P.pz = i2 - M.dom_vox[2];
+    const bool fast = P.px >= T.reach[0] && P.px + T.reach[0] < M.dim_vox[0] &&
+                      P.py >= T.reach[1] && P.py + T.reach[1] < M.dim_vox[1] &&
+                      P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
+    P.row = fast ? (P.pz * M.dim_vox[1] + P.py) * M.row_words : 0;
+    if (fast)
+      split_item<true>(M, T, P, g, S.res + o, lane);
+    else
+      split_item<false>(M, T, P, g, S.res + o, lane);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_score_finish(ScoreSplit S, int n_c,
+                                                      uint8_t* __restrict__ label,
+                                                      int16_t* __restrict__ best_out) {
+  const uint32_t n = __ldcg(S.count);
+  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    const uint32_t r = S.res[o];
+    const uint32_t pi = (uint32_t)S.over[o].x;
+    const int sc = (int)(r >> 16), g = (int)(r & 0xFFFFu);
+    best_out[pi] = g == 0xFFFF ? (int16_t)-1 : (int16_t)g;
+    label[pi] = (g != 0xFFFF && sc < n_c) ? 1 : 2;
+  }
 }
 
 cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts,
                          const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
-                         cudaStream_t stream) {
+                         const ScoreSplit& S, int num_sms, cudaStream_t stream) {
   if (m == 0) return cudaSuccess;
   constexpr int WARPS = 2;
-  k_score<WARPS><<<(m + WARPS - 1) / WARPS, WARPS * 32, 0, stream>>>(M, T, d_pts, d_nrm, m,
-                                                                      d_label, d_best);
+  if (S.budget >= 0) {
+    cudaError_t e = cudaMemsetAsync(S.count, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (S.budget >= 0)
+    k_score<WARPS, true><<<(m + WARPS - 1) / WARPS, WARPS * 32, 0, stream>>>(M, T, d_pts, d_nrm,
+                                                                            m, d_label, d_best, S);
+  else
+    k_score<WARPS, false><<<(m + WARPS - 1) / WARPS, WARPS * 32, 0, stream>>>(M, T, d_pts, d_nrm,
+                                                                             m, d_label, d_best, S);
+  if (S.budget >= 0) {
+    k_score_split<<<num_sms * 16, 128, 0, stream>>>(M, T, d_pts, d_nrm, S);
+    k_score_finish<<<num_sms, 256, 0, stream>>>(S, T.n_c, d_label, d_best);
+  }
   return cudaGetLastError();
 }
 
@@ -111,7 +215,8 @@ __global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
   for (uint32_t pg = blockIdx.x * WARPS + (threadIdx.x >> 5); pg < total; pg += nw) {
     const int s = scene_of<2>(D, count, pg);
     const SceneDesc& d = D[s];
-    score_point(d.M, d.T, d.pts, d.nrm, pg - d.pt_off, d.label, d.best, threadIdx.x & 31);
+    score_point<false>(d.M, d.T, d.pts, d.nrm, pg - d.pt_off, d.label, d.best, threadIdx.x & 31,
+                       ScoreSplit{nullptr, nullptr, nullptr, -1});
   }
 }
 

@@ -228,4 +228,65 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
   return make_int2(bscore, best);
 }
 
+
+// best_direction with a budget: at most `budget` directions are taken past
+// the arm screen (tool count and corridor). If the search stops early,
+// *next receives the first direction index not searched and the result is
+// exact over the directions before it; *next = -1 when the search finished.
+template <bool FAST, class Cand>
+__device__ inline int2 best_direction_budget(const MapView& M, const ToolView& T, const Pt& P,
+                                             const Cand& cand_of, int lane, int budget,
+                                             int* next) {
+  const int nc = T.n_c;
+  int bscore = nc + 2, best = -1, spent = 0;
+  *next = -1;
+  for (int gb = 0; gb < T.G && bscore != 0; gb += 32) {
+    const bool cand = cand_of(T, gb + lane);
+    unsigned mask = __ballot_sync(0xffffffffu, cand);
+    const unsigned arm_ok = __ballot_sync(0xffffffffu, cand && arm_clear<FAST>(M, T, gb + lane, P));
+    while (mask) {
+      const int bit = __ffs(mask) - 1;
+      const int g = gb + bit;
+      mask &= mask - 1u;
+      if (!((arm_ok >> bit) & 1u)) {
+        if (best < 0) {
+          bscore = nc + 1;
+          best = g;
+        }
+        continue;
+      }
+      if (spent == budget) {
+        *next = g;
+        return make_int2(bscore, best);
+      }
+      ++spent;
+      if (bscore <= nc) {
+        const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
+        if (cnt >= bscore) continue;
+        if (corridor_blocked<FAST>(M, T, g, P, lane)) continue;
+        bscore = cnt;
+        best = g;
+      } else {
+        if (corridor_blocked<FAST>(M, T, g, P, lane)) {
+          if (best < 0) {
+            bscore = nc + 1;
+            best = g;
+          }
+          continue;
+        }
+        bscore = tool_count<FAST>(M, T, g, P, nc, lane);
+        best = g;
+      }
+      if (bscore == 0) break;
+    }
+  }
+  return make_int2(bscore, best);
+}
+
+// A (score, direction) result packed so that the lowest-index minimum is the
+// smallest word: score in the high half, direction (0xFFFF: none) below.
+__device__ inline uint32_t pack_result(int2 r) {
+  return ((uint32_t)r.x << 16) | (r.y < 0 ? 0xFFFFu : (uint32_t)r.y);
+}
+
 }  // namespace af

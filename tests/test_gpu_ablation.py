@@ -160,12 +160,12 @@ def test_yaw_ring_scoring():
     g.set_tool(af.ToolConfig(**t), dirs)
     lab, best = g.score(to_dev(pts.astype(np.float32)), to_dev(nrm.astype(np.float32)))
     torch.cuda.synchronize()
-    ol, ob = o.score(oracle.Tool(**t), dirs, pts, nrm)
+    ol, ob, ds = o.score(oracle.Tool(**t), dirs, pts, nrm, dir_scores=True)
     gl, gb = lab.cpu().numpy(), best.cpu().numpy()
     bad = np.nonzero((gl != ol) | (gb != ob))[0]
     assert len(bad) == 0, (len(bad), bad[:5])
     assert (ol == oracle.ACCESSIBLE).sum() > 20 and (ol == oracle.BLOCKED).sum() > 20
-    assert (ob >= 160).any()          # the last, partial group of 32 directions is searched
+    assert (ds[:, 160:] >= 0).any()   # the last, partial group of 32 holds candidates
 
 
 @pytest.mark.parametrize("c2f", [False, True])

@@ -133,3 +133,38 @@ def test_score_before_tool_is_state_error(single):
     with pytest.raises(af.AfError) as e:
         _gpu_score(g, np.zeros((4, 3), np.float32), np.ones((4, 3), np.float32))
     assert e.value.status == af.ERR_STATE
+
+
+@pytest.fixture(scope="module")
+def oracle_single(single):
+    W, fr, pts, nrm, g, o = single
+    return o.score(oracle_tool(W), W.dirs, pts, nrm)
+
+
+@pytest.mark.parametrize("budget", [-1, 0, 1, 3, 8, 1000])
+def test_work_sharing_budgets(single, oracle_single, budget):
+    """af_set_score_split: every hand-off threshold gives the single-pass
+    result (0: every searched direction is its own warp; -1: no hand-off)."""
+    W, fr, pts, nrm, g, o = single
+    g.set_tool(W.af_tool(), W.dirs)
+    g.set_score_split(budget)
+    try:
+        gl, gb = _gpu_score(g, pts, nrm)
+    finally:
+        g.set_score_split(8)
+    _compare(gl, gb, *oracle_single)
+
+
+def test_work_sharing_grows_past_max_points(single, oracle_single):
+    """More points per call than the map's max_points: the hand-off records
+    grow; a bad budget is rejected."""
+    W, fr, pts, nrm, _, o = single
+    g = gpu_map(W, max_points=64)
+    g.integrate_scan(to_dev(fr.pts), fr.pose)
+    g.set_tool(W.af_tool(), W.dirs)
+    g.set_score_split(0)
+    gl, gb = _gpu_score(g, pts, nrm)
+    _compare(gl, gb, *oracle_single)
+    with pytest.raises(af.AfError) as e:
+        g.set_score_split(-2)
+    assert e.value.status == af.ERR_INVALID_ARG
