@@ -182,7 +182,7 @@ af_status af_score(af_ctx *ctx, const float *d_pts, const float *d_normals, uint
  * of its directions to a second kernel that searches them one warp per
  * (point, direction); the labels and best directions are identical to the
  * single-pass search for every budget. budget = -1: single pass, one warp
- * per point; 0 .. 4096: the hand-off threshold (default 8). The hand-off
+ * per point (the default); 0 .. 4096: the hand-off threshold. The hand-off
  * records take 12 bytes per point, allocated for max_points at af_create and
  * grown (synchronously) for larger m. Adds two launches per af_score call.
  */

@@ -63,7 +63,7 @@ struct af_ctx {
   uint32_t* d_sres = nullptr;
   uint32_t* d_scount = nullptr;
   uint32_t split_cap = 0;
-  int score_budget = 8;
+  int score_budget = -1;
   // the projective ablation's range image (af_integrate_scan_projective)
   unsigned* d_img = nullptr;
   size_t img_cap = 0;

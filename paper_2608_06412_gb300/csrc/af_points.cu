@@ -349,13 +349,17 @@ struct CoarseFilter {
     return g < T.G && g % stride == 0 && F(T, g);
   }
 };
+// The window around `centre`; with `coarse` also every stride-th direction,
+// else without them (they were searched already).
 struct WindowFilter {
   const NormalViewFilter& F;
-  int centre, half;
+  int centre, half, stride;
+  bool coarse;
   __device__ bool operator()(const ToolView& T, int g) const {
     if (g >= T.G) return false;
     const int d = abs(g - centre);
-    return min(d, T.G - d) <= half && F(T, g);
+    const bool in_coarse = g % stride == 0;
+    return (min(d, T.G - d) <= half ? (coarse || !in_coarse) : (coarse && in_coarse)) && F(T, g);
   }
 };
 
@@ -559,13 +563,17 @@ __global__ void __launch_bounds__(128) k_pts_eval(MapView M, ToolView T, PtView 
       // coarse set, then the window around the nearest resolved neighbour's
       // direction (else around the coarse best); lowest-index minimum of both
       const int nb = nearest_resolved(M, V, st, s_c2f[threadIdx.x >> 5], lane);
-      const CoarseFilter Fc{F, V.c2f_stride};
-      res = fast ? best_direction<true>(M, T, P, Fc, lane) : best_direction<false>(M, T, P, Fc, lane);
-      const int centre = nb >= 0 ? nb : res.y;
-      if (centre >= 0) {
-        const WindowFilter Fw{F, centre, V.c2f_half};
-        res = better(res, fast ? best_direction<true>(M, T, P, Fw, lane)
-                               : best_direction<false>(M, T, P, Fw, lane));
+      if (nb >= 0) {  // one pass over the coarse set and the neighbour's window
+        const WindowFilter Fu{F, nb, V.c2f_half, V.c2f_stride, true};
+        res = fast ? best_direction<true>(M, T, P, Fu, lane) : best_direction<false>(M, T, P, Fu, lane);
+      } else {  // the coarse set, then the window around its best
+        const CoarseFilter Fc{F, V.c2f_stride};
+        res = fast ? best_direction<true>(M, T, P, Fc, lane) : best_direction<false>(M, T, P, Fc, lane);
+        if (res.y >= 0) {
+          const WindowFilter Fw{F, res.y, V.c2f_half, V.c2f_stride, false};
+          res = better(res, fast ? best_direction<true>(M, T, P, Fw, lane)
+                                 : best_direction<false>(M, T, P, Fw, lane));
+        }
       }
     }
     const int nc = T.n_c;

@@ -139,28 +139,42 @@ __device__ inline bool arm_clear(const MapView& M, const ToolView& T, int g, con
   return !blocked;
 }
 
+// One corridor run: occupied (strict: or not known) anywhere in it.
+template <bool FAST>
+__device__ inline bool corridor_run_hit(const MapView& M, const ToolView& T, int r, const Pt& P) {
+  const RunEntry e = load_run<FAST>(T, r);
+  int len;
+  bool out = false;
+  bool h = run_bits<FAST>(M.occ, M, e, P, &len, &out) != 0ull;
+  if (T.strict && !h) {
+    const unsigned long long kb = run_bits<FAST>(M.known, M, e, P, &len, &out);
+    const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
+    h = out || (kb != full);
+  }
+  return h;
+}
+
 // Corridor of direction g: any occupied voxel (strict: or unknown) blocks.
+// The first warp step tests 32 runs (most blocked corridors end there); later
+// steps test 64, then 128 runs, each lane issuing its runs' loads together,
+// so a clear corridor costs fewer dependent round trips.
 template <bool FAST>
 __device__ inline bool corridor_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
                                         int lane) {
   const int4 dt = __ldg(T.dtab + g);
-  bool blocked = false;
-  walk_runs<FAST>(T, dt.z, dt.w, lane, [&](RunEntry e, bool valid) {
+  int b = dt.z, per = 1;
+  while (b < dt.w) {
     bool h = false;
-    if (valid) {
-      int len;
-      bool out = false;
-      h = run_bits<FAST>(M.occ, M, e, P, &len, &out) != 0ull;
-      if (T.strict && !h) {
-        const unsigned long long kb = run_bits<FAST>(M.known, M, e, P, &len, &out);
-        const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
-        h = out || (kb != full);
-      }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = b + 32 * k + lane;
+      if (k < per && r < dt.w) h |= corridor_run_hit<FAST>(M, T, r, P);
     }
-    blocked = __any_sync(0xffffffffu, h);
-    return blocked;
-  });
-  return blocked;
+    if (__any_sync(0xffffffffu, h)) return true;
+    b += 32 * per;
+    per = per < 4 ? 2 * per : 4;
+  }
+  return false;
 }
 
 __device__ inline bool candidate(const ToolView& T, int g, float n0, float n1, float n2) {

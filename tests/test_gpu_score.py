@@ -151,7 +151,7 @@ def test_work_sharing_budgets(single, oracle_single, budget):
     try:
         gl, gb = _gpu_score(g, pts, nrm)
     finally:
-        g.set_score_split(8)
+        g.set_score_split(-1)
     _compare(gl, gb, *oracle_single)
 
 
