@@ -5,6 +5,7 @@
 #include <af.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -151,25 +152,42 @@ std::vector<Offset> rasterise(const af_tool& t, double v, const double u[3], int
   return out;
 }
 
-// Groups z-major offsets into x-runs of at most 64 voxels, ordered by the
+// The axis a direction's runs follow: the one it is closest to (largest
+// |u_k|, the lowest k on ties).
+int run_axis(const double u[3]) {
+  int a = std::fabs(u[1]) > std::fabs(u[0]) ? 1 : 0;
+  return std::fabs(u[2]) > std::fabs(u[a]) ? 2 : a;
+}
+
+// Groups offsets into runs of at most 64 voxels along `axis`, ordered by the
 // axial distance of their first voxel (near runs first: blocking geometry
-// next to the surface is met early).
-void to_runs(const std::vector<Offset>& offs, double v, const double u[3],
+// next to the surface is met early). A run is (d_axis, len | axis << 8,
+// d_o1, d_o2), o1 < o2 the other two axes.
+void to_runs(const std::vector<Offset>& offs, double v, const double u[3], int axis,
              std::vector<short4>* runs) {
   struct R {
     double a;
     short4 s;
   };
+  const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+  std::vector<std::array<int, 3>> c(offs.size());
+  for (size_t k = 0; k < offs.size(); ++k) c[k] = {offs[k].x, offs[k].y, offs[k].z};
+  std::sort(c.begin(), c.end(), [&](const std::array<int, 3>& p, const std::array<int, 3>& q) {
+    if (p[o2] != q[o2]) return p[o2] < q[o2];
+    if (p[o1] != q[o1]) return p[o1] < q[o1];
+    return p[axis] < q[axis];
+  });
   std::vector<R> rs;
   size_t i = 0;
-  while (i < offs.size()) {
+  while (i < c.size()) {
     size_t j = i + 1;
-    while (j < offs.size() && offs[j].y == offs[i].y && offs[j].z == offs[i].z &&
-           offs[j].x == offs[j - 1].x + 1 && (int)(j - i) < 64)
+    while (j < c.size() && c[j][o1] == c[i][o1] && c[j][o2] == c[i][o2] &&
+           c[j][axis] == c[j - 1][axis] + 1 && (int)(j - i) < 64)
       ++j;
-    const Offset& o = offs[i];
-    const double a = ((double)o.x * v * u[0] + (double)o.y * v * u[1]) + (double)o.z * v * u[2];
-    rs.push_back({a, make_short4((short)o.x, (short)(j - i), (short)o.y, (short)o.z)});
+    const std::array<int, 3>& o = c[i];
+    const double a = ((double)o[0] * v * u[0] + (double)o[1] * v * u[1]) + (double)o[2] * v * u[2];
+    rs.push_back({a, make_short4((short)o[axis], (short)((int)(j - i) | (axis << 8)), (short)o[o1],
+                                 (short)o[o2])});
     i = j;
   }
   std::stable_sort(rs.begin(), rs.end(), [](const R& p, const R& q) { return p.a < q.a; });
@@ -265,6 +283,8 @@ static void free_all(af_ctx* c) {
   cudaFree(M.rtab);
   cudaFree(M.occ);
   cudaFree(M.known);
+  cudaFree(M.occ_y);
+  cudaFree(M.occ_z);
   cudaFree(M.ctl);
   cudaFree(c->d_ret);
   cudaFree(c->d_xyz);
@@ -349,6 +369,8 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
     M.dim_vox[k] = (int)cfg->domain_bricks[k] * 8;
   }
   M.row_words = (M.dim_vox[0] + 63) / 64;
+  M.row_words_y = (M.dim_vox[1] + 63) / 64;
+  M.row_words_z = (M.dim_vox[2] + 63) / 64;
   M.hmask = cfg->hash_capacity - 1;
   M.pool_blocks = cfg->pool_blocks;
   {
@@ -376,6 +398,10 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   if (st == AF_OK) st = alloc((void**)&M.dirty, P * 4, 0);
   if (st == AF_OK) st = alloc((void**)&M.occ, plane, 0);
   if (st == AF_OK) st = alloc((void**)&M.known, plane, 0);
+  if (st == AF_OK)
+    st = alloc((void**)&M.occ_y, (size_t)M.row_words_y * 8 * M.dim_vox[0] * M.dim_vox[2], 0);
+  if (st == AF_OK)
+    st = alloc((void**)&M.occ_z, (size_t)M.row_words_z * 8 * M.dim_vox[0] * M.dim_vox[1], 0);
   if (st == AF_OK) st = alloc((void**)&M.ctl, sizeof(af::Control), 0);
   if (st == AF_OK) st = alloc((void**)&c->d_ret, R * sizeof(float4), 0);
   if (st == AF_OK) st = alloc((void**)&M.rtab, R * (size_t)M.nbmax * 4, 0);
@@ -449,6 +475,7 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
     if (!finite3(h_dirs + 3 * g)) return fail(ctx, AF_ERR_INVALID_ARG, "non-finite direction");
 
   const double v = (double)ctx->cfg.voxel_size, tau = (double)ctx->cfg.truncation;
+  int reach[3] = {0, 0, 0};
   std::vector<short4> runs;
   std::vector<int4> dtab(G);
   std::vector<short4> arm(3 * G);
@@ -460,12 +487,21 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
       for (const Offset& x : *o)
         if (std::abs(x.x) > 32000 || std::abs(x.y) > 32000 || std::abs(x.z) > 32000)
           return fail(ctx, AF_ERR_INVALID_ARG, "tool reach exceeds 32000 voxels");
+    // runs along the direction's closest axis; the strict corridor also reads
+    // the known view, which has x rows only
+    const int ax = run_axis(u);
     dtab[g].x = (int)runs.size();
-    to_runs(tool_o, v, u, &runs);
+    to_runs(tool_o, v, u, ax, &runs);
     dtab[g].y = (int)runs.size();
     dtab[g].z = (int)runs.size();
-    to_runs(corr_o, v, u, &runs);
+    to_runs(corr_o, v, u, tool->corridor_strict ? 0 : ax, &runs);
     dtab[g].w = (int)runs.size();
+    for (const std::vector<Offset>* o : {&tool_o, &corr_o})
+      for (const Offset& x : *o) {
+        reach[0] = std::max(reach[0], std::abs(x.x));
+        reach[1] = std::max(reach[1], std::abs(x.y));
+        reach[2] = std::max(reach[2], std::abs(x.z));
+      }
     int a[9];
     arm_offsets(v, tau, u, a);
     for (int k = 0; k < 3; ++k)
@@ -476,17 +512,19 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
   // the point's row, valid while every plane index fits in 31 bits. `reach` bounds
   // every offset, so a point at least `reach` voxels inside the box needs no checks.
   const MapView& M = ctx->M;
-  const int64_t plane_words = (int64_t)M.row_words * M.dim_vox[1] * M.dim_vox[2];
-  const bool fast_ok = plane_words < (1ll << 31);
+  const int X = M.dim_vox[0], Y = M.dim_vox[1], Z = M.dim_vox[2];
+  const bool fast_ok = (int64_t)M.row_words * Y * Z < (1ll << 31) &&
+                       (int64_t)M.row_words_y * X * Z < (1ll << 31) &&
+                       (int64_t)M.row_words_z * X * Y < (1ll << 31);
+  // plane rows: axis x -> row z * Y + y; axis y -> z * X + x; axis z -> y * X + x
+  const int dim_o1[3] = {Y, X, X};
+  const int rw[3] = {M.row_words, M.row_words_y, M.row_words_z};
   std::vector<int2> fruns(runs.size());
-  int reach[3] = {0, 0, 0};
   for (size_t r = 0; r < runs.size(); ++r) {
     const short4 s = runs[r];
-    const int64_t delta = ((int64_t)s.w * M.dim_vox[1] + s.z) * M.row_words;
-    fruns[r] = make_int2((int)delta, (int)(uint16_t)s.x | ((int)s.y << 16));
-    reach[0] = std::max({reach[0], std::abs((int)s.x), std::abs((int)s.x + (int)s.y - 1)});
-    reach[1] = std::max(reach[1], std::abs((int)s.z));
-    reach[2] = std::max(reach[2], std::abs((int)s.w));
+    const int ax = ((uint16_t)s.y >> 8) & 3, len = (uint16_t)s.y & 0xFF;
+    const int64_t delta = ((int64_t)s.w * dim_o1[ax] + s.z) * rw[ax];
+    fruns[r] = make_int2((int)delta, (int)(uint16_t)s.x | (len << 16) | (ax << 24));
   }
   for (const short4& a : arm) {
     reach[0] = std::max(reach[0], std::abs((int)a.x));

@@ -354,15 +354,20 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
 }
 
 // Weight cap and bit view of one dirty brick; called by a CTA of 512 threads
-// (one voxel each).
+// (one voxel each). The x-row bytes come straight from the ballots; the y-
+// and z-row bytes of the occupied view are gathered from the brick's 512
+// bits in shared memory.
 __device__ void bitview_brick(const MapView& M, uint32_t blk) {
+  __shared__ unsigned s_ob[16];
   const int l = threadIdx.x;
   const int lane = l & 31, wi = l >> 5;
   unsigned char* occ = reinterpret_cast<unsigned char*>(M.occ);
   unsigned char* known = reinterpret_cast<unsigned char*>(M.known);
   const size_t row_bytes = (size_t)M.row_words * 8;
+  const uint64_t key = M.bkey[blk];
+  const uint32_t bx = (uint32_t)(key & 0x1FFFFF), by = (uint32_t)((key >> 21) & 0x1FFFFF),
+                 bz = (uint32_t)(key >> 42);
   {
-    const uint64_t key = M.bkey[blk];
     unsigned long long* wp = M.vox + (size_t)blk * kBrickVox + l;
     unsigned long long word = *wp;
     unsigned long long w = word & kWMask;
@@ -377,9 +382,8 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
     const bool kn = w >= 1 || cl;
     const unsigned ob = __ballot_sync(0xffffffffu, o);
     const unsigned kb = __ballot_sync(0xffffffffu, kn);
+    if (lane == 0) s_ob[wi] = ob;
     if (lane < 4) {
-      const uint32_t bx = (uint32_t)(key & 0x1FFFFF), by = (uint32_t)((key >> 21) & 0x1FFFFF),
-                     bz = (uint32_t)(key >> 42);
       const size_t y = (size_t)by * 8 + (wi & 1) * 4 + lane;
       const size_t z = (size_t)bz * 8 + (wi >> 1);
       const size_t at = (z * (size_t)M.dim_vox[1] + y) * row_bytes + bx;
@@ -387,6 +391,28 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
       known[at] = (unsigned char)(kb >> (8 * lane));
     }
   }
+  __syncthreads();
+  if (l < 128) {
+    // l < 64: the y row at (x, z) = (l & 7, l >> 3); else the z row at (x, y)
+    const int x = l & 7, c = (l >> 3) & 7;
+    unsigned byte = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int v = l < 64 ? x + 8 * k + 64 * c : x + 8 * c + 64 * k;
+      byte |= ((s_ob[v >> 5] >> (v & 31)) & 1u) << k;
+    }
+    const size_t X = (size_t)M.dim_vox[0], xa = (size_t)bx * 8 + x;
+    if (l < 64) {
+      const size_t z = (size_t)bz * 8 + c;
+      reinterpret_cast<unsigned char*>(M.occ_y)[(z * X + xa) * ((size_t)M.row_words_y * 8) + by] =
+          (unsigned char)byte;
+    } else {
+      const size_t y = (size_t)by * 8 + c;
+      reinterpret_cast<unsigned char*>(M.occ_z)[(y * X + xa) * ((size_t)M.row_words_z * 8) + bz] =
+          (unsigned char)byte;
+    }
+  }
+  __syncthreads();  // s_ob is rewritten for the CTA's next brick
 }
 
 // Weight cap and bit view of every brick touched by the scan.

@@ -17,7 +17,10 @@
 //  * planes : the occupied and known views as dense bit planes over the map
 //             box, one bit per voxel, rows along x (64 voxels per u64 word),
 //             row index z * Y + y. A brick row of 8 voxels is one byte, so the
-//             view of a brick is 64 byte stores per plane.
+//             view of a brick is 64 byte stores per plane. The occupied view
+//             is also kept with rows along y (row index z * X + x) and along
+//             z (row index y * X + x), so a kernel run can follow whichever
+//             axis its direction is closest to.
 #pragma once
 
 #include <cstdint>
@@ -86,6 +89,9 @@ struct MapView {
   int dom_vox[3];     // absolute voxel index of the box's min corner
   int dim_vox[3];     // box size in voxels (multiples of 8)
   int row_words;      // u64 words per plane row
+  unsigned long long* occ_y;  // occupied, rows along y: row z * X + x
+  unsigned long long* occ_z;  // occupied, rows along z: row y * X + x
+  int row_words_y, row_words_z;
   // hash
   struct HashSlot* slots;
   uint32_t hmask;     // capacity - 1

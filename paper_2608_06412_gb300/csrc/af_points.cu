@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(128) k_pts_eval(MapView M, ToolView T, PtView 
                       P.py >= T.reach[1] && P.py + T.reach[1] < M.dim_vox[1] &&
                       P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
     int2 res;
-    P.row = fast ? (P.pz * M.dim_vox[1] + P.py) * M.row_words : 0;
+    if (fast) set_rows(M, P); else P.row = P.rowy = P.rowz = 0;
     if (V.c2f_stride == 0) {
       res = fast ? best_direction<true>(M, T, P, F, lane) : best_direction<false>(M, T, P, F, lane);
     } else {

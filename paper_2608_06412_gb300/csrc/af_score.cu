@@ -76,7 +76,7 @@ __device__ void score_point(const MapView& M, const ToolView& T, const float* __
                     P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
   int2 res;
   int next = -1;
-  P.row = fast ? (P.pz * M.dim_vox[1] + P.py) * M.row_words : 0;
+  if (fast) set_rows(M, P); else P.row = P.rowy = P.rowz = 0;
   const NormalFilter F{n0, n1, n2};
   if (!SPLIT)
     res = fast ? best_direction<true>(M, T, P, F, lane) : best_direction<false>(M, T, P, F, lane);
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(128, 16)
     const bool fast = P.px >= T.reach[0] && P.px + T.reach[0] < M.dim_vox[0] &&
                       P.py >= T.reach[1] && P.py + T.reach[1] < M.dim_vox[1] &&
                       P.pz >= T.reach[2] && P.pz + T.reach[2] < M.dim_vox[2];
-    P.row = fast ? (P.pz * M.dim_vox[1] + P.py) * M.row_words : 0;
+    if (fast) set_rows(M, P); else P.row = P.rowy = P.rowz = 0;
     if (fast)
       split_item<true>(M, T, P, g, S.res + o, lane);
     else

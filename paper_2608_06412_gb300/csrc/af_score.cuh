@@ -1,12 +1,14 @@
 // af_score.cuh -- the scoring device functions (Sec. 3.4, 3.5), shared by the
 // plain, batched and stateful-layer scoring kernels.
 //
-// Kernels are x-runs rather than voxel lists: a cylinder meets every x-row
-// in one interval (two at most next to the self-exclusion ball), so a run
-// of up to 64 voxels costs one or two loads of the bit plane. A point whose
-// whole kernel reach lies inside the map box takes the FAST path: the run
-// table then holds each run's row as a plane-word offset from the point's
-// row, and no bound is checked.
+// Kernels are runs rather than voxel lists: a cylinder meets every row in
+// one interval (two at most next to the self-exclusion ball), so a run of up
+// to 64 voxels costs one or two loads of a bit plane. Each direction's runs
+// follow the axis it is closest to, read from the occupied view with rows
+// along that axis, so a kernel is a few long runs instead of many short
+// ones. A point whose whole kernel reach lies inside the map box takes the
+// FAST path: the run table then holds each run's row as a plane-word offset
+// from the point's row on that plane, and no bound is checked.
 #pragma once
 
 #include "af_internal.cuh"
@@ -15,26 +17,39 @@ namespace af {
 
 struct Pt {
   int px, py, pz;  // box-relative voxel of the point
-  int row;         // plane-word index of the point's row (FAST path only)
+  int row;         // plane-word index of the point's x row (FAST path only)
+  int rowy, rowz;  // ... of its y row and z row
 };
 
-// Bits x0 .. x0+len-1 of plane row (y, z), bit i = voxel x0 + i; voxels
+// The point's row bases on the three planes (FAST path).
+__device__ inline void set_rows(const MapView& M, Pt& P) {
+  P.row = (P.pz * M.dim_vox[1] + P.py) * M.row_words;
+  P.rowy = (P.pz * M.dim_vox[0] + P.px) * M.row_words_y;
+  P.rowz = (P.py * M.dim_vox[0] + P.px) * M.row_words_z;
+}
+
+// Bits a0 .. a0+len-1 along axis `ax` of the plane row at the other two
+// coordinates (o1, o2) (o1 the lower axis), bit i = voxel a0 + i; voxels
 // outside the map box read 0 and set *outside.
 __device__ inline unsigned long long row_bits(const unsigned long long* __restrict__ plane,
-                                              const MapView& M, int x0, int y, int z, int len,
-                                              bool* outside) {
-  if ((unsigned)y >= (unsigned)M.dim_vox[1] || (unsigned)z >= (unsigned)M.dim_vox[2]) {
+                                              const MapView& M, int ax, int x0, int o1, int o2,
+                                              int len, bool* outside) {
+  const int A = M.dim_vox[ax];
+  const int O1 = ax == 0 ? M.dim_vox[1] : M.dim_vox[0];
+  const int O2 = ax == 2 ? M.dim_vox[1] : M.dim_vox[2];
+  const int rw = ax == 0 ? M.row_words : (ax == 1 ? M.row_words_y : M.row_words_z);
+  if ((unsigned)o1 >= (unsigned)O1 || (unsigned)o2 >= (unsigned)O2) {
     *outside = true;
     return 0ull;
   }
   int xa = x0, xb = x0 + len - 1;
-  if (xa < 0 || xb >= M.dim_vox[0]) {
+  if (xa < 0 || xb >= A) {
     *outside = true;
     xa = max(xa, 0);
-    xb = min(xb, M.dim_vox[0] - 1);
+    xb = min(xb, A - 1);
     if (xa > xb) return 0ull;
   }
-  const unsigned long long* row = plane + ((size_t)z * M.dim_vox[1] + y) * M.row_words;
+  const unsigned long long* row = plane + ((size_t)o2 * O1 + o1) * rw;
   const int wa = xa >> 6, wb = xb >> 6, sh = xa & 63;
   unsigned long long win = __ldg(row + wa) >> sh;
   if (wb != wa) win |= __ldg(row + wb) << (64 - sh);
@@ -43,8 +58,9 @@ __device__ inline unsigned long long row_bits(const unsigned long long* __restri
   return win << (xa - x0);
 }
 
-// One run-table entry: the fast form (plane-word row offset, dx0 | len << 16)
-// or the plain form (dx0 | len << 16, dy | dz << 16), 16-bit fields.
+// One run-table entry: the fast form (plane-word row offset,
+// d0 | len << 16 | axis << 24) or the plain form (d0 | (len | axis << 8) << 16,
+// d1 | d2 << 16), d0 along the run's axis, d1 < d2 the other two axes.
 struct RunEntry {
   int a, b;
 };
@@ -61,15 +77,19 @@ __device__ inline RunEntry load_run(const ToolView& T, int r) {
 }
 
 // Bits of the run of entry e for point P; *len receives the run length.
+// `px`, `py`, `pz`: the view with rows along x, y, z (a view kept with x
+// rows only is passed for all three; its runs are all along x).
 template <bool FAST>
-__device__ inline unsigned long long run_bits(const unsigned long long* __restrict__ plane,
+__device__ inline unsigned long long run_bits(const unsigned long long* __restrict__ px,
+                                              const unsigned long long* __restrict__ py,
+                                              const unsigned long long* __restrict__ pz,
                                               const MapView& M, RunEntry e, const Pt& P,
                                               int* len, bool* outside) {
-  const int dx0 = (int)(short)(e.a & 0xffff), dxy = (int)(short)(e.b & 0xffff);
   if (FAST) {
-    const int n = e.b >> 16;
-    const int xa = P.px + dxy;
-    const int row = P.row + e.a;
+    const int d0 = (int)(short)(e.b & 0xffff), n = (e.b >> 16) & 0xFF, ax = (e.b >> 24) & 3;
+    const int xa = (ax == 0 ? P.px : (ax == 1 ? P.py : P.pz)) + d0;
+    const int row = (ax == 0 ? P.row : (ax == 1 ? P.rowy : P.rowz)) + e.a;
+    const unsigned long long* plane = ax == 0 ? px : (ax == 1 ? py : pz);
     const int wa = xa >> 6, wb = (xa + n - 1) >> 6, sh = xa & 63;
     unsigned long long win = __ldg(plane + row + wa) >> sh;
     if (wb != wa) win |= __ldg(plane + row + wb) << (64 - sh);
@@ -77,9 +97,15 @@ __device__ inline unsigned long long run_bits(const unsigned long long* __restri
     *len = n;
     return win;
   }
-  const int n = (int)((uint32_t)e.a >> 16), dz = (int)(short)((uint32_t)e.b >> 16);
+  const int d0 = (int)(short)(e.a & 0xffff), n = (int)(((uint32_t)e.a >> 16) & 0xFF),
+            ax = (int)(((uint32_t)e.a >> 24) & 3);
+  const int d1 = (int)(short)(e.b & 0xffff), d2 = (int)(short)((uint32_t)e.b >> 16);
   *len = n;
-  return row_bits(plane, M, P.px + dx0, P.py + dxy, P.pz + dz, n, outside);
+  // (a, o1, o2) coordinates of the run's first voxel
+  const int a0 = (ax == 0 ? P.px : (ax == 1 ? P.py : P.pz)) + d0;
+  const int o1 = (ax == 0 ? P.py : P.px) + d1;
+  const int o2 = (ax == 2 ? P.py : P.pz) + d2;
+  return row_bits(ax == 0 ? px : (ax == 1 ? py : pz), M, ax, a0, o1, o2, n, outside);
 }
 
 // Walks runs [r0, r1) of the tables a warp step (32 runs, one per lane) at a
@@ -116,7 +142,7 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, con
     if (valid) {
       int len;
       bool out = false;
-      c = __popcll(run_bits<FAST>(M.occ, M, e, P, &len, &out));
+      c = __popcll(run_bits<FAST>(M.occ, M.occ_y, M.occ_z, M, e, P, &len, &out));
     }
     total += __reduce_add_sync(0xffffffffu, c);
     return total >= sat;
@@ -139,42 +165,28 @@ __device__ inline bool arm_clear(const MapView& M, const ToolView& T, int g, con
   return !blocked;
 }
 
-// One corridor run: occupied (strict: or not known) anywhere in it.
-template <bool FAST>
-__device__ inline bool corridor_run_hit(const MapView& M, const ToolView& T, int r, const Pt& P) {
-  const RunEntry e = load_run<FAST>(T, r);
-  int len;
-  bool out = false;
-  bool h = run_bits<FAST>(M.occ, M, e, P, &len, &out) != 0ull;
-  if (T.strict && !h) {
-    const unsigned long long kb = run_bits<FAST>(M.known, M, e, P, &len, &out);
-    const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
-    h = out || (kb != full);
-  }
-  return h;
-}
-
 // Corridor of direction g: any occupied voxel (strict: or unknown) blocks.
-// The first warp step tests 32 runs (most blocked corridors end there); later
-// steps test 64, then 128 runs, each lane issuing its runs' loads together,
-// so a clear corridor costs fewer dependent round trips.
 template <bool FAST>
 __device__ inline bool corridor_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
                                         int lane) {
   const int4 dt = __ldg(T.dtab + g);
-  int b = dt.z, per = 1;
-  while (b < dt.w) {
+  bool blocked = false;
+  walk_runs<FAST>(T, dt.z, dt.w, lane, [&](RunEntry e, bool valid) {
     bool h = false;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int r = b + 32 * k + lane;
-      if (k < per && r < dt.w) h |= corridor_run_hit<FAST>(M, T, r, P);
+    if (valid) {
+      int len;
+      bool out = false;
+      h = run_bits<FAST>(M.occ, M.occ_y, M.occ_z, M, e, P, &len, &out) != 0ull;
+      if (T.strict && !h) {  // strict corridors run along x (the known view's rows)
+        const unsigned long long kb = run_bits<FAST>(M.known, M.known, M.known, M, e, P, &len, &out);
+        const unsigned long long full = len == 64 ? ~0ull : ((1ull << len) - 1ull);
+        h = out || (kb != full);
+      }
     }
-    if (__any_sync(0xffffffffu, h)) return true;
-    b += 32 * per;
-    per = per < 4 ? 2 * per : 4;
-  }
-  return false;
+    blocked = __any_sync(0xffffffffu, h);
+    return blocked;
+  });
+  return blocked;
 }
 
 __device__ inline bool candidate(const ToolView& T, int g, float n0, float n1, float n2) {
@@ -274,23 +286,17 @@ __device__ inline int2 best_direction_budget(const MapView& M, const ToolView& T
         return make_int2(bscore, best);
       }
       ++spent;
-      if (bscore <= nc) {
-        const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
-        if (cnt >= bscore) continue;
-        if (corridor_blocked<FAST>(M, T, g, P, lane)) continue;
-        bscore = cnt;
-        best = g;
-      } else {
-        if (corridor_blocked<FAST>(M, T, g, P, lane)) {
-          if (best < 0) {
-            bscore = nc + 1;
-            best = g;
-          }
-          continue;
+      const int sc = eval_direction<FAST>(M, T, g, P, bscore, lane);
+      if (sc < 0) continue;
+      if (sc == nc + 1) {
+        if (best < 0) {
+          bscore = nc + 1;
+          best = g;
         }
-        bscore = tool_count<FAST>(M, T, g, P, nc, lane);
-        best = g;
+        continue;
       }
+      bscore = sc;
+      best = g;
       if (bscore == 0) break;
     }
   }
