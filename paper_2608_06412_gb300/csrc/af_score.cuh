@@ -286,17 +286,23 @@ __device__ inline int2 best_direction_budget(const MapView& M, const ToolView& T
         return make_int2(bscore, best);
       }
       ++spent;
-      const int sc = eval_direction<FAST>(M, T, g, P, bscore, lane);
-      if (sc < 0) continue;
-      if (sc == nc + 1) {
-        if (best < 0) {
-          bscore = nc + 1;
-          best = g;
+      if (bscore <= nc) {
+        const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
+        if (cnt >= bscore) continue;
+        if (corridor_blocked<FAST>(M, T, g, P, lane)) continue;
+        bscore = cnt;
+        best = g;
+      } else {
+        if (corridor_blocked<FAST>(M, T, g, P, lane)) {
+          if (best < 0) {
+            bscore = nc + 1;
+            best = g;
+          }
+          continue;
         }
-        continue;
+        bscore = tool_count<FAST>(M, T, g, P, nc, lane);
+        best = g;
       }
-      bscore = sc;
-      best = g;
       if (bscore == 0) break;
     }
   }
