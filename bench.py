@@ -263,8 +263,9 @@ SCORE_BYTES_PER_POINT = 27.0
 # DRAM bytes (read + write) per launch from one ncu capture of the benchmark
 # (profiles/), valid only while the kernel's sources hash as recorded.
 TRAFFIC = {
-    "k_score": (4747093, {"paper_2608_06412_gb300/csrc/af_score.cu": "53999a238a44b5d9",
-                          "paper_2608_06412_gb300/csrc/af_internal.cuh": "fac2bd6c4e4f889d"}),
+    "k_score": (7545216, {"paper_2608_06412_gb300/csrc/af_score.cu": "782390e2ac205c07",
+                       "paper_2608_06412_gb300/csrc/af_score.cuh": "512e8110f02b4e33",
+                       "paper_2608_06412_gb300/csrc/af_internal.cuh": "82fc985526067848"}),
 }
 
 
