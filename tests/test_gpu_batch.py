@@ -37,10 +37,11 @@ def _items(S, f, empty=2, no_points=4):
 
 
 def test_batch_ticks_equal_per_scene_path(scenes):
+    """Odd scenes use the [-tau, tau] clamp, so one batch mixes both clamps."""
     import torch
     S = scenes
-    plain = [af.Map(W.af_config(**CAPS)) for W in S]
-    mapsb = [af.Map(W.af_config(**CAPS)) for W in S]
+    plain = [af.Map(W.af_config(clamp_signed=s % 2, **CAPS)) for s, W in enumerate(S)]
+    mapsb = [af.Map(W.af_config(clamp_signed=s % 2, **CAPS)) for s, W in enumerate(S)]
     for W, a, b in zip(S, plain, mapsb):
         a.set_tool(W.af_tool(), W.dirs)
         b.set_tool(W.af_tool(), W.dirs)
@@ -63,6 +64,7 @@ def test_batch_ticks_equal_per_scene_path(scenes):
         va, vb = gpu_voxels(a), gpu_voxels(b)
         for k in va:
             np.testing.assert_array_equal(va[k], vb[k], f"scene {s} field {k}")
+        assert ((va["S"] < 0).any() == bool(s % 2)) or len(va["S"]) == 0
         assert a.stats()["tests"] == b.stats()["tests"]
         assert a.stats()["returns_accepted"] == b.stats()["returns_accepted"]
     t = batch.tuning()
