@@ -59,11 +59,13 @@ def _args():
     ap.add_argument("--score-split", type=int, default=None,
                     help="af_set_score_split budget (-1: one warp per point; default: library's)")
     ap.add_argument("--ring", action="store_true",
-                    help="--points: the paper's approach set, 180 yaw directions and a 70 degree cone")
+                    help="the paper's approach set, 180 yaw directions and a 70 degree cone")
+    ap.add_argument("--projective", action="store_true",
+                    help="projective integration over an octahedral range image (Tab. 3 ablation)")
     ap.add_argument("--c2f", action="store_true",
                     help="--points --ring: coarse-to-fine search (20 degrees, +-24 degrees, 0.3 m)")
     ap.add_argument("--clamp-signed", action="store_true",
-                    help="--points: the [-tau, tau] clamp ablation (Tab. 4)")
+                    help="the [-tau, tau] clamp ablation (Tab. 4)")
     return ap.parse_args()
 
 
@@ -245,16 +247,17 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def score_bytes_per_test(W) -> float:
+def score_bytes_per_test(W, tool=None, dirs=None) -> float:
     """Algorithmic bytes of one point x orientation test: the occupied and
     known bits (2 bits per voxel) of every voxel the test's tool kernel,
     corridor kernel and three arm samples cover, with no early exit; the
     mean over the direction table."""
     from paper_2608_06412_gb300 import af
-    t = W.af_tool()
+    t = W.af_tool() if tool is None else tool
     v = W.params["v"]
     vox = [len(af.kernel_offsets(t, v, u, af.KERNEL_TOOL)) +
-           len(af.kernel_offsets(t, v, u, af.KERNEL_CORRIDOR)) + 3 for u in W.dirs]
+           len(af.kernel_offsets(t, v, u, af.KERNEL_CORRIDOR)) + 3
+           for u in (W.dirs if dirs is None else dirs)]
     return 2.0 * float(np.mean(vox)) / 8.0
 
 # per scored point: 24 B of point + normal in, 3 B of label + best out
@@ -308,7 +311,18 @@ def run_ours(args, W, ws, rank, local):
     nfr = args.warmup + args.steps
     frames = _frames(W, 0, nfr)
     from paper_2608_06412_gb300.workload import BENCH_CAPS
-    caps = dict(BENCH_CAPS)
+    from paper_2608_06412_gb300 import synth
+    caps = dict(BENCH_CAPS, clamp_signed=int(args.clamp_signed))
+    tool, dirs = W.af_tool(), W.dirs
+    if args.ring:   # the paper's approach set: 180 yaw directions, 70 degree cone
+        tool.cos_theta_max = synth.COS_70
+        dirs = synth.yaw_ring(180)
+
+    def integrate(g, k):
+        if args.projective:
+            g.integrate_scan_projective(d_xyz[k], frames[k][0].pose, 812)
+        else:
+            g.integrate_scan(d_xyz[k], frames[k][0].pose)
 
     d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
     d_pts = [torch.from_numpy(f[1]).to(dev) for f in frames]
@@ -325,11 +339,11 @@ def run_ours(args, W, ws, rank, local):
 
     def pass_device(profile: bool, clocks: Clocks | None):
         g = af.Map(W.af_config(**caps))
-        g.set_tool(W.af_tool(), W.dirs)
+        g.set_tool(tool, dirs)
         if args.score_split is not None:
             g.set_score_split(args.score_split)
         for k in range(args.warmup):
-            g.integrate_scan(d_xyz[k], frames[k][0].pose)
+            integrate(g, k)
             m = len(d_pts[k])
             g.score(d_pts[k], d_nrm[k], lab[:m], best[:m])
         torch.cuda.synchronize()
@@ -346,7 +360,7 @@ def run_ours(args, W, ws, rank, local):
         for i, k in enumerate(range(args.warmup, nfr)):
             flush.zero_()
             ev[i][0].record(stream)
-            g.integrate_scan(d_xyz[k], frames[k][0].pose)
+            integrate(g, k)
             m = len(d_pts[k])
             g.score(d_pts[k], d_nrm[k], lab[:m], best[:m])
             ev[i][1].record(stream)
@@ -372,7 +386,7 @@ def run_ours(args, W, ws, rank, local):
 
     # e2e through af_frame_host with pinned host buffers (pass C)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.projective and not args.ring and not args.clamp_signed:
         g = af.Map(W.af_config(**caps))
         g.set_tool(W.af_tool(), W.dirs)
         if args.score_split is not None:
@@ -432,7 +446,7 @@ def run_ours(args, W, ws, rank, local):
             "kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
             "kernel_share": {k: round(v / max(sum(kt.values()), 1e-9), 4) for k, v in kt.items()}}
     if dom == "k_score":
-        bpt = score_bytes_per_test(W)
+        bpt = score_bytes_per_test(W, tool, dirs)
         tests_l = (sB1["tests"] - sB0["tests"]) / max(n_launch, 1)
         pts_l = (sB1["points_scored"] - sB0["points_scored"]) / max(n_launch, 1)
         alg = bpt * tests_l + SCORE_BYTES_PER_POINT * pts_l
@@ -449,9 +463,13 @@ def run_ours(args, W, ws, rank, local):
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
         "config": {"workload": W.name, "returns_per_frame": W.params["n_returns"],
-                   "K": W.params["K"], "G": len(W.dirs), "voxel_m": W.params["v"],
+                   "K": W.params["K"], "G": len(dirs), "voxel_m": W.params["v"],
                    "frames": f"{args.warmup}..{nfr - 1}",
                    "score_split": args.score_split if args.score_split is not None else "default",
+                   "integration": "projective (812^2 octahedral cells)" if args.projective
+                   else "scan-centric",
+                   "clamp": "[-tau, tau]" if args.clamp_signed else "[0, tau]",
+                   "directions": "yaw ring, 70 deg cone" if args.ring else "Fibonacci sphere",
                    "l2": "flushed between steps (256 MiB write)"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                        "max": float(max(ms))},
@@ -858,7 +876,8 @@ def main():
     else:
         out = run_ours(args, W, ws, rank, local)
         frames = out.pop("_frames")
-        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        variant = args.projective or args.ring or args.clamp_signed
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline and not variant:
             out["cpu_baseline"] = cpu_baseline(W, frames)
         if rank != 0:
             out = None

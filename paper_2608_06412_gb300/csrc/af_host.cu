@@ -21,6 +21,9 @@ cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const
 cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], const float4* d_ret,
                         uint32_t frame, cudaStream_t stream);
 cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream);
+cudaError_t launch_projective(const MapView& M, const float* d_xyz, uint32_t n,
+                              const float pose[16], const float4* d_ret, unsigned* d_img,
+                              uint32_t bins, int num_sms, cudaStream_t s);
 cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts,
                          const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
                          const ScoreSplit& S, int num_sms, cudaStream_t stream);
@@ -458,6 +461,44 @@ extern "C" af_status af_integrate_scan(af_ctx* ctx, const float* d_xyz, uint32_t
   AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, ctx->frame, s); }));
   if (n > 0)
     AF_CUDA(ctx, timed(ctx, 1, s, [&] { return af::launch_cube(M, n, pose, ctx->d_ret, ctx->frame, s); }));
+  AF_CUDA(ctx, timed(ctx, 2, s, [&] { return af::launch_bitview(M, ctx->num_sms, s); }));
+  ctx->last_stream = s;
+  ctx->scans++;
+  ctx->returns_in += n;
+  return AF_OK;
+}
+
+// Projective integration (the ablation of Tab. 3): the scan-centric
+// allocation without band bricks, the range-image update (af_projective.cu),
+// then the weight cap and bit view. Profiling slots as af_integrate_scan.
+extern "C" af_status af_integrate_scan_projective(af_ctx* ctx, const float* d_xyz, uint32_t n,
+                                                  const float pose[16], uint32_t bins,
+                                                  void* stream) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_integrate_scan_projective: NULL context");
+  if (!pose) return fail(ctx, AF_ERR_INVALID_ARG, "af_integrate_scan_projective: NULL pose");
+  if (n > 0 && !d_xyz) return fail(ctx, AF_ERR_INVALID_ARG, "af_integrate_scan_projective: NULL points");
+  if (n > ctx->cfg.max_returns)
+    return fail(ctx, AF_ERR_CAPACITY, "af_integrate_scan_projective: n exceeds max_returns");
+  if (bins < 2 || bins > 8192)
+    return fail(ctx, AF_ERR_INVALID_ARG, "af_integrate_scan_projective: bins must be in 2..8192");
+  for (int k = 0; k < 12; ++k)
+    if (!std::isfinite(pose[k])) return fail(ctx, AF_ERR_INVALID_ARG, "non-finite pose");
+  const size_t cells = (size_t)bins * bins;
+  if (cells > ctx->img_cap) {
+    cudaFree(ctx->d_img);
+    ctx->d_img = nullptr;
+    ctx->img_cap = 0;
+    AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_img, cells * sizeof(unsigned)));
+    ctx->img_cap = cells;
+  }
+  ctx->frame = ctx->frame + 1 >= 0xFFFFFFFFu ? 1 : ctx->frame + 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  af::MapView M = ctx->M;
+  M.ns = 0;  // no cleared band: the projective update has none
+  AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, ctx->frame, s); }));
+  AF_CUDA(ctx, timed(ctx, 1, s, [&] {
+            return af::launch_projective(M, d_xyz, n, pose, ctx->d_ret, ctx->d_img, bins, ctx->num_sms, s);
+          }, n > 0 ? 2 : 1));
   AF_CUDA(ctx, timed(ctx, 2, s, [&] { return af::launch_bitview(M, ctx->num_sms, s); }));
   ctx->last_stream = s;
   ctx->scans++;

@@ -4,7 +4,8 @@
 // range image instead of being updated from the returns around them.
 //
 // Per scan, on the caller's stream:
-//  k_alloc        (the scan-centric allocation, without cleared-band bricks)
+//  k_alloc        (the scan-centric allocation, without cleared-band bricks;
+//                 launched by af_integrate_scan_projective in af_host.cu)
 //                 bricks overlapped by the cubes of the accepted returns,
 //                 listed once each in the map's dirty list
 //  k_proj_image   one thread per return: the nearest range in each cell of
@@ -21,16 +22,11 @@
 #include <af.h>
 
 #include <cmath>
-#include <cstdio>
 
 #include "af_ctx.cuh"
 #include "af_internal.cuh"
 
 namespace af {
-cudaError_t launch_alloc(const MapView& M, const float* d_xyz, uint32_t n, const float pose[16],
-                         float4* d_ret, uint32_t frame, cudaStream_t stream);
-cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream);
-
 namespace {
 
 constexpr unsigned kEmptyCell = 0xFFFFFFFFu;
@@ -106,55 +102,24 @@ __global__ void __launch_bounds__(512) k_proj_update(MapView M, Pose P,
 }  // namespace
 }  // namespace af
 
-extern "C" af_status af_integrate_scan_projective(af_ctx* ctx, const float* d_xyz, uint32_t n,
-                                                  const float pose[16], uint32_t bins,
-                                                  void* stream) {
-  if (!ctx) return AF_ERR_INVALID_ARG;
-  auto bad = [&](af_status s, const char* msg) {
-    std::snprintf(ctx->err, sizeof ctx->err, "af_integrate_scan_projective: %s", msg);
-    return s;
-  };
-  if (!pose) return bad(AF_ERR_INVALID_ARG, "NULL pose");
-  if (n > 0 && !d_xyz) return bad(AF_ERR_INVALID_ARG, "NULL points");
-  if (n > ctx->cfg.max_returns) return bad(AF_ERR_CAPACITY, "n exceeds max_returns");
-  if (bins < 2 || bins > 8192) return bad(AF_ERR_INVALID_ARG, "bins must be in 2..8192");
-  for (int k = 0; k < 12; ++k)
-    if (!std::isfinite(pose[k])) return bad(AF_ERR_INVALID_ARG, "non-finite pose");
-  const size_t cells = (size_t)bins * bins;
-  if (cells > ctx->img_cap) {
-    cudaFree(ctx->d_img);
-    ctx->d_img = nullptr;
-    ctx->img_cap = 0;
-    if (cudaMalloc((void**)&ctx->d_img, cells * sizeof(unsigned)) != cudaSuccess)
-      return bad(AF_ERR_CUDA, "range image allocation failed");
-    ctx->img_cap = cells;
-  }
-  ctx->frame = ctx->frame + 1 >= 0xFFFFFFFFu ? 1 : ctx->frame + 1;
-  cudaStream_t s = (cudaStream_t)stream;
-  af::MapView M = ctx->M;
-  M.ns = 0;  // no cleared band: the projective update has none
-  af::Pose P;
+namespace af {
+
+// The projective update of one scan (the range image, then every voxel of
+// the scan's bricks); the allocation and the bit view are launched by the
+// caller around it.
+cudaError_t launch_projective(const MapView& M, const float* d_xyz, uint32_t n,
+                              const float pose[16], const float4* d_ret, unsigned* d_img,
+                              uint32_t bins, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_img, 0xFF, (size_t)bins * bins * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  if (n > 0)
+    k_proj_image<<<(n + 255) / 256, 256, 0, s>>>(d_xyz, d_ret, n, pose[3], pose[7], pose[11], d_img,
+                                                 (int)bins);
+  Pose P;
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 4; ++c) P.r[r][c] = pose[4 * r + c];
-  cudaError_t e = af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, ctx->frame, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_img, 0xFF, cells * sizeof(unsigned), s);
-  if (e == cudaSuccess && n > 0) {
-    af::k_proj_image<<<(n + 255) / 256, 256, 0, s>>>(d_xyz, ctx->d_ret, n, pose[3], pose[7],
-                                                      pose[11], ctx->d_img, (int)bins);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) {
-    af::k_proj_update<<<ctx->num_sms * 4, 512, 0, s>>>(M, P, ctx->d_img, (int)bins);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = af::launch_bitview(M, ctx->num_sms, s);
-  if (e != cudaSuccess) {
-    std::snprintf(ctx->err, sizeof ctx->err, "af_integrate_scan_projective: %s",
-                  cudaGetErrorString(e));
-    return AF_ERR_CUDA;
-  }
-  ctx->last_stream = s;
-  ctx->scans++;
-  ctx->returns_in += n;
-  return AF_OK;
+  k_proj_update<<<num_sms * 4, 512, 0, s>>>(M, P, d_img, (int)bins);
+  return cudaGetLastError();
 }
+
+}  // namespace af
