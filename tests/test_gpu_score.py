@@ -168,3 +168,23 @@ def test_work_sharing_grows_past_max_points(single, oracle_single):
     with pytest.raises(af.AfError) as e:
         g.set_score_split(-2)
     assert e.value.status == af.ERR_INVALID_ARG
+
+
+def test_work_sharing_pine_frames():
+    """The hand-off (budget 4) on pine-stream frames, whose points are heavier
+    and more uneven than the single frame's: labels and directions equal the
+    single-pass search on the same map."""
+    import torch
+    W = workload.pine_stream()
+    g = gpu_map(W, hash_capacity=1 << 18, pool_blocks=1 << 16, max_returns=1 << 15)
+    g.set_tool(W.af_tool(), W.dirs)
+    for f in range(12):
+        fr, pts, nrm = workload.pine_frame(W, f)
+        g.integrate_scan(to_dev(fr.pts), fr.pose)
+    g.set_score_split(-1)
+    a = _gpu_score(g, pts, nrm)
+    g.set_score_split(4)
+    b = _gpu_score(g, pts, nrm)
+    g.set_score_split(-1)
+    _compare(*b, *a)
+    assert (a[0] == af.ACCESSIBLE).sum() > 100 and (a[0] == af.BLOCKED).sum() > 100
