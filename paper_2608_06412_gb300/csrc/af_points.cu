@@ -82,43 +82,46 @@ __device__ inline bool return_voxel(const MapView& M, const float4* ret, uint32_
   return true;
 }
 
+// One thread per (return, brick of its cube): the brick is stamped as
+// changed; the thread whose brick holds the return also claims its voxel as
+// a new point if it has none.
 __global__ void __launch_bounds__(256) k_pts_mark(MapView M, const float4* __restrict__ ret,
                                                   uint32_t n, PtView V, uint32_t frame) {
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ba = (2 * M.m + 7) / 8 + 1;  // bricks a cube edge can span
+  const int per = ba * ba * ba;
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t k = e / per;
+  const int j = (int)(e % per);
   if (k >= n) return;
   int r[3];
   if (!return_voxel(M, ret, k, r)) return;
-  const uint32_t blk = lookup_brick(M, pack_brick(r[0] >> 3, r[1] >> 3, r[2] >> 3));
-  if (blk != kNoBlock) {
-    int32_t* slot = V.pid + (size_t)blk * kBrickVox + vox_slot(r[0], r[1], r[2]);
+  // brick j of the cube (inside the box for an accepted return)
+  const int bx = ((r[0] - M.m) >> 3) + j % ba, by = ((r[1] - M.m) >> 3) + (j / ba) % ba,
+            bz = ((r[2] - M.m) >> 3) + j / (ba * ba);
+  if (bx > (r[0] + M.m) >> 3 || by > (r[1] + M.m) >> 3 || bz > (r[2] + M.m) >> 3) return;
+  const uint32_t b = lookup_brick(M, pack_brick(bx, by, bz));
+  if (b == kNoBlock) return;
+  if (atomicExch(V.chg + b, frame) != frame) V.chglist[atomicAdd(&V.C->nchg, 1u)] = b;
+  if (bx == r[0] >> 3 && by == r[1] >> 3 && bz == r[2] >> 3) {
+    int32_t* slot = V.pid + (size_t)b * kBrickVox + vox_slot(r[0], r[1], r[2]);
     if (*slot == -1 && atomicCAS(slot, -1, -2) == -1)
       V.newkeys[atomicAdd(&V.C->nnew, 1u)] = rel_key(r[0], r[1], r[2]);
   }
-  // bricks overlapped by the return's cube (inside the box for an accepted return)
-  for (int bz = (r[2] - M.m) >> 3; bz <= (r[2] + M.m) >> 3; ++bz)
-    for (int by = (r[1] - M.m) >> 3; by <= (r[1] + M.m) >> 3; ++by)
-      for (int bx = (r[0] - M.m) >> 3; bx <= (r[0] + M.m) >> 3; ++bx) {
-        const uint32_t b = lookup_brick(M, pack_brick(bx, by, bz));
-        if (b != kNoBlock && atomicExch(V.chg + b, frame) != frame)
-          V.chglist[atomicAdd(&V.C->nchg, 1u)] = b;
-      }
 }
 
+// One thread per (changed brick, neighbour of its 3 x 3 x 3 block).
 __global__ void __launch_bounds__(256) k_pts_near(MapView M, PtView V, uint32_t frame) {
-  const uint32_t count = V.C->nchg;
+  const uint32_t count = V.C->nchg * 27u;
   const int BX = M.dim_vox[0] >> 3, BY = M.dim_vox[1] >> 3, BZ = M.dim_vox[2] >> 3;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const uint64_t key = M.bkey[V.chglist[i]];
-    const int bx = (int)(key & 0x1FFFFF), by = (int)((key >> 21) & 0x1FFFFF), bz = (int)(key >> 42);
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x = bx + dx, y = by + dy, z = bz + dz;
-          if ((unsigned)x >= (unsigned)BX || (unsigned)y >= (unsigned)BY || (unsigned)z >= (unsigned)BZ)
-            continue;
-          const uint32_t b = lookup_brick(M, pack_brick(x, y, z));
-          if (b != kNoBlock) V.near[b] = frame;
-        }
+    const uint64_t key = M.bkey[V.chglist[i / 27u]];
+    const int o = (int)(i % 27u);
+    const int x = (int)(key & 0x1FFFFF) + o % 3 - 1, y = (int)((key >> 21) & 0x1FFFFF) + (o / 3) % 3 - 1,
+              z = (int)(key >> 42) + o / 9 - 1;
+    if ((unsigned)x >= (unsigned)BX || (unsigned)y >= (unsigned)BY || (unsigned)z >= (unsigned)BZ)
+      continue;
+    const uint32_t b = lookup_brick(M, pack_brick(x, y, z));
+    if (b != kNoBlock) V.near[b] = frame;
   }
 }
 
@@ -781,8 +784,12 @@ extern "C" af_status af_points_frame(af_ctx* ctx, const float* d_xyz, uint32_t n
   const af::PtView V = af::pt_view(ctx);
   const uint32_t frame = ctx->frame;
   PT_CUDA(ctx, cudaMemsetAsync(&ctx->d_pcount->nnew, 0, 2 * sizeof(uint32_t), s));  // nnew, nchg
-  if (n > 0) af::k_pts_mark<<<(n + 255) / 256, 256, 0, s>>>(M, ctx->d_ret, n, V, frame);
-  af::k_pts_near<<<af::grid_cap(M.pool_blocks, 256, ctx->num_sms, 4), 256, 0, s>>>(M, V, frame);
+  if (n > 0) {
+    const int ba = (2 * M.m + 7) / 8 + 1;
+    const uint64_t threads = (uint64_t)n * (uint64_t)(ba * ba * ba);
+    af::k_pts_mark<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(M, ctx->d_ret, n, V, frame);
+  }
+  af::k_pts_near<<<af::grid_cap((size_t)M.pool_blocks * 27, 256, ctx->num_sms, 8), 256, 0, s>>>(M, V, frame);
   af::k_pts_create<<<af::grid_cap(ctx->cfg.max_returns, 256, ctx->num_sms, 8), 256, 0, s>>>(M, V);
   af::k_pts_commit<<<1, 1, 0, s>>>(V);
   const float q[3] = {pose[3], pose[7], pose[11]};
