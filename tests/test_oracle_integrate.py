@@ -94,6 +94,10 @@ def test_concentric_sphere_tsdf_is_signed_distance():
     got = e["S"][has].astype(np.float64) / e["w"][has] / 2.0 ** 20
     # quantisation 2^-21 m plus single-precision range rounding
     assert np.max(np.abs(got - sdf)) < 1e-5
+    # round(d 2^20) rounds to nearest: over the unclamped voxels the error has
+    # no bias (rounding down would shift its mean by -2^-21 m = -4.8e-7 m)
+    inner = (sdf > 1e-4) & (sdf < tau - 1e-4)
+    assert inner.sum() > 10000 and abs(np.mean(got[inner] - sdf[inner])) < 1.2e-7
     # both clamp ends are reached, so the test covers the clamp
     assert (sdf == 0).sum() > 100 and (sdf == tau).sum() > 100
 
