@@ -362,3 +362,21 @@ def test_projective_erodes_thin_structures():
 
     sc, pj = pole_occ(a), pole_occ(b)
     assert sc > 50 and pj < 0.5 * sc, (sc, pj)
+
+
+def test_projective_cell_keeps_the_nearest_range():
+    """Two returns along one ray (the same cell) at 1.0 and 1.6 m: the cell
+    holds the nearer range, so the voxel holding the near return reads the
+    surface (occupied, |TSDF| < v) and the voxel holding the far one, 0.6 m
+    behind it, lies beyond the truncation and is not updated."""
+    v, tau = 0.02, 0.06
+    u = np.array([0.8, 0.36, 0.48])
+    u /= np.linalg.norm(u)
+    ps = np.array([1.0 * u, 1.6 * u], np.float32)
+    mp = oracle.Map(_cfg(v, tau, 3, 8))
+    assert mp.integrate_projective(ps, _pose([0.0, 0.0, 0.0]), 64) == 2
+    near = tuple(int(x) for x in np.floor(ps[0] / np.float32(v)))
+    far = tuple(int(x) for x in np.floor(ps[1] / np.float32(v)))
+    S, w, _ = mp.voxel(*near)
+    assert w == 1 and mp.occ(*near) and abs(S / 2.0 ** 20) < v
+    assert mp.voxel(*far)[1] == 0
