@@ -316,34 +316,37 @@ __device__ inline float trilinear(const float4& lo, const float4& hi, const floa
   return __fmaf_rn(f[2], b1 - b0, b0);
 }
 
-// Records in flight per lane: the lane computes kInFlight sample cells,
-// issues their loads, then folds them into the softmin in sample order.
-constexpr int kInFlight = 2;
+// Records in flight per lane (NF): the lane computes NF sample cells, issues
+// their loads, then folds them into the softmin in sample order, so the
+// result does not depend on NF. The field takes 3, the refinement 4
+// (measured best; more in flight trade registers for memory parallelism).
+constexpr int kInFlightField = 3;
+constexpr int kInFlightRefine = 4;
 
 // C of one pair and, with GRAD, dC / d(alpha, beta, h); *cmin = min_j phi_j.
 // Called by all kLanes lanes of the pair's group (lane g of it); with
 // `live` false the lane samples nothing.
-template <bool GRAD, bool FIXED>
+template <bool GRAD, bool FIXED, int NF>
 __device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const Dir& d,
                                   const float t1[3], const float t2[3], bool live, int g,
                                   float* ga, float* gb, float* gh, float* cmin) {
   Softmin<GRAD, FIXED> sm;
   if (live) {
-    for (int j = S.j0 + g; j <= S.J; j += kInFlight * kLanes) {
-      float f[kInFlight][3];
-      uint32_t id[kInFlight];
-      bool has[kInFlight], in[kInFlight];
+    for (int j = S.j0 + g; j <= S.J; j += NF * kLanes) {
+      float f[NF][3];
+      uint32_t id[NF];
+      bool has[NF], in[NF];
 #pragma unroll
-      for (int q = 0; q < kInFlight; ++q) {
+      for (int q = 0; q < NF; ++q) {
         has[q] = j + q * kLanes <= S.J;
         in[q] = has[q] && sample_cell(S, pc, d, j + q * kLanes, f[q], &id[q]);
       }
-      float4 lo[kInFlight], hi[kInFlight];
+      float4 lo[NF], hi[NF];
 #pragma unroll
-      for (int q = 0; q < kInFlight; ++q)
+      for (int q = 0; q < NF; ++q)
         if (in[q]) load_cell(S, id[q], lo[q], hi[q]);
 #pragma unroll
-      for (int q = 0; q < kInFlight; ++q) {
+      for (int q = 0; q < NF; ++q) {
         if (!has[q]) break;
         const int jq = j + q * kLanes;
         float G[3] = {0.f, 0.f, 0.f};
@@ -435,7 +438,8 @@ __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restric
     const Dir d = make_dir(S, u, t1, t2, __ldg(alpha + i), __ldg(beta + i), __ldg(hh + i));
     const bool fin = pc.finite && d.finite;
     float da, db, dh, mn;
-    float C = soft_eval<GRAD, FIXED>(S, pc, d, t1, t2, fin && act, w.g, &da, &db, &dh, &mn);
+    float C = soft_eval<GRAD, FIXED, kInFlightField>(S, pc, d, t1, t2, fin && act, w.g, &da, &db,
+                                                     &dh, &mn);
     if (!act || w.g != 0) continue;
     if (!fin) C = mn = da = db = dh = NAN;
     if (c) c[i] = C;
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
       const Dir d = make_dir(S, u, t1, t2, al, be, h);
       const bool live = fin && act && d.finite;
       float da, db, dh, mn;
-      soft_eval<true, FIXED>(S, pc, d, t1, t2, live, w.g, &da, &db, &dh, &mn);
+      soft_eval<true, FIXED, kInFlightRefine>(S, pc, d, t1, t2, live, w.g, &da, &db, &dh, &mn);
       if (live) {
         al = __fmaf_rn(R.lr_dir, da, al);
         be = __fmaf_rn(R.lr_dir, db, be);
@@ -488,7 +492,8 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
     const Dir d = make_dir(S, u, t1, t2, al, be, h);
     const bool ok = fin && d.finite;
     float mn;
-    float C = soft_eval<false, FIXED>(S, pc, d, t1, t2, ok && act, w.g, nullptr, nullptr, nullptr,
+    float C = soft_eval<false, FIXED, kInFlightRefine>(S, pc, d, t1, t2, ok && act, w.g, nullptr,
+                                                        nullptr, nullptr,
                                       &mn);
     if (!act || w.g != 0) continue;
     if (!ok) C = mn = al = be = h = NAN;
