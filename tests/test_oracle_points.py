@@ -415,6 +415,22 @@ def test_coarse_to_fine_search_brute_force():
     assert checked > 1000
     labels = after["label"]
     assert (labels == oracle.ACCESSIBLE).sum() > 50 and (labels == oracle.BLOCKED).sum() > 50
+    # a second frame re-queues resolved points: their centre comes from another
+    # point (never their own stored direction), and the stored score only
+    # decreases (a strictly lower score replaces it, with its direction)
+    pts, pose = _frame(_slotted_scene(), (0.0, 0.03, 0.0), n=6000, seed=1)
+    P.frame(pts, pose)
+    before = P.export()
+    P.drain(10 ** 9)
+    after = P.export()
+    n0 = len(before["score"])
+    again = np.flatnonzero((before["score"][:n0] >= 0) & (before["queued"][:n0] == 1))
+    assert len(again) > 500
+    exp = _c2f_expected(mp, tool, dirs, after, again, before["best"], 10, 12, 0.3)
+    for i, (s, g) in zip(again, exp):
+        old = (int(before["score"][i]), int(before["best"][i]))
+        want = (int(s), int(g)) if s < old[0] else old
+        assert (int(after["score"][i]), int(after["best"][i])) == want, i
 
 
 @pytest.mark.parametrize("stride,half", [(1, 0), (10, 90)])
