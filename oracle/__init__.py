@@ -106,6 +106,10 @@ def _load():
         lib.or_arm_offsets.argtypes = [C.c_float, C.c_float, P, P]
         lib.or_score.argtypes = [P, C.POINTER(_Tool), P, C.c_int32, P, P, C.c_int64,
                                  P, P, P]
+        lib.or_tables_new.restype = P
+        lib.or_tables_new.argtypes = [C.POINTER(_Tool), C.c_float, C.c_float, P, C.c_int32]
+        lib.or_tables_free.argtypes = [P]
+        lib.or_score_tables.argtypes = [P, P, P, P, C.c_int64, P, P, P]
         lib.or_soft_clearance.argtypes = [P, C.POINTER(_Tool), P, C.c_uint32, P, P, P, P,
                                           C.c_int64, C.c_double, C.c_int, P, P, P, P, P]
         lib.or_soft_seed.argtypes = [P, C.c_int64, P, C.c_int32, P]
@@ -271,6 +275,20 @@ class Map:
                            _ptr(label), _ptr(best), _ptr(ds) if ds is not None else None)
         return (label, best, ds) if dir_scores else (label, best)
 
+    def score_tables(self, tables: "ScoreTables", pts: np.ndarray, normals: np.ndarray,
+                     dir_scores: bool = False):
+        """Map.score with kernel tables built once (or_score_tables)."""
+        if (tables.cfg.v, tables.cfg.tau) != (self.cfg.v, self.cfg.tau):
+            raise ValueError("tables were built for another voxel size or truncation")
+        pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
+        normals = np.ascontiguousarray(normals, np.float32).reshape(-1, 3)
+        m, G = len(pts), len(tables.dirs)
+        label = np.zeros(m, np.uint8)
+        best = np.zeros(m, np.int16)
+        ds = np.zeros((m, G), np.int32) if dir_scores else None
+        self._lib.or_score_tables(self._h, tables._h, _ptr(pts), _ptr(normals), m, _ptr(label),
+                                  _ptr(best), _ptr(ds) if ds is not None else None)
+        return (label, best, ds) if dir_scores else (label, best)
 
     def soft_clearance(self, tool: Tool, pts: np.ndarray, per_point: int, u0: np.ndarray,
                        alpha: np.ndarray, beta: np.ndarray, h: np.ndarray,
@@ -338,6 +356,24 @@ def arm_offsets(v: float, tau: float, u) -> np.ndarray:
     out = np.zeros((3, 3), np.int32)
     lib.or_arm_offsets(C.c_float(v), C.c_float(tau), _ptr(u), _ptr(out))
     return out
+
+
+class ScoreTables:
+    """The kernel tables of one tool over a direction set, built once for a
+    voxel size and truncation (Sec. 3.6: precomputed at initialisation)."""
+
+    def __init__(self, cfg: Config, tool: Tool, dirs: np.ndarray):
+        self._lib = _load()
+        self.cfg = cfg
+        self.dirs = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+        self._tc = tool._c()
+        self._h = self._lib.or_tables_new(C.byref(self._tc), cfg.v, cfg.tau, _ptr(self.dirs),
+                                          len(self.dirs))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.or_tables_free(self._h)
+            self._h = None
 
 
 @dataclass

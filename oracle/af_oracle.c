@@ -542,29 +542,76 @@ void or_arm_offsets(float v, float tau, const float u[3], int32_t out[9]) {
 /* Accessibility scoring (Sec. 3.4, 3.5).                                    */
 /* ------------------------------------------------------------------------- */
 
+struct or_tables {
+    or_tool t;
+    float v, tau;
+    int32_t G;
+    float *dirs;
+    int32_t **tool, **corr;
+    int64_t *ntool, *ncorr;
+    int32_t *arm;
+};
+
+/* Precomputed kernels, one per direction, no run-time rotation (Sec. 3.6). */
+or_tables *or_tables_new(const or_tool *t, float v, float tau, const float *dirs, int32_t G) {
+    or_tables *T = (or_tables *)calloc(1, sizeof(or_tables));
+    T->t = *t;
+    T->v = v;
+    T->tau = tau;
+    T->G = G;
+    T->dirs = (float *)malloc(sizeof(float) * 3 * (size_t)(G > 0 ? G : 1));
+    memcpy(T->dirs, dirs, sizeof(float) * 3 * (size_t)G);
+    T->tool = (int32_t **)calloc((size_t)G, sizeof(int32_t *));
+    T->corr = (int32_t **)calloc((size_t)G, sizeof(int32_t *));
+    T->ntool = (int64_t *)calloc((size_t)G, sizeof(int64_t));
+    T->ncorr = (int64_t *)calloc((size_t)G, sizeof(int64_t));
+    T->arm = (int32_t *)calloc((size_t)G * 9, sizeof(int32_t));
+    for (int32_t g = 0; g < G; ++g) {
+        const float *u = dirs + 3 * g;
+        T->ntool[g] = or_kernel_offsets(t, v, u, OR_KERNEL_TOOL, NULL, 0);
+        T->tool[g] = (int32_t *)malloc((size_t)(3 * T->ntool[g] + 1) * sizeof(int32_t));
+        or_kernel_offsets(t, v, u, OR_KERNEL_TOOL, T->tool[g], T->ntool[g]);
+        T->ncorr[g] = or_kernel_offsets(t, v, u, OR_KERNEL_CORRIDOR, NULL, 0);
+        T->corr[g] = (int32_t *)malloc((size_t)(3 * T->ncorr[g] + 1) * sizeof(int32_t));
+        or_kernel_offsets(t, v, u, OR_KERNEL_CORRIDOR, T->corr[g], T->ncorr[g]);
+        or_arm_offsets(v, tau, u, T->arm + 9 * g);
+    }
+    return T;
+}
+
+void or_tables_free(or_tables *T) {
+    if (!T) return;
+    for (int32_t g = 0; g < T->G; ++g) {
+        free(T->tool[g]);
+        free(T->corr[g]);
+    }
+    free(T->tool);
+    free(T->corr);
+    free(T->ntool);
+    free(T->ncorr);
+    free(T->arm);
+    free(T->dirs);
+    free(T);
+}
+
 void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G, const float *pts,
               const float *normals, int64_t npts, uint8_t *label, int16_t *best,
               int32_t *dir_score) {
+    or_tables *T = or_tables_new(t, m->cfg.v, m->cfg.tau, dirs, G);
+    or_score_tables(m, T, pts, normals, npts, label, best, dir_score);
+    or_tables_free(T);
+}
+
+void or_score_tables(const or_map *m, const or_tables *T, const float *pts, const float *normals,
+                     int64_t npts, uint8_t *label, int16_t *best, int32_t *dir_score) {
     const or_config *c = &m->cfg;
     const float v = c->v;
-    const int32_t n_c = (int32_t)t->n_c;
-
-    /* Precomputed kernels, one per direction, no run-time rotation (Sec. 3.6). */
-    int32_t **tool = (int32_t **)calloc((size_t)G, sizeof(int32_t *));
-    int32_t **corr = (int32_t **)calloc((size_t)G, sizeof(int32_t *));
-    int64_t *ntool = (int64_t *)calloc((size_t)G, sizeof(int64_t));
-    int64_t *ncorr = (int64_t *)calloc((size_t)G, sizeof(int64_t));
-    int32_t *arm = (int32_t *)calloc((size_t)G * 9, sizeof(int32_t));
-    for (int32_t g = 0; g < G; ++g) {
-        const float *u = dirs + 3 * g;
-        ntool[g] = or_kernel_offsets(t, v, u, OR_KERNEL_TOOL, NULL, 0);
-        tool[g] = (int32_t *)malloc((size_t)(3 * ntool[g] + 1) * sizeof(int32_t));
-        or_kernel_offsets(t, v, u, OR_KERNEL_TOOL, tool[g], ntool[g]);
-        ncorr[g] = or_kernel_offsets(t, v, u, OR_KERNEL_CORRIDOR, NULL, 0);
-        corr[g] = (int32_t *)malloc((size_t)(3 * ncorr[g] + 1) * sizeof(int32_t));
-        or_kernel_offsets(t, v, u, OR_KERNEL_CORRIDOR, corr[g], ncorr[g]);
-        or_arm_offsets(v, c->tau, u, arm + 9 * g);
-    }
+    const or_tool *t = &T->t;
+    const int32_t n_c = (int32_t)t->n_c, G = T->G;
+    const float *dirs = T->dirs;
+    int32_t *const *tool = T->tool, *const *corr = T->corr;
+    const int64_t *ntool = T->ntool, *ncorr = T->ncorr;
+    const int32_t *arm = T->arm;
 
     for (int64_t k = 0; k < npts; ++k) {
         const float *s = pts + 3 * k, *nrm = normals + 3 * k;
@@ -622,16 +669,6 @@ void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G, c
         best[k] = (int16_t)best_g;
         label[k] = (best_g >= 0 && best_score < n_c) ? OR_ACCESSIBLE : OR_BLOCKED;
     }
-
-    for (int32_t g = 0; g < G; ++g) {
-        free(tool[g]);
-        free(corr[g]);
-    }
-    free(tool);
-    free(corr);
-    free(ntool);
-    free(ncorr);
-    free(arm);
 }
 
 

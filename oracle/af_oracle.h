@@ -107,6 +107,18 @@ void or_score(const or_map *m, const or_tool *t, const float *dirs, int32_t G,
               const float *pts, const float *normals, int64_t npts,
               uint8_t *label, int16_t *best, int32_t *dir_score);
 
+/* The same scoring with the kernel tables built once (Sec. 3.6: the kernels
+ * are precomputed at initialisation): or_score is or_tables_new,
+ * or_score_tables, or_tables_free. The tables hold the tool, the directions
+ * and the voxel size and truncation they were built for, which must be the
+ * map's. */
+typedef struct or_tables or_tables;
+or_tables *or_tables_new(const or_tool *t, float v, float tau, const float *dirs, int32_t G);
+void or_tables_free(or_tables *T);
+void or_score_tables(const or_map *m, const or_tables *T, const float *pts,
+                     const float *normals, int64_t npts, uint8_t *label, int16_t *best,
+                     int32_t *dir_score);
+
 /* The differentiable form: soft clearance of (point, direction) pairs.
  * Pair i belongs to point i / per_point. For pair i with base direction u0,
  * tangent coordinates (alpha, beta) and standoff h it writes

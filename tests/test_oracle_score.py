@@ -310,3 +310,30 @@ def test_adding_geometry_never_unblocks():
     assert not ((lab0 == oracle.BLOCKED) & (lab1 == oracle.ACCESSIBLE)).any()
     assert (ds1[cand] > ds0[cand]).any()       # the added geometry mattered
     assert (lab0 == oracle.ACCESSIBLE).any()
+
+
+def test_prebuilt_tables_score_identically():
+    """or_score_tables with kernel tables built once gives exactly what
+    or_score (which builds them per call) gives, on two maps in turn."""
+    from paper_2608_06412_gb300 import workload
+    W = workload.single_frame()
+    fr, pts, nrm = workload.single_frame_inputs(W, n=4000)
+    p = W.map_params()
+    cfg = oracle.Config(v=p["v"], tau=p["tau"], r_c=p["r_c"], cube_radius=p["cube_radius"],
+                        clear_samples=p["clear_samples"], dom_min=tuple(8 * b for b in W.dom_min),
+                        dom_size=tuple(8 * b for b in W.dom_bricks), w_min=p["w_min"])
+    tool = oracle.Tool(**W.tool())
+    T = oracle.ScoreTables(cfg, tool, W.dirs)
+    sel = slice(0, 400)
+    for half in (fr.pts[:2000], fr.pts):
+        mp = oracle.Map(cfg)
+        mp.integrate(half, fr.pose)
+        a = mp.score(tool, W.dirs, pts[sel], nrm[sel], dir_scores=True)
+        b = mp.score_tables(T, pts[sel], nrm[sel], dir_scores=True)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert (a[0] == oracle.ACCESSIBLE).any() and (a[0] == oracle.BLOCKED).any()
+    with pytest.raises(ValueError):
+        oracle.Map(oracle.Config(v=0.01, tau=0.04, r_c=0.005, cube_radius=4, clear_samples=10,
+                                 dom_min=(0, 0, 0), dom_size=(8, 8, 8))).score_tables(T, pts[:1],
+                                                                                       nrm[:1])
