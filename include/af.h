@@ -14,7 +14,18 @@
  *    centre is ((float)i + 0.5f) * v.
  *  - Pointers named d_* are device memory owned by the caller; pointers named
  *    h_* are host memory owned by the caller. The library owns the map, the
- *    kernel tables and its scratch, all allocated in af_create / af_set_tool.
+ *    kernel tables and its scratch, allocated in af_create / af_set_tool, and
+ *    on first use by the calls that say so (af_points_enable, the af_soft_*
+ *    views, the projective range image, work-sharing records beyond
+ *    max_points); all of it is freed by af_destroy.
+ *
+ * Entry points: the map (af_create, af_integrate_scan, af_set_tool,
+ * af_score, af_frame_host), batched ticks (af_batch_*), the differentiable
+ * form (af_soft_*), the stateful point layer (af_points_*), the paper's
+ * variants (af_integrate_scan_projective; clamp_signed in af_config; the
+ * coarse-to-fine search in af_points_config), scheduling (af_set_score_split),
+ * an allocation-free integration (af_integrate_scan_noalloc), and status,
+ * statistics, export, profiling and kernel-table inspection calls.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
  *    that take a stream are asynchronous on it unless stated otherwise.
  *  - Argument errors are returned synchronously and nothing is enqueued.
