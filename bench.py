@@ -281,6 +281,22 @@ TRAFFIC = {
 }
 
 
+# L2 traffic of k_score per launch (lts__t_sectors.sum x 32 B) and the L2 sector peak ncu
+# reports for it (lts__t_sectors.sum.per_second / its pct_of_peak_sustained_elapsed), from
+# the same --set full capture (profiles/k_score_pine_stream.md); keyed like TRAFFIC.
+L2_TRAFFIC = {"k_score": 315048672}
+L2_PEAK_GBS = 36300.0
+
+
+def _l2(kernel: str, avg_ms: float):
+    if kernel not in L2_TRAFFIC or _traffic(kernel) is None:
+        return None
+    b = L2_TRAFFIC[kernel]
+    rate = b / (avg_ms * 1e-3) / 1e9
+    return {"bound": "l2", "traffic": b, "achieved": rate, "peak": L2_PEAK_GBS,
+            "peak_kind": "ncu lts__t_sectors peak", "unit": "GB/s", "frac": rate / L2_PEAK_GBS}
+
+
 def _traffic(kernel: str):
     import hashlib
     if kernel not in TRAFFIC:
@@ -463,6 +479,7 @@ def run_ours(args, W, ws, rank, local):
         roof["bytes_per_test"] = bpt
         roof["achieved"] = alg / (avg_ms * 1e-3) / 1e9
         roof["frac"] = roof["achieved"] / peak
+        roof["l2"] = _l2(dom, avg_ms)
     else:
         roof["achieved"] = None
         roof["frac"] = None
