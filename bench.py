@@ -201,8 +201,9 @@ def cpu_baseline(W, frames, n_frames=6, n_sample=200):
         tests, secs = te, se
         t_int += ti
         t_sc, pts_scored = ts, ns
+    returns = sum(len(frames[k][0].pts) for k in range(n_frames))
     return {"value": tests / secs if secs > 0 else None, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
+            "kind": "oracle", "returns_per_s": returns / t_int if t_int > 0 else None,
             "sample": f"single-threaded C oracle: frames 0-{n_frames - 1} integrated "
                       f"({t_int / n_frames:.2f} s/frame), {pts_scored} random points of "
                       f"frame {n_frames - 1} scored in full ({t_sc:.2f} s, kernel tables "
