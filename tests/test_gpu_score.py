@@ -188,3 +188,23 @@ def test_work_sharing_pine_frames():
     g.set_score_split(-1)
     _compare(*b, *a)
     assert (a[0] == af.ACCESSIBLE).sum() > 100 and (a[0] == af.BLOCKED).sum() > 100
+
+
+def test_points_near_the_box_faces():
+    """A map box barely larger than the scene and smaller than twice the
+    kernels' reach (corridor 1 m = 50 voxels): every scored point takes the
+    bounds-checked path, with runs along all three axes reading voxels beyond
+    the faces as free and unknown."""
+    import torch
+    W = workload.single_frame()
+    fr, pts, nrm = workload.single_frame_inputs(W)
+    W2 = workload.Workload(W.name, W.params, W.scene, (9, -4, -5), (8, 8, 10), W.dirs)
+    g = gpu_map(W2)
+    g.integrate_scan(to_dev(fr.pts), fr.pose)
+    o = oracle.Map(oracle_config(W2))
+    o.integrate(fr.pts, fr.pose)
+    g.set_tool(W.af_tool(), W.dirs)
+    gl, gb = _gpu_score(g, pts, nrm)
+    ol, ob = o.score(oracle_tool(W), W.dirs, pts, nrm)
+    _compare(gl, gb, ol, ob)
+    assert (ol == oracle.ACCESSIBLE).sum() > 20 and (ol == oracle.BLOCKED).sum() > 20
