@@ -450,3 +450,36 @@ def test_coarse_to_fine_degenerate_cases_are_the_full_search(stride, half):
     for key in ("score", "best", "label", "a"):
         assert (res[0][key] == res[1][key]).all(), key
     assert (res[0]["score"] >= 0).sum() > 1000
+
+
+def test_brick_trigger_covers_the_voxel_rule():
+    """Reading P5: trigger (ii) at brick granularity re-queues every point that
+    the paper's voxel rule would (a voxel within r_u = 3v updated by the
+    frame's returns), and leaves points far from the frame's returns alone."""
+    from scipy.spatial import cKDTree
+    dirs = synth.fibonacci_dirs(32)
+    mp = oracle.Map(_cfg())
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, budget=0), _tool(), dirs)
+    pts, pose = _frame(_slotted_scene(), (0.0, 0.0, 0.0), n=6000)
+    P.frame(pts, pose)
+    P.drain(10 ** 9)
+    n0 = len(P)
+    # returns on the right part of the wall only; the sensor moves 2 cm (no motion trigger)
+    pts, pose = _frame(_slotted_scene(), (0.0, 0.02, 0.0), n=6000, seed=4)
+    side = pts[pts[:, 1] > 0.2]
+    P.frame(side, pose)
+    e = P.export()
+    T = np.asarray(pose, np.float64).reshape(4, 4)
+    world = side.astype(np.float64) @ T[:3, :3].T + T[:3, 3]
+    ij = np.unique(np.floor(world / np.float64(np.float32(V))).astype(np.int64), axis=0)
+    m = _cfg().cube_radius
+    cube = np.array([(x, y, z) for z in range(-m, m + 1) for y in range(-m, m + 1)
+                     for x in range(-m, m + 1)])
+    changed = np.unique((ij[:, None, :] + cube[None]).reshape(-1, 3), axis=0)
+    d, _ = cKDTree(changed.astype(np.float64)).query(e["ijk"][:n0].astype(np.float64),
+                                                      distance_upper_bound=3.0 + 1e-9)
+    voxel_rule = np.isfinite(d)
+    queued = e["queued"][:n0].astype(bool)
+    assert voxel_rule.sum() > 100
+    assert not (voxel_rule & ~queued).any()        # the voxel rule is covered
+    assert (~queued).sum() > 100                   # far points stay unqueued
