@@ -18,7 +18,12 @@ and mathematics fix:
   accessible set after two (c a = 0.5625 < 0.7), its stored score unchanged;
 * a sensor move above trig_move re-queues blocked points, a smaller one
   does not, and the distance is measured from where the trigger last fired;
-  returns far away queue nothing.
+  returns far away queue nothing;
+* the brick-level neighbourhood trigger covers the exact voxel rule
+  (a changed voxel within r_u = 3v);
+* the coarse-to-fine search (Sec. 3.6) against a brute force over the plain
+  scorer's per-direction scores, for first evaluations and re-evaluations,
+  and its degenerate cases against the full search.
 Parity status: pinned.
 """
 import numpy as np
