@@ -2,8 +2,13 @@
 
 Each test checks the oracle (oracle/af_oracle.c) against a value that does
 not come from the oracle itself: hand-worked fixtures (tests/golden), the
-analytic signed distance of a sphere and of a plane, exact invariances (pose,
-order, splitting), and the rejection rules. Parity status: pinned.
+analytic signed distance of a sphere and of a plane, an unbiased quantisation
+(rounding to nearest), exact invariances (pose, order, splitting), and the
+rejection rules. The variants of Tab. 3 and 4 are pinned the same way: the
+[-tau, tau] clamp by the analytic signed distance and the floor rounding of
+negative capped sums; projective integration by an octahedral-cell round trip,
+the analytic distance with a brute force of the updated voxels, the nearest
+range per cell, and the erosion of a thin pole. Parity status: pinned.
 """
 import math
 

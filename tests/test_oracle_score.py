@@ -7,8 +7,9 @@ scenes for every term of the score, the lowest-index tie-break, the
 confidence gate, and the paper's qualitative ground truth on exactly
 voxelised analytic scenes -- a slot narrower than the tool is inaccessible,
 a convex sphere and a flat wall are accessible near their normals (Tab. 1),
-and adding geometry never turns a blocked point accessible. Parity status:
-pinned.
+and adding geometry never turns a blocked point accessible. Scoring with
+kernel tables built once equals scoring that builds them per call. Parity
+status: pinned.
 """
 import math
 
