@@ -153,7 +153,7 @@ class Clocks:
 # Oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def _oracle_objs(W):
+def _oracle_objs(W, tables: bool = True):
     import oracle
     p = W.map_params()
     cfg = oracle.Config(v=p["v"], tau=p["tau"], r_c=p["r_c"], cube_radius=p["cube_radius"],
@@ -165,7 +165,7 @@ def _oracle_objs(W):
                         w_cap=p["w_cap"])
     tool = oracle.Tool(**W.tool())
     # the kernel tables are built once, as the method precomputes them (Sec. 3.6)
-    return oracle.Map(cfg), (tool, oracle.ScoreTables(cfg, tool, W.dirs))
+    return oracle.Map(cfg), (tool, oracle.ScoreTables(cfg, tool, W.dirs) if tables else None)
 
 
 def _oracle_frame(om, tool, W, frame, n_sample, rng):
@@ -209,6 +209,74 @@ def cpu_baseline(W, frames, n_frames=6, n_sample=200):
                       f"frame {n_frames - 1} scored in full ({t_sc:.2f} s, kernel tables "
                       f"built once beforehand); per-frame tests and time prorated to all "
                       f"points of that frame"}
+
+
+def points_cpu_baseline(W, frames, n_frames=6, budget=400):
+    """The oracle's stateful layer over the first frames of the stream with a
+    per-frame budget: evaluations per second (integration, point set,
+    triggers and evaluations all timed)."""
+    import oracle
+    om, (tool, _) = _oracle_objs(W)
+    P = oracle.PointSet(om, oracle.PointsConfig(trig_tsdf=2 * W.params["v"], budget=budget),
+                        tool, W.dirs)
+    t0 = time.perf_counter()
+    evals = 0
+    for k in range(n_frames):
+        fr = frames[k][0]
+        evals += P.frame(fr.pts, fr.pose)
+    secs = time.perf_counter() - t0
+    return {"value": evals / secs if secs > 0 else None, "unit": "evaluations/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"single-threaded C oracle: the stateful layer over frames 0-{n_frames - 1} "
+                      f"with {budget} evaluations per frame ({evals} evaluations, {secs:.1f} s)"}
+
+
+def sample_cpu_baseline(W, frames, n_frames, n_points, seed=0):
+    """The plain oracle on one workload: frames integrated, then a random
+    sample of the last frame's points scored with kernel tables built once.
+    Returns (tests, seconds, returns integrated, integration seconds)."""
+    import oracle
+    om, (tool, tables) = _oracle_objs(W)
+    t0 = time.perf_counter()
+    for k in range(n_frames):
+        om.integrate(frames[k][0], frames[k][1])
+    t1 = time.perf_counter()
+    P, N = frames[n_frames - 1][2], frames[n_frames - 1][3]
+    sel = np.random.default_rng(seed).choice(len(P), min(n_points, len(P)), replace=False)
+    t2 = time.perf_counter()
+    _, _, ds = om.score_tables(tables, P[sel], N[sel], dir_scores=True)
+    t3 = time.perf_counter()
+    returns = sum(len(frames[k][0]) for k in range(n_frames))
+    return int((ds >= 0).sum()), t3 - t2, returns, t1 - t0
+
+
+def large_cpu_baseline(W, frames, n_frames=5, n_points=30, every=16):
+    """The plain oracle on the large map: the first frames integrated, then a
+    random sample of the last one's points scored against every `every`-th
+    direction (kernel tables for all 512 take minutes to build; a test costs
+    the same whichever direction it is)."""
+    import oracle
+    om, _ = _oracle_objs(W, tables=False)
+    tool = oracle.Tool(**W.tool())
+    dirs = np.ascontiguousarray(W.dirs[::every])
+    tables = oracle.ScoreTables(om.cfg, tool, dirs)
+    t0 = time.perf_counter()
+    for k in range(n_frames):
+        om.integrate(frames[k][0], frames[k][1])
+    t1 = time.perf_counter()
+    P, N = frames[n_frames - 1][3], frames[n_frames - 1][4]
+    sel = np.random.default_rng(0).choice(len(P), min(n_points, len(P)), replace=False)
+    t2 = time.perf_counter()
+    _, _, ds = om.score_tables(tables, P[sel], N[sel], dir_scores=True)
+    t3 = time.perf_counter()
+    tests = int((ds >= 0).sum())
+    returns = sum(len(frames[k][0]) for k in range(n_frames))
+    return {"value": tests / (t3 - t2), "unit": "tests/s", "cores": 1, "kind": "oracle",
+            "returns_per_s": returns / (t1 - t0),
+            "sample": f"single-threaded C oracle: frames 0-{n_frames - 1} integrated "
+                      f"({(t1 - t0) / n_frames:.2f} s/frame), {len(sel)} random points of frame "
+                      f"{n_frames - 1} scored against {len(dirs)} of the {len(W.dirs)} directions "
+                      f"({tests} tests, {t3 - t2:.1f} s)"}
 
 
 def run_reference(args, W, ws, rank):
@@ -602,7 +670,24 @@ def run_batched(args, local):
         "speedup_vs_per_scene": (sum(msp) / steps) / (sum(msb) / steps),
         "label_agreement": agree,
         "tests_equal": testsb == testsp,
+        "cpu_baseline": None if args.no_cpu_baseline else batched_cpu_baseline(S, frames),
     }
+
+
+def batched_cpu_baseline(S, frames, n_scenes=2, n_points=40):
+    """The plain oracle on the first scenes of the batch, each on its own
+    three frames and tool, tests/s over the scored samples."""
+    tests = secs = 0.0
+    for W, fs in zip(S[:n_scenes], frames[:n_scenes]):
+        t, sec, _, _ = sample_cpu_baseline(W, [(fr.pts, fr.pose, p, n) for fr, p, n in fs],
+                                           len(fs), n_points)
+        tests += t
+        secs += sec
+    return {"value": tests / secs if secs > 0 else None, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"single-threaded C oracle: scenes 0-{n_scenes - 1} of the batch, each "
+                      f"integrated from its frames, then {n_points} random points of its last "
+                      f"frame scored with its tool (kernel tables built once)"}
 
 
 SOFT_METRIC = ("soft clearance evaluations/s (plain scoring of 100k points, then 20 ascent "
@@ -894,6 +979,7 @@ def run_large(args, local):
         "tests_per_point": tests / max(scored, 1),
         "gpu_launches": int(sum(v[0] for v in prof.values())),
         "clocks": clk,
+        "cpu_baseline": None if args.no_cpu_baseline else large_cpu_baseline(W, frames),
     }
     g.close()
     return out
@@ -979,6 +1065,9 @@ def run_points(args, local):
                    "queued": int(e["queued"].sum())},
         "with_direction": int((e["best"] >= 0).sum()),
         "clocks": clk,
+        # the oracle's layer on the default set-up (a variant line reports none)
+        "cpu_baseline": None if (args.no_cpu_baseline or args.ring or args.clamp_signed)
+        else points_cpu_baseline(W, frames),
     }
     g.close()
     g2.close()
