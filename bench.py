@@ -18,6 +18,14 @@ The CPU oracle is timed on a bounded sample of the same workload
 
 Under torchrun with N > 1 every rank runs an independent replica (the path
 has no exchange step); value = all ranks' tests / the slowest rank's time.
+
+Other lines, each with the oracle timed beside it on a bounded sample:
+  --batched    64 uneven scenes ticked together, against the per-scene path;
+  --soft       the differentiable step: 100k points, 20 ascent steps each;
+  --points     the stateful layer (triggers, budget, PCA normals, c and a);
+  --large      the 40 x 40 m map at 1 cm: 3,000 frames, then every surface point;
+and variants of the default line: --projective, --clamp-signed, --ring
+(the paper's yaw ring; with --points also --c2f), --score-split B.
 """
 from __future__ import annotations
 
