@@ -505,13 +505,16 @@ af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);
  * The library allocates nothing: its per-return scratch is a fixed device
  * array of AF_NOALLOC_MAX_RETURNS float4 (1 MiB) that every GPU loading the
  * library holds until the process exits. n > AF_NOALLOC_MAX_RETURNS returns
- * AF_ERR_CAPACITY (split the scan). The first call on a device looks up the
+ * AF_ERR_CAPACITY (split the scan). A box of more than
+ * AF_NOALLOC_MAX_BOX_VOXELS (2^40) voxels returns AF_ERR_INVALID_ARG. The
+ * first call on a device looks up the
  * array's device address once; make that first call before any stream
  * capture. All calls share the array: calls that overlap on the GPU race and
  * must be serialised by the caller. Asynchronous on `stream`; errors are
  * reported through af_last_error(NULL).
  */
 #define AF_NOALLOC_MAX_RETURNS 65536
+#define AF_NOALLOC_MAX_BOX_VOXELS (1ull << 40)
 af_status af_integrate_scan_noalloc(const af_config *cfg, const float *d_xyz, uint32_t n,
                                     const float pose[16], const int32_t box_min[3],
                                     const uint32_t box_dim[3], uint64_t *d_vox,

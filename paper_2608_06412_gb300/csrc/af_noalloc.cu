@@ -115,9 +115,11 @@ __global__ void __launch_bounds__(256) k_na_integrate(MapView M, const float4* _
     const float range =
         __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(b0, b0), __fmul_rn(b1, b1)), __fmul_rn(b2, b2)));
     int i[3];
-    voxel_index(p.x, M, &i[0]);
-    voxel_index(p.y, M, &i[1]);
-    voxel_index(p.z, M, &i[2]);
+    // k_na_prepare accepted the return, so its voxel index exists; checked
+    // again here so that no index is used unchecked
+    if (!(voxel_index(p.x, M, &i[0]) && voxel_index(p.y, M, &i[1]) &&
+          voxel_index(p.z, M, &i[2])))
+      return;
     const int jx = i[0] - M.dom_vox[0] + o % W - M.m;
     const int jy = i[1] - M.dom_vox[1] + (o / W) % W - M.m;
     const int jz = i[2] - M.dom_vox[2] + o / (W * W) - M.m;
@@ -209,7 +211,12 @@ extern "C" af_status af_integrate_scan_noalloc(const af_config* cfg, const float
         std::abs((long long)cfg->domain_min[k]) > (1 << 25) || box_dim[k] < 1 ||
         box_dim[k] >= (1u << 24) || std::abs((long long)box_min[k]) > (1 << 28))
       return nfail(AF_ERR_INVALID_ARG, "af_integrate_scan_noalloc: domain or box out of range");
+    // each factor is below 2^24, so the running product (at most 2^40 before
+    // this step) cannot wrap before the check
     count *= box_dim[k];
+    if (count > AF_NOALLOC_MAX_BOX_VOXELS)
+      return nfail(AF_ERR_INVALID_ARG,
+                   "af_integrate_scan_noalloc: the box holds more than 2^40 voxels");
   }
   for (int k = 0; k < 12; ++k)
     if (!finite_f(pose[k])) return nfail(AF_ERR_INVALID_ARG, "af_integrate_scan_noalloc: non-finite pose");

@@ -43,6 +43,26 @@ def test_host_errors_are_reported_without_gpu():
     assert lib.af_create(None, None) == 1
 
 
+def test_noalloc_rejects_boxes_beyond_its_limit():
+    """af_integrate_scan_noalloc rejects a box of more than 2^40 voxels before
+    touching the GPU, including boxes whose voxel count would wrap a 64-bit
+    product (2^23 per axis = 2^69 voxels)."""
+    import ctypes as C
+    from paper_2608_06412_gb300 import workload
+    lib = af.load()
+    cc = workload.single_frame().af_config()._c()
+    pose = np.eye(4, dtype=np.float32).reshape(16)
+    bmin = np.zeros(3, np.int32)
+    dummy = C.c_void_p(256)  # never dereferenced: the call returns before any CUDA work
+    for dims in ((1 << 23, 1 << 23, 1 << 23), (1 << 20, 1 << 20, 2), (1 << 23, 1 << 23, 1 << 8)):
+        bdim = np.asarray(dims, np.uint32)
+        st = lib.af_integrate_scan_noalloc(C.byref(cc), C.c_void_p(0), 0, af._np_ptr(pose),
+                                           af._np_ptr(bmin), af._np_ptr(bdim), dummy, dummy,
+                                           C.c_void_p(0))
+        assert st == 1, dims
+        assert b"2^40" in lib.af_last_error(None)
+
+
 def _tools():
     yield synth.SINGLE_FRAME["tool"], 0.02
     yield dict(radius=0.03, length=0.15, self_excl=0.005, corr_radius=0.03,
