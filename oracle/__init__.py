@@ -69,7 +69,8 @@ class _PtsConfig(C.Structure):
                 ("trig_move", C.c_float), ("budget", C.c_uint32), ("k_c", C.c_float),
                 ("c_min", C.c_float), ("a_decay", C.c_float), ("a_recover", C.c_float),
                 ("ca_min", C.c_float), ("c2f_stride", C.c_uint32), ("c2f_half", C.c_uint32),
-                ("c2f_radius", C.c_float)]
+                ("c2f_radius", C.c_float), ("trig_exact", C.c_int32), ("trig_radius", C.c_int32),
+                ("trig_sample", C.c_uint32)]
 
 
 def _load():
@@ -126,6 +127,8 @@ def _load():
         lib.or_pts_count.argtypes = [P]
         lib.or_pts_export.argtypes = [P, P, P, P, P, P, P, P, P]
         lib.or_jacobi3.argtypes = [P, C.c_int, P, P]
+        lib.or_mix64.restype = C.c_uint64
+        lib.or_mix64.argtypes = [C.c_uint64]
         lib.or_pts_state_step.argtypes = [C.POINTER(_PtsConfig), C.c_int32, C.c_int32, C.c_int32,
                                           C.c_float, P, P, P, P]
         lib.or_soft_refine.argtypes = [P, C.POINTER(_Tool), P, C.c_uint32, P, P, P, P,
@@ -397,6 +400,12 @@ class PointsConfig:
     c2f_stride: int = 0
     c2f_half: int = 0
     c2f_radius: float = 0.3
+    # trigger (ii): 1 = a changed voxel within trig_radius voxels (r_u = 3v),
+    # among at most trig_sample changed voxels drawn per frame (0: all of
+    # them); 0 = the brick rule, a superset
+    trig_exact: int = 1
+    trig_radius: int = 3
+    trig_sample: int = 256
 
     def _c(self) -> _PtsConfig:
         c = _PtsConfig()
@@ -474,3 +483,9 @@ def pts_state_step(pc: PointsConfig, n_c: int, state: dict, s: int, g: int, c: f
     lab = np.array([state.get("label", 0)], np.uint8)
     lib.or_pts_state_step(C.byref(cc), n_c, s, g, c, _ptr(sc), _ptr(bs), _ptr(a), _ptr(lab))
     return dict(score=int(sc[0]), best=int(bs[0]), a=float(a[0]), label=int(lab[0]))
+
+
+def mix64(z: int) -> int:
+    """splitmix64's output function as the oracle computes it (the hash that
+    draws the sample of changed voxels for the re-evaluation trigger)."""
+    return int(_load().or_mix64(z & 0xFFFFFFFFFFFFFFFF))

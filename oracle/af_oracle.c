@@ -224,11 +224,16 @@ static int voxel_index(float c, float v, int32_t *out) {
 static float voxel_centre(int32_t i, float v) { return ((float)i + 0.5f) * v; }
 
 int64_t or_integrate(or_map *m, const float *pts, int64_t n, const float pose[16]) {
-    return or_integrate2(m, pts, n, pose, NULL);
+    return or_integrate_bands(m, pts, n, pose, NULL, NULL);
 }
 
 int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[16],
                       int32_t *voxel_out) {
+    return or_integrate_bands(m, pts, n, pose, voxel_out, NULL);
+}
+
+int64_t or_integrate_bands(or_map *m, const float *pts, int64_t n, const float pose[16],
+                           int32_t *voxel_out, int32_t *band_out) {
     const or_config *c = &m->cfg;
     const float v = c->v, tau = c->tau, lo = c->clamp_signed ? -c->tau : 0.0f;
     const int32_t mr = c->cube_radius;
@@ -238,6 +243,8 @@ int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[1
 
     if (voxel_out)
         for (int64_t k = 0; k < 3 * n; ++k) voxel_out[k] = INT32_MIN;
+    if (band_out)
+        for (int64_t k = 0; k < 3 * n * c->clear_samples; ++k) band_out[k] = INT32_MIN;
     for (int64_t k = 0; k < n; ++k) {
         const float *ps = pts + 3 * k;
         if (!isfinite(ps[0]) || !isfinite(ps[1]) || !isfinite(ps[2])) continue;
@@ -306,6 +313,9 @@ int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[1
                 continue;
             if (!in_domain(c, js[0], js[1], js[2])) continue;
             voxel_ref(m, js[0], js[1], js[2])->cleared = 1;
+            if (band_out)
+                for (int r = 0; r < 3; ++r)
+                    band_out[3 * (k * c->clear_samples + (s - 1)) + r] = js[r];
         }
     }
 

@@ -75,6 +75,12 @@ int32_t or_octa_bin(const float d[3], int32_t bins);
  * (n x 3, INT32_MIN for dropped returns) when it is not NULL. */
 int64_t or_integrate2(or_map *m, const float *pts, int64_t n, const float pose[16],
                       int32_t *voxel_out);
+/* As or_integrate2; band_out (n x clear_samples x 3, or NULL) receives the
+ * voxel of each cleared-band sample marked for return k, sample s at row
+ * k * clear_samples + (s - 1) (INT32_MIN where the return was dropped or the
+ * sample fell outside the box). */
+int64_t or_integrate_bands(or_map *m, const float *pts, int64_t n, const float pose[16],
+                           int32_t *voxel_out, int32_t *band_out);
 
 /* Voxel state. Absent voxels report S = 0, w = 0, cleared = 0. */
 int or_get_voxel(const or_map *m, int32_t ix, int32_t iy, int32_t iz,
@@ -165,7 +171,22 @@ typedef struct {
     uint32_t c2f_stride;
     uint32_t c2f_half;
     float c2f_radius;
+    /* Trigger (ii) of Sec. 3.5. trig_exact = 1: a voxel within trig_radius
+     * voxels (|o|^2 <= trig_radius^2; r_u = 3v: 3) of the point's voxel
+     * changed its stored state (S, w or ray-cleared mark) in this scan, among
+     * the changed voxels sampled for the frame: at most trig_sample (256) of
+     * them, those with the smallest or_mix64(key ^ or_mix64(frame)); 0 = all.
+     * trig_exact = 0 (the brick rule): a brick within one brick of the point's
+     * brick was touched by the scan (a return's cube or cleared-band sample
+     * lies in it), a superset of the unsampled exact rule. */
+    int32_t trig_exact;
+    int32_t trig_radius;
+    uint32_t trig_sample;
 } or_pts_config;
+
+/* splitmix64's output function: a bijection of 64-bit words (the hash that
+ * draws the sample of trigger (ii)). */
+uint64_t or_mix64(uint64_t z);
 
 typedef struct or_pts or_pts;
 

@@ -28,12 +28,25 @@
  *    u . (q - s) / |q - s| > obs_dot (u points from the surface outward).
  *  - Triggers, after the frame's integration: (i) the TSDF at the point's
  *    voxel moved by more than trig_tsdf since the previous frame; (ii) a
- *    brick within one brick of the point's brick lies in the cube of an
- *    accepted return of the frame (a superset of "a voxel within r_u = 3v
- *    changed", as 3v is less than a brick; the paper's sampling of at most
- *    256 changed voxels only bounds its query cost); (iii) the sensor moved
- *    more than trig_move since the last time this trigger fired: every point
- *    labelled BLOCKED is re-queued; new points are always queued.
+ *    changed voxel within r_u of the point: |o|^2 <= R^2 for the integer
+ *    offset o between the two voxels, R = trig_radius (3 for r_u = 3v). A
+ *    voxel changes in a scan when its stored state (S, w, ray-cleared mark)
+ *    after the scan, weight cap included, differs from its state before (a
+ *    voxel never stored has S = w = 0 and no mark). Like the paper, the
+ *    changed voxels are sampled to bound the query: when there are more
+ *    than trig_sample (256) of them, the trig_sample with the smallest
+ *    h = mix(key ^ mix(f)) are tested, mix the splitmix64 finaliser (a
+ *    bijection, so no two voxels tie), key the packed absolute voxel index
+ *    and f the layer's frame number (1, 2, ...); trig_sample = 0 tests them
+ *    all. The sample is why (i) is not implied by (ii): the point's own
+ *    voxel may change without being drawn. (iii) the sensor moved more than
+ *    trig_move since the last time this trigger fired: every point labelled
+ *    BLOCKED is re-queued; new points are always queued.
+ *    The brick rule (trig_exact = 0), a cheaper superset of (ii) taken over
+ *    every changed voxel: a brick within one brick of the point's brick was
+ *    touched by the scan, i.e. it overlaps the cube of an accepted return or
+ *    holds one of its cleared-band samples; every voxel that can change lies
+ *    in such a brick, and r_u < one brick.
  *  - Budget: each frame dequeues up to `budget` queued points in id order;
  *    the rest stay queued (the backlog, also drained by or_pts_drain).
  *  - A dequeued point with c = w / (w + k_c) < c_min at its voxel keeps its
@@ -509,16 +522,115 @@ static int key_cmp(const void *x, const void *y) {
     return 0;
 }
 
+/* The stored state of every voxel: key -> index into (S, w, cleared). */
+typedef struct {
+    keymap at;
+    int64_t *S;
+    uint32_t *w;
+    uint8_t *cl;
+    int32_t *ijk;
+    int64_t n;
+} snapshot;
+
+static void state_snapshot(const or_map *m, snapshot *out) {
+    const int64_t nv = or_voxel_count(m);
+    const size_t cnt = (size_t)(nv > 0 ? nv : 1);
+    out->n = nv;
+    out->ijk = (int32_t *)malloc(sizeof(int32_t) * 3 * cnt);
+    out->S = (int64_t *)malloc(sizeof(int64_t) * cnt);
+    out->w = (uint32_t *)malloc(sizeof(uint32_t) * cnt);
+    out->cl = (uint8_t *)malloc(cnt);
+    uint8_t *oc = (uint8_t *)malloc(cnt), *kn = (uint8_t *)malloc(cnt);
+    or_export(m, out->ijk, out->S, out->w, out->cl, oc, kn);
+    free(oc);
+    free(kn);
+    km_init(&out->at, 1024);
+    for (int64_t k = 0; k < nv; ++k)
+        km_put(&out->at, vkey(out->ijk[3 * k], out->ijk[3 * k + 1], out->ijk[3 * k + 2]), k);
+}
+
+static void snapshot_free(snapshot *s) {
+    km_free(&s->at);
+    free(s->ijk);
+    free(s->S);
+    free(s->w);
+    free(s->cl);
+}
+
+/* splitmix64's output function (Steele, Lea, Flood 2014): a bijection of
+ * 64-bit words. */
+uint64_t or_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static int u64_cmp(const void *x, const void *y) {
+    const uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* The changed voxels of the scan that trigger (ii) tests (see the header):
+ * all of them, or the `sample` with the smallest h. */
+static void changed_sample(const snapshot *before, const snapshot *after, uint32_t sample,
+                           uint32_t f, keymap *out) {
+    const uint64_t salt = or_mix64((uint64_t)f);
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(after->n > 0 ? after->n : 1));
+    uint64_t *h = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(after->n > 0 ? after->n : 1));
+    int64_t nc = 0;
+    for (int64_t k = 0; k < after->n; ++k) {
+        const uint64_t kk = vkey(after->ijk[3 * k], after->ijk[3 * k + 1], after->ijk[3 * k + 2]);
+        const int64_t b = km_get(&before->at, kk);
+        const int same = b >= 0 ? (before->S[b] == after->S[k] && before->w[b] == after->w[k] &&
+                                   before->cl[b] == after->cl[k])
+                                : (after->S[k] == 0 && after->w[k] == 0 && after->cl[k] == 0);
+        if (same) continue;
+        key[nc] = kk;
+        h[nc] = or_mix64(kk ^ salt);
+        ++nc;
+    }
+    uint64_t t = UINT64_MAX; /* the largest h tested */
+    if (sample > 0 && nc > (int64_t)sample) {
+        uint64_t *sorted = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nc);
+        memcpy(sorted, h, sizeof(uint64_t) * (size_t)nc);
+        qsort(sorted, (size_t)nc, sizeof(uint64_t), u64_cmp);
+        t = sorted[sample - 1];
+        free(sorted);
+    }
+    km_init(out, 1024);
+    for (int64_t k = 0; k < nc; ++k)
+        if (h[k] <= t) km_put(out, key[k], 1);
+    free(key);
+    free(h);
+}
+
 int64_t or_pts_frame(or_pts *P, or_map *m, const float *pts, int64_t n, const float pose[16]) {
     const float q[3] = {pose[3], pose[7], pose[11]};
-    const int32_t mr = P->mc.cube_radius;
+    const int32_t mr = P->mc.cube_radius, ns = P->mc.clear_samples;
+    const int exact = P->pc.trig_exact != 0;
+    snapshot before;
+    keymap tested; /* the changed voxels trigger (ii) tests */
+    if (exact) state_snapshot(m, &before);
     int32_t *vox = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * (n > 0 ? n : 1)));
-    or_integrate2(m, pts, n, pose, vox);
+    int32_t *band = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * (n > 0 ? n : 1) * (ns > 0 ? ns : 1)));
+    or_integrate_bands(m, pts, n, pose, vox, band);
     P->scan++;
+    if (exact) {
+        snapshot after;
+        state_snapshot(m, &after);
+        changed_sample(&before, &after, P->pc.trig_sample, P->scan, &tested);
+        snapshot_free(&after);
+        snapshot_free(&before);
+    }
 
-    /* bricks overlapped by the cubes of the accepted returns */
+    /* bricks touched by the scan: the cubes and cleared-band samples of the
+       accepted returns (the brick rule) */
     keymap changed;
     km_init(&changed, 1024);
+    for (int64_t k = 0; k < n * ns; ++k) {
+        const int32_t *j = band + 3 * k;
+        if (j[0] != INT32_MIN) km_put(&changed, vkey(floor8(j[0]), floor8(j[1]), floor8(j[2])), 1);
+    }
     /* new points, unique, in (z, y, x) order */
     int32_t *fresh = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * (n > 0 ? n : 1)));
     int64_t nf = 0;
@@ -582,16 +694,27 @@ int64_t or_pts_frame(or_pts *P, or_map *m, const float *pts, int64_t n, const fl
     }
 
     /* triggers (i) and (ii) */
+    const int32_t R = P->pc.trig_radius;
     for (int64_t id = 0; id < P->n; ++id) {
         or_point *pt = &P->p[id];
         const float cur = tsdf_at(m, pt->ijk, NULL);
         if (fabsf(cur - pt->last_tsdf) > P->pc.trig_tsdf) pt->queued = 1;
         pt->last_tsdf = cur;
-        const int32_t bx = floor8(pt->ijk[0]), by = floor8(pt->ijk[1]), bz = floor8(pt->ijk[2]);
-        for (int32_t dz = -1; dz <= 1 && !pt->queued; ++dz)
-            for (int32_t dy = -1; dy <= 1 && !pt->queued; ++dy)
-                for (int32_t dx = -1; dx <= 1 && !pt->queued; ++dx)
-                    if (km_get(&changed, vkey(bx + dx, by + dy, bz + dz)) >= 0) pt->queued = 1;
+        if (exact) {
+            for (int32_t dz = -R; dz <= R && !pt->queued; ++dz)
+                for (int32_t dy = -R; dy <= R && !pt->queued; ++dy)
+                    for (int32_t dx = -R; dx <= R && !pt->queued; ++dx)
+                        if (dx * dx + dy * dy + dz * dz <= R * R &&
+                            km_get(&tested, vkey(pt->ijk[0] + dx, pt->ijk[1] + dy,
+                                                 pt->ijk[2] + dz)) >= 0)
+                            pt->queued = 1;
+        } else {
+            const int32_t bx = floor8(pt->ijk[0]), by = floor8(pt->ijk[1]), bz = floor8(pt->ijk[2]);
+            for (int32_t dz = -1; dz <= 1 && !pt->queued; ++dz)
+                for (int32_t dy = -1; dy <= 1 && !pt->queued; ++dy)
+                    for (int32_t dx = -1; dx <= 1 && !pt->queued; ++dx)
+                        if (km_get(&changed, vkey(bx + dx, by + dy, bz + dz)) >= 0) pt->queued = 1;
+        }
     }
     /* trigger (iii) */
     if (P->have_q_last) {
@@ -607,9 +730,11 @@ int64_t or_pts_frame(or_pts *P, or_map *m, const float *pts, int64_t n, const fl
     }
 
     km_free(&changed);
+    if (exact) km_free(&tested);
     km_free(&seen);
     free(fresh);
     free(vox);
+    free(band);
     return or_pts_drain(P, m, (int64_t)P->pc.budget);
 }
 

@@ -19,8 +19,12 @@ and mathematics fix:
 * a sensor move above trig_move re-queues blocked points, a smaller one
   does not, and the distance is measured from where the trigger last fired;
   returns far away queue nothing;
-* the brick-level neighbourhood trigger covers the exact voxel rule
-  (a changed voxel within r_u = 3v);
+* the neighbourhood trigger (a changed voxel within r_u = 3v, among the
+  changed voxels drawn for the frame, or all of them) against a brute force
+  over the map's voxel states before and after the frame; the TSDF trigger
+  firing on its own; the brick rule covering the unsampled voxel rule, which
+  covers the sampled one; the hash that draws the sample against published
+  splitmix64 outputs;
 * the coarse-to-fine search (Sec. 3.6) against a brute force over the plain
   scorer's per-direction scores, for first evaluations and re-evaluations,
   and its degenerate cases against the full search.
@@ -211,7 +215,10 @@ def test_two_conflicts_leave_the_accessible_set():
     leaves it accessible, two push c a below 0.7; the stored score stays."""
     mp = oracle.Map(_cfg())
     dirs = np.array([[-1.0, 0.0, 0.0]], np.float32)     # one approach direction: from -x
-    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, k_c=1e-3), _tool(), dirs)
+    # every changed voxel is tested (no sample), so the wall's own returns
+    # re-queue the point each frame and both blocking evaluations happen
+    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, k_c=1e-3, trig_sample=0), _tool(),
+                        dirs)
     wall = _wall(half=0.3)
     for k in range(3):
         pts, pose = _frame(wall, (0.0, 0.0, 0.0), n=4000, seed=k)
@@ -457,34 +464,170 @@ def test_coarse_to_fine_degenerate_cases_are_the_full_search(stride, half):
     assert (res[0]["score"] >= 0).sum() > 1000
 
 
-def test_brick_trigger_covers_the_voxel_rule():
-    """Reading P5: trigger (ii) at brick granularity re-queues every point that
-    the paper's voxel rule would (a voxel within r_u = 3v updated by the
-    frame's returns), and leaves points far from the frame's returns alone."""
+_M64 = (1 << 64) - 1
+
+
+def _mix64(z):
+    """splitmix64's output function written out (Steele, Lea, Flood 2014)."""
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def test_mix64_gives_the_published_splitmix64_outputs():
+    """The hash that draws the sample: splitmix64 seeded with 0 outputs
+    0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f (the state
+    advances by 0x9e3779b97f4a7c15 before each output)."""
+    state, out = 0, []
+    for _ in range(3):
+        state = (state + 0x9E3779B97F4A7C15) & _M64
+        out.append(oracle.mix64(state))
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    for z in (0, 1, 2 ** 63, 0x123456789ABCDEF, _M64):
+        assert oracle.mix64(z) == _mix64(z)
+
+
+def _voxel_state(mp):
+    e = mp.export()
+    return {tuple(map(int, k)): (int(S), int(w), int(c))
+            for k, S, w, c in zip(e["ijk"], e["S"], e["w"], e["cleared"])}
+
+
+def _tsdf(state, k, tau):
+    S, w, _ = state.get(tuple(map(int, k)), (0, 0, 0))
+    return np.float32(tau) if w == 0 else np.float32(S / (w * 1048576.0))
+
+
+def _expected_queue(before, after, ijk, frame, sample, radius=3):
+    """Sec. 3.5 triggers (i) and (ii) by brute force over the map's voxels:
+    the changed voxels (stored state before != after), the sample of the
+    `sample` smallest hashes (all if 0), every point within `radius` voxels
+    of a sampled one; and the TSDF moving by more than 2v at the point."""
     from scipy.spatial import cKDTree
-    dirs = synth.fibonacci_dirs(32)
-    mp = oracle.Map(_cfg())
-    P = oracle.PointSet(mp, oracle.PointsConfig(trig_tsdf=2 * V, budget=0), _tool(), dirs)
-    pts, pose = _frame(_slotted_scene(), (0.0, 0.0, 0.0), n=6000)
+    changed = np.array([k for k, v in after.items() if before.get(k, (0, 0, 0)) != v], np.int64)
+    assert len(changed) > 0
+    salt = _mix64(frame)
+    h = [_mix64((((x + (1 << 20)) & 0x1FFFFF) | (((y + (1 << 20)) & 0x1FFFFF) << 21) |
+                 (((z + (1 << 20)) & 0x1FFFFF) << 42)) ^ salt)
+         for x, y, z in changed.tolist()]
+    ranked = sorted(range(len(h)), key=lambda i: h[i])
+    sel = changed if sample == 0 or len(changed) <= sample else changed[ranked[:sample]]
+    d, _ = cKDTree(sel.astype(np.float64)).query(ijk.astype(np.float64),
+                                                 distance_upper_bound=radius + 1e-9)
+    trig_ii = np.isfinite(d)
+    tau = _cfg().tau
+    trig_i = np.array([abs(_tsdf(after, k, tau) - _tsdf(before, k, tau)) > np.float32(2 * V)
+                       for k in ijk])
+    return trig_i, trig_ii, len(changed)
+
+
+def _two_frames(pc, second, first=None, cfg=None):
+    """First frame of the slotted scene, drained; then `second` (points,
+    pose) with nothing evaluated. Returns the layer, the voxel states before
+    and after the second frame and the count of points before it."""
+    mp = oracle.Map(cfg or _cfg())
+    P = oracle.PointSet(mp, pc, _tool(), synth.fibonacci_dirs(32))
+    pts, pose = first if first is not None else _frame(_slotted_scene(), (0.0, 0.0, 0.0), n=6000)
     P.frame(pts, pose)
     P.drain(10 ** 9)
     n0 = len(P)
-    # returns on the right part of the wall only; the sensor moves 2 cm (no motion trigger)
+    before = _voxel_state(mp)
+    P.frame(*second)
+    return P, before, _voxel_state(mp), n0
+
+
+def _side_frame():
     pts, pose = _frame(_slotted_scene(), (0.0, 0.02, 0.0), n=6000, seed=4)
-    side = pts[pts[:, 1] > 0.2]
-    P.frame(side, pose)
+    return pts[pts[:, 1] > 0.2], pose
+
+
+@pytest.mark.parametrize("sample", [0, 256, 16, 2])
+def test_neighbourhood_trigger_against_brute_force(sample):
+    """Sec. 3.5 (ii), sampled as the paper samples it: after a second frame
+    that sees only part of the scene (the sensor moves 2 cm, below the
+    motion trigger), the queued old points are exactly those within r_u = 3v
+    of a drawn changed voxel, or whose TSDF moved by more than 2v; new
+    points are all queued."""
+    P, before, after, n0 = _two_frames(
+        oracle.PointsConfig(trig_tsdf=2 * V, budget=0, trig_sample=sample), _side_frame())
     e = P.export()
-    T = np.asarray(pose, np.float64).reshape(4, 4)
-    world = side.astype(np.float64) @ T[:3, :3].T + T[:3, 3]
-    ij = np.unique(np.floor(world / np.float64(np.float32(V))).astype(np.int64), axis=0)
-    m = _cfg().cube_radius
-    cube = np.array([(x, y, z) for z in range(-m, m + 1) for y in range(-m, m + 1)
-                     for x in range(-m, m + 1)])
-    changed = np.unique((ij[:, None, :] + cube[None]).reshape(-1, 3), axis=0)
-    d, _ = cKDTree(changed.astype(np.float64)).query(e["ijk"][:n0].astype(np.float64),
-                                                      distance_upper_bound=3.0 + 1e-9)
-    voxel_rule = np.isfinite(d)
+    trig_i, trig_ii, nchg = _expected_queue(before, after, e["ijk"][:n0], 2, sample)
     queued = e["queued"][:n0].astype(bool)
-    assert voxel_rule.sum() > 100
-    assert not (voxel_rule & ~queued).any()        # the voxel rule is covered
-    assert (~queued).sum() > 100                   # far points stay unqueued
+    assert np.array_equal(queued, trig_i | trig_ii)
+    assert e["queued"][n0:].all()
+    assert trig_ii.sum() > (100 if sample == 0 or sample > 16 else 10)
+    assert (~queued).sum() > 100                          # far points stay unqueued
+    if sample:
+        assert nchg > sample                                 # the sample is a strict subset
+
+
+def test_brick_rule_covers_the_neighbourhood_trigger():
+    """The brick rule (a touched brick within one brick) queues every point
+    that the unsampled voxel rule does, which queues every point the sampled
+    rule does; all three leave far points alone."""
+    q = {}
+    for name, pc in (("brick", dict(trig_exact=0)), ("all", dict(trig_sample=0)),
+                     ("sampled", dict(trig_sample=256))):
+        P, _, _, n0 = _two_frames(oracle.PointsConfig(trig_tsdf=2 * V, budget=0, **pc),
+                                  _side_frame())
+        q[name] = P.export()["queued"][:n0].astype(bool)
+    assert not (q["all"] & ~q["brick"]).any()
+    assert not (q["sampled"] & ~q["all"]).any()
+    assert q["brick"].sum() > q["all"].sum() > q["sampled"].sum()
+    assert (~q["brick"]).sum() > 100
+
+
+def test_tsdf_trigger_fires_without_the_neighbourhood_trigger():
+    """Sec. 3.5 (i) on its own: the wall moves 6 cm (3 voxels) back and is
+    seen by ten times as many returns, so the TSDF at the old surface voxels
+    rises from about 0 to about 5 cm, more than 2v; with one changed voxel
+    drawn per frame, (ii) misses most of them and (i) alone queues them."""
+    wall0 = _wall(x0=2.0, half=0.3)
+    wall1 = _wall(x0=2.06, half=0.3)
+    first = _frame(wall0, (0.0, 0.0, 0.0), n=2000, seed=1)
+    second = _frame(wall1, (0.0, 0.0, 0.0), n=20000, seed=2)
+    P, before, after, n0 = _two_frames(
+        oracle.PointsConfig(trig_tsdf=2 * V, budget=0, trig_sample=1), second, first=first)
+    e = P.export()
+    trig_i, trig_ii, _ = _expected_queue(before, after, e["ijk"][:n0], 2, 1)
+    assert (trig_i & ~trig_ii).sum() > 50
+    assert np.array_equal(e["queued"][:n0].astype(bool), trig_i | trig_ii)
+
+
+def _pole_and_wall():
+    """A wall at x = 2.0 m and, 26 cm in front of it, a 2 x 8 cm pole."""
+    boxes = np.array([[2.0, -0.3, -0.3, 2.04, 0.3, 0.3], [1.74, -0.04, -0.3, 1.76, 0.04, 0.3]])
+    g = synth.Group(a=np.array([1.9, 0, 0]), b=np.array([1.9, 0, 0]), radius=0.6, boxes=boxes)
+    return synth.Scene([g], *synth._bounds([g]))
+
+
+def test_cleared_band_changes_trigger_on_their_own():
+    """A ray-cleared mark is a change of state: the first frame keeps only
+    the pole's returns, the second only the wall's. The wall's cleared band,
+    stretched to (tau, 4 tau], passes beside the pole and marks voxels there
+    that were never touched, while the wall's cubes stay more than r_u away
+    from the pole. The pole's points are queued by those marks alone, in the
+    brute force and in the oracle; the brick rule reaches them only through
+    the bricks of band samples (two bricks from every cube brick)."""
+    cfg = _cfg()
+    cfg.clear_hi = 4.0
+    cfg.clear_samples = 12
+    fr1 = _frame(_pole_and_wall(), (0.0, 0.0, 0.0), n=6000, seed=5)
+    fr2 = _frame(_pole_and_wall(), (0.0, 0.0, 0.0), n=6000, seed=6)
+    first = (fr1[0][fr1[0][:, 0] < 1.9], fr1[1])
+    second = (fr2[0][fr2[0][:, 0] > 1.9], fr2[1])
+    q = {}
+    for name, pc in (("brick", dict(trig_exact=0)), ("all", dict(trig_sample=0))):
+        P, before, after, n0 = _two_frames(oracle.PointsConfig(trig_tsdf=2 * V, budget=0, **pc),
+                                           second, first=first, cfg=cfg)
+        e = P.export()
+        q[name] = e["queued"][:n0].astype(bool)
+        if name == "all":
+            trig_i, trig_ii, _ = _expected_queue(before, after, e["ijk"][:n0], 2, 0)
+            assert np.array_equal(q[name], trig_i | trig_ii)
+            pole = e["ijk"][:n0, 0] == 87            # every old point is on the pole
+            assert pole.all() and not trig_i.any()
+            chg_w = [k for k, v in after.items() if before.get(k, (0, 0, 0))[:2] != v[:2]]
+            assert min(abs(k[0] - 87) for k in chg_w) > 3   # no S or w change within r_u
+            assert trig_ii.sum() > 10
+    assert not (q["all"] & ~q["brick"]).any()
