@@ -404,11 +404,21 @@ af_status af_soft_best(af_ctx *ctx, const float *d_c, uint64_t n, uint32_t per_p
  *    mean sensor position; fewer than 3 neighbours: not evaluated;
  *  - candidates: n . u > cos_theta_max and u . (q - s) / |q - s| > obs_dot for
  *    some stored viewpoint q; scores as af_score (no candidate: n_c + 1);
- *  - triggers: new points; TSDF at the voxel moved more than trig_tsdf since
- *    the previous frame; a brick within one brick of the point's brick
- *    overlapped by the cube of an accepted return of the frame; a sensor move
- *    of more than trig_move since the motion trigger last fired re-queues the
- *    points labelled AF_BLOCKED;
+ *  - triggers: new points; (i) TSDF at the voxel moved more than trig_tsdf
+ *    since the previous frame; (ii) a changed voxel within r_u of the point
+ *    (|o|^2 <= trig_radius^2 for the integer voxel offset o; r_u = 3v: 3):
+ *    a voxel changes when its stored state (S, w, ray-cleared mark) after the
+ *    frame's scan, weight cap included, differs from its state before; as in
+ *    the paper, only a sample of the changed voxels is tested: when there are
+ *    more than trig_sample (256), the trig_sample with the smallest
+ *    h = mix(key ^ mix(f)), mix splitmix64's output function, key the
+ *    absolute voxel index (x + 2^20) | (y + 2^20) << 21 | (z + 2^20) << 42,
+ *    f the layer's frame number 1, 2, ... (trig_sample = 0 tests all);
+ *    trig_exact = 0 replaces (ii) with the brick rule, a cheaper superset:
+ *    a brick within one brick of the point's brick was touched by the scan
+ *    (a return's cube or cleared-band sample lies in it); (iii) a sensor
+ *    move of more than trig_move since the motion trigger last fired
+ *    re-queues the points labelled AF_BLOCKED;
  *  - evaluation: points with c = w / (w + k_c) < c_min keep their state; the
  *    stored score only decreases (strictly lower replaces it and its
  *    direction); an accessible stored score (< n_c) with a new score >= n_c is
@@ -444,9 +454,14 @@ typedef struct {
     uint32_t c2f_stride;   /* 0: full search; yaw ring of 180: 10 (20 degrees)           */
     uint32_t c2f_half;     /* window half-width in directions; yaw ring: 12 (+-24 deg)   */
     float c2f_radius;      /* neighbour radius, 0.3 m; below 32 voxels                   */
+    int32_t trig_exact;    /* 1: trigger (ii) over changed voxels; 0: the brick rule      */
+    int32_t trig_radius;   /* 3: r_u in voxels, 0..7                                      */
+    uint32_t trig_sample;  /* 256: changed voxels drawn per frame; 0: all of them         */
 } af_points_config;
 
-/* Allocates the layer: 2 KB per pool brick plus 200 B per point of capacity. */
+/* Allocates the layer: 2 KB per pool brick plus 200 B per point of capacity;
+ * with trig_exact another 4.2 KB per pool brick (the touched bricks' state
+ * before each scan). */
 af_status af_points_enable(af_ctx *ctx, const af_points_config *cfg);
 /* Integrate one scan and update the point layer (see above). */
 af_status af_points_frame(af_ctx *ctx, const float *d_xyz, uint32_t n, const float pose[16],
@@ -519,6 +534,18 @@ af_status af_integrate_scan_noalloc(const af_config *cfg, const float *d_xyz, ui
                                     const float pose[16], const int32_t box_min[3],
                                     const uint32_t box_dim[3], uint64_t *d_vox,
                                     uint8_t *d_flags, void *stream);
+
+/*
+ * The library's L2 read-bandwidth probe (no counterpart in the paper: the
+ * denominator of the roofline of the kernels whose working set stays in L2).
+ * Allocates a working set of `bytes` (a multiple of 16 in [1 MiB, 96 MiB],
+ * well inside the L2) on the current device, brings it into L2, then reads it
+ * `reps` times per launch with 16-byte L2-only loads from a persistent grid,
+ * `launches` launches each timed with CUDA events on a stream of its own;
+ * *gbs receives bytes * reps / (fastest launch's time) in GB/s. Synchronous;
+ * frees what it allocated; errors through af_last_error(NULL).
+ */
+af_status af_probe_l2_read(uint64_t bytes, uint32_t reps, uint32_t launches, double *gbs);
 
 /* Last error message of the context (static storage if ctx is NULL). */
 const char *af_last_error(const af_ctx *ctx);

@@ -30,7 +30,7 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
            "af_soft_start", "af_points_enable", "af_points_frame", "af_points_drain",
            "af_points_stats", "af_points_export", "af_integrate_scan_projective",
-           "af_set_score_split", "af_last_error")
+           "af_set_score_split", "af_probe_l2_read", "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
@@ -85,7 +85,8 @@ class _PointsConfig(C.Structure):
                 ("trig_tsdf", C.c_float), ("trig_move", C.c_float), ("budget", C.c_uint32),
                 ("k_c", C.c_float), ("c_min", C.c_float), ("a_decay", C.c_float),
                 ("a_recover", C.c_float), ("ca_min", C.c_float), ("c2f_stride", C.c_uint32),
-                ("c2f_half", C.c_uint32), ("c2f_radius", C.c_float)]
+                ("c2f_half", C.c_uint32), ("c2f_radius", C.c_float), ("trig_exact", C.c_int32),
+                ("trig_radius", C.c_int32), ("trig_sample", C.c_uint32)]
 
 
 class _BatchItem(C.Structure):
@@ -118,6 +119,7 @@ def load(build: bool = True) -> C.CDLL:
             "af_integrate_scan": (C.c_int, [P, P, U32, P, P]),
             "af_integrate_scan_projective": (C.c_int, [P, P, U32, P, U32, P]),
             "af_set_score_split": (C.c_int, [P, C.c_int32]),
+            "af_probe_l2_read": (C.c_int, [C.c_uint64, U32, U32, C.POINTER(C.c_double)]),
             "af_set_tool": (C.c_int, [P, C.POINTER(_Tool), P, U32]),
             "af_score": (C.c_int, [P, P, P, U32, P, P, P]),
             "af_frame_host": (C.c_int, [P, P, U32, P, P, P, U32, P, P, P]),
@@ -243,6 +245,12 @@ class PointsConfig:
     c2f_stride: int = 0
     c2f_half: int = 0
     c2f_radius: float = 0.3
+    # neighbourhood trigger: 1 = a changed voxel within trig_radius voxels
+    # (r_u = 3v) among trig_sample changed voxels drawn per frame (0: all);
+    # 0 = the brick rule (a touched brick next to the point's), a superset
+    trig_exact: int = 1
+    trig_radius: int = 3
+    trig_sample: int = 256
 
     def _c(self) -> _PointsConfig:
         c = _PointsConfig()
@@ -616,6 +624,15 @@ def kernel_offsets(tool: ToolConfig, v: float, u, which: int) -> np.ndarray:
                                  C.byref(cnt)))
     out = out[:cnt.value]
     return out[np.lexsort((out[:, 0], out[:, 1], out[:, 2]))]
+
+
+def probe_l2_read(nbytes: int = 32 << 20, reps: int = 40, launches: int = 20) -> float:
+    """af_probe_l2_read: the L2 read bandwidth (GB/s) of the current device,
+    measured by the library's own kernel on an L2-resident working set."""
+    lib = load()
+    out = C.c_double()
+    _check(lib.af_probe_l2_read(nbytes, reps, launches, C.byref(out)))
+    return float(out.value)
 
 
 def arm_offsets(v: float, tau: float, u) -> np.ndarray:

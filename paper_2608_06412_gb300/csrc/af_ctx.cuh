@@ -47,9 +47,14 @@ struct af_ctx {
   af::PtState* d_pst = nullptr;
   float4* d_pviews = nullptr;
   unsigned long long* d_pnew = nullptr;
-  uint32_t* d_pchg = nullptr;
   uint32_t* d_pnear = nullptr;
-  uint32_t* d_pchglist = nullptr;
+  unsigned long long* d_psnapw = nullptr;  // trigger (ii): dirty bricks before the scan
+  uint32_t* d_psnapc = nullptr;
+  uint32_t* d_pchgmask = nullptr;
+  uint32_t* d_phist = nullptr;
+  af::PtSample* d_psamp = nullptr;
+  uint32_t pts_frames = 0;       // af_points_frame calls (the draw's salt)
+  bool pts_snapshot = false;     // af_integrate_scan copies the dirty bricks after allocation
   uint32_t* d_psel = nullptr;
   uint32_t* d_pblock = nullptr;
   af::PtCounters* d_pcount = nullptr;

@@ -47,6 +47,7 @@ cudaError_t launch_soft_best(const float* c, uint64_t n, uint32_t per_point, con
 cudaError_t launch_soft_start(const uint8_t* label, const int16_t* best, uint32_t m,
                               const float* dirs, int G, float* u0, int num_sms,
                               cudaStream_t stream);
+cudaError_t launch_pts_snapshot(af_ctx* ctx, cudaStream_t stream);
 }  // namespace af
 
 using af::MapView;
@@ -303,9 +304,9 @@ static void free_all(af_ctx* c) {
   cudaFree(c->d_table);
   cudaFree(c->d_img);
   for (void* p : {(void*)c->d_pid, (void*)c->d_pst, (void*)c->d_pviews, (void*)c->d_pnew,
-                  (void*)c->d_pchg, (void*)c->d_pnear, (void*)c->d_pchglist, (void*)c->d_psel,
-                  (void*)c->d_pblock, (void*)c->d_pcount, (void*)c->d_pnnoff, (void*)c->d_pc2f,
-                  (void*)c->d_psnap})
+                  (void*)c->d_pnear, (void*)c->d_psnapw, (void*)c->d_psnapc, (void*)c->d_pchgmask,
+                  (void*)c->d_phist, (void*)c->d_psamp, (void*)c->d_psel, (void*)c->d_pblock,
+                  (void*)c->d_pcount, (void*)c->d_pnnoff, (void*)c->d_pc2f, (void*)c->d_psnap})
     cudaFree(p);
   cudaFreeHost(c->h_status);
 }
@@ -459,6 +460,9 @@ extern "C" af_status af_integrate_scan(af_ctx* ctx, const float* d_xyz, uint32_t
   cudaStream_t s = (cudaStream_t)stream;
   const MapView& M = ctx->M;
   AF_CUDA(ctx, timed(ctx, 0, s, [&] { return af::launch_alloc(M, d_xyz, n, pose, ctx->d_ret, ctx->frame, s); }));
+  // the point layer's neighbourhood trigger compares the touched bricks
+  // after the scan with their state before it
+  if (ctx->pts_snapshot) AF_CUDA(ctx, af::launch_pts_snapshot(ctx, s));
   if (n > 0)
     AF_CUDA(ctx, timed(ctx, 1, s, [&] { return af::launch_cube(M, n, pose, ctx->d_ret, ctx->frame, s); }));
   AF_CUDA(ctx, timed(ctx, 2, s, [&] { return af::launch_bitview(M, ctx->num_sms, s); }));

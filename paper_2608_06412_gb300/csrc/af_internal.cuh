@@ -138,14 +138,19 @@ __host__ __device__ inline uint64_t pack_brick(uint32_t bx, uint32_t by, uint32_
   return (uint64_t)bx | ((uint64_t)by << 21) | ((uint64_t)bz << 42);
 }
 
-__device__ inline uint32_t hash_slot(uint64_t key, uint32_t mask) {
-  // splitmix64 finaliser
+// splitmix64's output function (Steele, Lea, Flood 2014): a bijection of
+// 64-bit words.
+__host__ __device__ inline uint64_t mix64(uint64_t key) {
   key ^= key >> 30;
   key *= 0xbf58476d1ce4e5b9ull;
   key ^= key >> 27;
   key *= 0x94d049bb133111ebull;
   key ^= key >> 31;
-  return (uint32_t)key & mask;
+  return key;
+}
+
+__device__ inline uint32_t hash_slot(uint64_t key, uint32_t mask) {
+  return (uint32_t)mix64(key) & mask;
 }
 
 // One 16-byte slot read: key, pool index, stamp.
@@ -251,12 +256,22 @@ struct PtState {
 };
 
 struct PtCounters {
-  uint32_t count;  // points
-  uint32_t nnew;   // points new in this frame
-  uint32_t nchg;   // bricks overlapped by the frame's cubes
-  uint32_t nsel;   // points selected for evaluation
-  uint32_t evals;  // evaluations of the last call
-  uint32_t pad[3];
+  uint32_t count;     // points
+  uint32_t nnew;      // points new in this frame
+  uint32_t nchanged;  // voxels whose stored state the frame's scan changed
+  uint32_t nsnap;     // bricks whose state was copied before the frame's scan
+  uint32_t nsel;      // points selected for evaluation
+  uint32_t evals;     // evaluations of the last call
+  uint32_t pad[2];
+};
+
+// The draw of changed voxels for the neighbourhood trigger: a radix
+// selection of the `trig_sample` smallest hashes, 16 bits per pass.
+struct PtSample {
+  unsigned long long prefix;  // high bits of the selected bound found so far
+  unsigned long long t;       // the largest hash drawn (all ones: every changed voxel)
+  uint32_t below;             // changed voxels known to lie below the prefix's range
+  uint32_t done;              // 1 once t is final
 };
 
 // Parameters of the layer as the kernels read them.
@@ -265,9 +280,16 @@ struct PtView {
   float4* views;         // capacity * 8
   int32_t* pid;          // point id per voxel of every pool brick, -1 none, -2 being created
   unsigned long long* newkeys;
-  uint32_t* chg;         // per pool brick: stamp of the last frame whose cubes overlap it
-  uint32_t* near;        // per pool brick: stamp of the last frame with such a brick next to it
-  uint32_t* chglist;
+  uint32_t* near;        // per pool brick: stamp of the last frame with a touched brick next to it
+  unsigned long long* snapw;  // per dirty brick of the frame: its 512 voxel words before the scan
+  uint32_t* snapc;            // ... and its 16 cleared-mark words
+  uint32_t* chgmask;          // per dirty brick: 512 bits, voxels whose state changed
+  uint32_t* hist;             // 65536 bins of the draw's radix selection
+  PtSample* samp;
+  int trig_exact;             // 1: changed voxels within trig_radius; 0: touched bricks
+  int trig_radius;
+  uint32_t trig_sample;       // changed voxels drawn per frame (0: all)
+  unsigned long long salt;    // mix64(frame number of the layer)
   uint32_t* sel;
   uint32_t* blocksum;
   PtCounters* C;

@@ -6,14 +6,21 @@
 // accessibility confidence a.
 //
 // Per frame, after the scan's integration, on the caller's stream:
+//  k_pts_snapshot (inside the scan's integration, after brick allocation)
+//                 the state of every brick the scan touches, before the scan
 //  k_pts_mark     one thread per return: new point voxels (claimed in the
-//                 per-brick point-id table), bricks overlapped by the cubes
-//  k_pts_near     bricks next to those (the re-evaluation neighbourhood)
+//                 per-brick point-id table)
+//  k_pts_near     (brick rule) bricks next to the scan's touched bricks
 //  k_pts_create   new points numbered by key order within the frame, so ids
 //                 never depend on thread timing
 //  k_pts_views    once per (point, scan): sensor sum and stored viewpoints
-//  k_pts_trigger  one thread per point: TSDF change, neighbourhood change,
-//                 sensor motion for blocked points
+//  k_pts_diff     per touched brick: the voxels whose stored state changed
+//  k_pts_hist / k_pts_pick
+//                 the draw: radix selection, 16 bits per pass, of the
+//                 trig_sample smallest hashes of the changed voxels
+//  k_pts_scatter  every drawn changed voxel queues the points within r_u
+//  k_pts_trigger  one thread per point: TSDF change, brick rule, sensor
+//                 motion for blocked points
 //  k_pts_count / k_pts_scan / k_pts_select
 //                 the first `budget` queued ids in id order
 //  k_pts_snap     (coarse-to-fine search only) the stored best directions
@@ -82,39 +89,29 @@ __device__ inline bool return_voxel(const MapView& M, const float4* ret, uint32_
   return true;
 }
 
-// One thread per (return, brick of its cube): the brick is stamped as
-// changed; the thread whose brick holds the return also claims its voxel as
-// a new point if it has none.
+// One thread per return: the voxel of an accepted return becomes a new
+// point if it has none (claimed with -2 until k_pts_create numbers it).
 __global__ void __launch_bounds__(256) k_pts_mark(MapView M, const float4* __restrict__ ret,
-                                                  uint32_t n, PtView V, uint32_t frame) {
-  const int ba = (2 * M.m + 7) / 8 + 1;  // bricks a cube edge can span
-  const int per = ba * ba * ba;
-  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t k = e / per;
-  const int j = (int)(e % per);
+                                                  uint32_t n, PtView V) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int r[3];
   if (!return_voxel(M, ret, k, r)) return;
-  // brick j of the cube (inside the box for an accepted return)
-  const int bx = ((r[0] - M.m) >> 3) + j % ba, by = ((r[1] - M.m) >> 3) + (j / ba) % ba,
-            bz = ((r[2] - M.m) >> 3) + j / (ba * ba);
-  if (bx > (r[0] + M.m) >> 3 || by > (r[1] + M.m) >> 3 || bz > (r[2] + M.m) >> 3) return;
-  const uint32_t b = lookup_brick(M, pack_brick(bx, by, bz));
+  const uint32_t b = lookup_brick(M, pack_brick(r[0] >> 3, r[1] >> 3, r[2] >> 3));
   if (b == kNoBlock) return;
-  if (atomicExch(V.chg + b, frame) != frame) V.chglist[atomicAdd(&V.C->nchg, 1u)] = b;
-  if (bx == r[0] >> 3 && by == r[1] >> 3 && bz == r[2] >> 3) {
-    int32_t* slot = V.pid + (size_t)b * kBrickVox + vox_slot(r[0], r[1], r[2]);
-    if (*slot == -1 && atomicCAS(slot, -1, -2) == -1)
-      V.newkeys[atomicAdd(&V.C->nnew, 1u)] = rel_key(r[0], r[1], r[2]);
-  }
+  int32_t* slot = V.pid + (size_t)b * kBrickVox + vox_slot(r[0], r[1], r[2]);
+  if (*slot == -1 && atomicCAS(slot, -1, -2) == -1)
+    V.newkeys[atomicAdd(&V.C->nnew, 1u)] = rel_key(r[0], r[1], r[2]);
 }
 
-// One thread per (changed brick, neighbour of its 3 x 3 x 3 block).
+// Brick rule: one thread per (brick touched by the scan, neighbour of its
+// 3 x 3 x 3 block). The scan's dirty list holds exactly the bricks that its
+// cubes and cleared-band samples touch.
 __global__ void __launch_bounds__(256) k_pts_near(MapView M, PtView V, uint32_t frame) {
-  const uint32_t count = V.C->nchg * 27u;
+  const uint32_t count = __ldcg(&M.ctl->dirty_count) * 27u;
   const int BX = M.dim_vox[0] >> 3, BY = M.dim_vox[1] >> 3, BZ = M.dim_vox[2] >> 3;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const uint64_t key = M.bkey[V.chglist[i / 27u]];
+    const uint64_t key = M.bkey[M.dirty[i / 27u]];
     const int o = (int)(i % 27u);
     const int x = (int)(key & 0x1FFFFF) + o % 3 - 1, y = (int)((key >> 21) & 0x1FFFFF) + (o / 3) % 3 - 1,
               z = (int)(key >> 42) + o / 9 - 1;
@@ -122,6 +119,166 @@ __global__ void __launch_bounds__(256) k_pts_near(MapView M, PtView V, uint32_t 
       continue;
     const uint32_t b = lookup_brick(M, pack_brick(x, y, z));
     if (b != kNoBlock) V.near[b] = frame;
+  }
+}
+
+// ---- trigger (ii): changed voxels near a point (Sec. 3.5) ----
+
+// Copies the voxel words and cleared marks of every brick the scan touches;
+// runs after brick allocation, which lists them all, and before integration.
+__global__ void __launch_bounds__(512) k_pts_snapshot(MapView M, PtView V) {
+  const uint32_t count = __ldcg(&M.ctl->dirty_count);
+  if (blockIdx.x == 0 && threadIdx.x == 0) V.C->nsnap = count;
+  const int l = threadIdx.x;
+  for (uint32_t d = blockIdx.x; d < count; d += gridDim.x) {
+    const uint32_t blk = M.dirty[d];
+    V.snapw[(size_t)d * kBrickVox + l] = __ldcg(M.vox + (size_t)blk * kBrickVox + l);
+    if (l < 16) V.snapc[(size_t)d * 16 + l] = __ldcg(M.cleared + (size_t)blk * 16 + l);
+  }
+}
+
+// Absolute voxel of the box-relative voxel (x, y, z) packed as the draw's key.
+__device__ inline unsigned long long draw_key(const MapView& M, int x, int y, int z) {
+  return ((unsigned long long)(uint32_t)(x + M.dom_vox[0] + (1 << 20)) & 0x1FFFFFull) |
+         (((unsigned long long)(uint32_t)(y + M.dom_vox[1] + (1 << 20)) & 0x1FFFFFull) << 21) |
+         (((unsigned long long)(uint32_t)(z + M.dom_vox[2] + (1 << 20)) & 0x1FFFFFull) << 42);
+}
+
+// Box-relative voxel l of brick blk.
+__device__ inline void brick_voxel(const MapView& M, uint32_t blk, int l, int* x, int* y, int* z) {
+  const uint64_t key = M.bkey[blk];
+  *x = (int)(key & 0x1FFFFF) * 8 + (l & 7);
+  *y = (int)((key >> 21) & 0x1FFFFF) * 8 + ((l >> 3) & 7);
+  *z = (int)(key >> 42) * 8 + (l >> 6);
+}
+
+// Per touched brick (after the weight cap): voxels whose word or cleared mark
+// differs from the snapshot, as a 512-bit mask, and their count.
+__global__ void __launch_bounds__(512) k_pts_diff(MapView M, PtView V) {
+  const uint32_t count = __ldcg(&M.ctl->dirty_count), nsnap = V.C->nsnap;
+  if (count > nsnap && blockIdx.x == 0 && threadIdx.x == 0)
+    latch_status(M.ctl, kStatusCapacity);  // a brick missed by the snapshot: never expected
+  const int l = threadIdx.x, lane = l & 31, wi = l >> 5;
+  const uint32_t nd = min(count, nsnap);
+  for (uint32_t d = blockIdx.x; d < nd; d += gridDim.x) {
+    const uint32_t blk = M.dirty[d];
+    const bool cl_now = (__ldcg(M.cleared + (size_t)blk * 16 + wi) >> lane) & 1u;
+    const bool cl_then = (V.snapc[(size_t)d * 16 + wi] >> lane) & 1u;
+    const bool ch = __ldcg(M.vox + (size_t)blk * kBrickVox + l) != V.snapw[(size_t)d * kBrickVox + l] ||
+                    cl_now != cl_then;
+    const unsigned b = __ballot_sync(0xffffffffu, ch);
+    if (lane == 0) {
+      V.chgmask[(size_t)d * 16 + wi] = b;
+      if (b) atomicAdd(&V.C->nchanged, (unsigned)__popc(b));
+    }
+  }
+}
+
+// One pass of the draw: histogram of the 16-bit digit at `shift` of the
+// hashes of the changed voxels whose higher bits equal the prefix so far.
+__global__ void __launch_bounds__(512) k_pts_hist(MapView M, PtView V, int pass) {
+  const uint32_t k = V.trig_sample;
+  if (V.samp->done || k == 0 || V.C->nchanged <= k) return;
+  const unsigned long long prefix = V.samp->prefix;
+  const int shift = 48 - 16 * pass;
+  const int l = threadIdx.x, lane = l & 31, wi = l >> 5;
+  const uint32_t nd = min(__ldcg(&M.ctl->dirty_count), V.C->nsnap);
+  for (uint32_t d = blockIdx.x; d < nd; d += gridDim.x) {
+    if (!((V.chgmask[(size_t)d * 16 + wi] >> lane) & 1u)) continue;
+    int x, y, z;
+    brick_voxel(M, M.dirty[d], l, &x, &y, &z);
+    const unsigned long long h = mix64(draw_key(M, x, y, z) ^ V.salt);
+    if (pass > 0 && (h >> (shift + 16)) != prefix) continue;
+    atomicAdd(V.hist + ((h >> shift) & 0xFFFFull), 1u);
+  }
+}
+
+// Picks the digit of this pass (one CTA of 1024 threads, 64 bins each) and
+// clears the histogram for the next pass. After the fourth pass the prefix
+// is the trig_sample-th smallest hash, the largest one drawn (hashes of
+// distinct voxels never tie: mix64 is a bijection).
+__global__ void __launch_bounds__(1024) k_pts_pick(PtView V, int pass) {
+  __shared__ uint32_t part[1024];
+  PtSample* S = V.samp;
+  const int tid = threadIdx.x;
+  const uint32_t k = V.trig_sample;
+  const bool all = k == 0 || V.C->nchanged <= k;
+  if (!S->done && all) {
+    if (tid == 0) {
+      S->t = ~0ull;
+      S->done = 1;
+    }
+  } else if (!S->done) {
+    const uint32_t need = k - S->below;
+    uint32_t sum = 0;
+    for (int j = 0; j < 64; ++j) sum += V.hist[tid * 64 + j];
+    part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan
+      const uint32_t t = tid >= off ? part[tid - off] : 0u;
+      __syncthreads();
+      part[tid] += t;
+      __syncthreads();
+    }
+    const uint32_t excl = part[tid] - sum;
+    if (excl < need && need <= part[tid]) {
+      uint32_t c = excl;
+      for (int j = 0; j < 64; ++j) {
+        const uint32_t hv = V.hist[tid * 64 + j];
+        if (c + hv >= need) {
+          S->below += c;
+          S->prefix = (S->prefix << 16) | (unsigned long long)(tid * 64 + j);
+          if (pass == 3) {
+            S->t = S->prefix;
+            S->done = 1;
+          }
+          break;
+        }
+        c += hv;
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < 64; ++j) V.hist[tid * 64 + j] = 0u;
+}
+
+// Every drawn changed voxel (hash <= t) queues the points within r_u of it;
+// one CTA per touched brick, the pool indices of its 27 neighbours looked up
+// once. r_u < 8 voxels, so the ball stays inside those bricks.
+__global__ void __launch_bounds__(512) k_pts_scatter(MapView M, PtView V) {
+  __shared__ uint32_t s_nb[27];
+  const unsigned long long t = V.samp->t;
+  const int R = V.trig_radius, R2 = R * R;
+  const int l = threadIdx.x, lane = l & 31, wi = l >> 5;
+  const int BX = M.dim_vox[0] >> 3, BY = M.dim_vox[1] >> 3, BZ = M.dim_vox[2] >> 3;
+  const uint32_t nd = min(__ldcg(&M.ctl->dirty_count), V.C->nsnap);
+  for (uint32_t d = blockIdx.x; d < nd; d += gridDim.x) {
+    const uint32_t blk = M.dirty[d];
+    const uint64_t key = M.bkey[blk];
+    const int bx = (int)(key & 0x1FFFFF), by = (int)((key >> 21) & 0x1FFFFF), bz = (int)(key >> 42);
+    __syncthreads();  // s_nb of the previous brick is no longer read
+    if (l < 27) {
+      const int x = bx + l % 3 - 1, y = by + (l / 3) % 3 - 1, z = bz + l / 9 - 1;
+      s_nb[l] = ((unsigned)x < (unsigned)BX && (unsigned)y < (unsigned)BY && (unsigned)z < (unsigned)BZ)
+                    ? lookup_brick(M, pack_brick(x, y, z))
+                    : kNoBlock;
+    }
+    __syncthreads();
+    if (!((V.chgmask[(size_t)d * 16 + wi] >> lane) & 1u)) continue;
+    int x, y, z;
+    brick_voxel(M, blk, l, &x, &y, &z);
+    if (mix64(draw_key(M, x, y, z) ^ V.salt) > t) continue;
+    for (int dz = -R; dz <= R; ++dz)
+      for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx) {
+          if (dx * dx + dy * dy + dz * dz > R2) continue;
+          const int nx = x + dx, ny = y + dy, nz = z + dz;
+          if (!box_rel(M, nx, ny, nz)) continue;
+          const uint32_t b = s_nb[((nx >> 3) - bx + 1) + 3 * (((ny >> 3) - by + 1) + 3 * ((nz >> 3) - bz + 1))];
+          if (b == kNoBlock) continue;
+          const int32_t id = V.pid[(size_t)b * kBrickVox + vox_slot(nx, ny, nz)];
+          if (id >= 0) V.st[id].queued = 1;
+        }
   }
 }
 
@@ -219,7 +376,7 @@ __global__ void __launch_bounds__(256) k_pts_trigger(MapView M, PtView V, uint32
     bool q = s->queued != 0;
     if (fabsf(__fsub_rn(cur, s->last_tsdf)) > V.trig_tsdf) q = true;
     s->last_tsdf = cur;
-    if (V.near[s->blk] == frame) q = true;
+    if (!V.trig_exact && V.near[s->blk] == frame) q = true;  // (ii) by the brick rule
     if (moved && s->label == 2) q = true;
     s->queued = q ? 1 : 0;
   }
@@ -640,9 +797,16 @@ PtView pt_view(af_ctx* ctx) {
   V.views = ctx->d_pviews;
   V.pid = ctx->d_pid;
   V.newkeys = ctx->d_pnew;
-  V.chg = ctx->d_pchg;
   V.near = ctx->d_pnear;
-  V.chglist = ctx->d_pchglist;
+  V.snapw = ctx->d_psnapw;
+  V.snapc = ctx->d_psnapc;
+  V.chgmask = ctx->d_pchgmask;
+  V.hist = ctx->d_phist;
+  V.samp = ctx->d_psamp;
+  V.trig_exact = c.trig_exact;
+  V.trig_radius = c.trig_radius;
+  V.trig_sample = c.trig_sample;
+  V.salt = mix64((uint64_t)ctx->pts_frames);
   V.sel = ctx->d_psel;
   V.blocksum = ctx->d_pblock;
   V.C = ctx->d_pcount;
@@ -682,6 +846,12 @@ af_status select_and_eval(af_ctx* ctx, uint32_t budget, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_pts_snapshot(af_ctx* ctx, cudaStream_t s) {
+  k_pts_snapshot<<<(unsigned)ctx->num_sms * 4, 512, 0, s>>>(ctx->M, pt_view(ctx));
+  return cudaGetLastError();
+}
+
 }  // namespace af
 
 using af::MapView;
@@ -695,7 +865,9 @@ extern "C" af_status af_points_enable(af_ctx* ctx, const af_points_config* cfg) 
   for (float x : f)
     if (!std::isfinite(x)) return af::pfail(ctx, AF_ERR_INVALID_ARG, "af_points_enable: non-finite parameter");
   if (c.capacity < 1 || c.capacity > (1u << 30) || c.k_nn < 3 || c.k_nn > 343 || c.nn_radius < 1 ||
-      c.nn_radius > 3 || c.max_views > 8 || !(c.k_c > 0.f) || c.view_min_dist < 0.f)
+      c.nn_radius > 3 || c.max_views > 8 || !(c.k_c > 0.f) || c.view_min_dist < 0.f ||
+      (c.trig_exact != 0 && c.trig_exact != 1) || c.trig_radius < 0 || c.trig_radius > 7 ||
+      c.trig_sample > (1u << 24))
     return af::pfail(ctx, AF_ERR_INVALID_ARG, "af_points_enable: parameter out of range");
   // coarse-to-fine ball: offsets o != 0 with |o|^2 v^2 <= radius^2 in double
   std::vector<int4> ball;
@@ -735,9 +907,14 @@ extern "C" af_status af_points_enable(af_ctx* ctx, const af_points_config* cfg) 
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_pst, P * sizeof(af::PtState), 0);
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_pviews, P * 8 * sizeof(float4), 0);
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_pnew, R * 8, 0);
-  if (e == cudaSuccess) e = alloc((void**)&ctx->d_pchg, B * 4, 0);
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_pnear, B * 4, 0);
-  if (e == cudaSuccess) e = alloc((void**)&ctx->d_pchglist, B * 4, 0);
+  if (c.trig_exact) {  // the dirty list holds at most every pool brick
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_psnapw, B * af::kBrickVox * 8, 0);
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_psnapc, B * 16 * 4, 0);
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_pchgmask, B * 16 * 4, 0);
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_phist, 65536 * 4, 0);
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_psamp, sizeof(af::PtSample), 0);
+  }
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_psel, P * 4, 0);
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_pblock, nblocks * 4, 0);
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_pcount, sizeof(af::PtCounters), 0);
@@ -777,23 +954,34 @@ extern "C" af_status af_points_frame(af_ctx* ctx, const float* d_xyz, uint32_t n
   if (!ctx) return af::pfail(ctx, AF_ERR_INVALID_ARG, "af_points_frame: NULL context");
   if (!ctx->pts_on) return af::pfail(ctx, AF_ERR_STATE, "af_points_frame: call af_points_enable first");
   if (!ctx->has_tool) return af::pfail(ctx, AF_ERR_STATE, "af_points_frame: call af_set_tool first");
+  const bool exact = ctx->pcfg.trig_exact != 0;
+  ctx->pts_snapshot = exact;
   af_status st = af_integrate_scan(ctx, d_xyz, n, pose, stream);
+  ctx->pts_snapshot = false;
   if (st != AF_OK) return st;
+  ctx->pts_frames += 1;
   cudaStream_t s = (cudaStream_t)stream;
   const MapView& M = ctx->M;
   const af::PtView V = af::pt_view(ctx);
   const uint32_t frame = ctx->frame;
-  PT_CUDA(ctx, cudaMemsetAsync(&ctx->d_pcount->nnew, 0, 2 * sizeof(uint32_t), s));  // nnew, nchg
-  if (n > 0) {
-    const int ba = (2 * M.m + 7) / 8 + 1;
-    const uint64_t threads = (uint64_t)n * (uint64_t)(ba * ba * ba);
-    af::k_pts_mark<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(M, ctx->d_ret, n, V, frame);
-  }
-  af::k_pts_near<<<af::grid_cap((size_t)M.pool_blocks * 27, 256, ctx->num_sms, 8), 256, 0, s>>>(M, V, frame);
+  PT_CUDA(ctx, cudaMemsetAsync(&ctx->d_pcount->nnew, 0, 2 * sizeof(uint32_t), s));  // nnew, nchanged
+  if (n > 0) af::k_pts_mark<<<(n + 255) / 256, 256, 0, s>>>(M, ctx->d_ret, n, V);
+  if (!exact)
+    af::k_pts_near<<<af::grid_cap((size_t)M.pool_blocks * 27, 256, ctx->num_sms, 8), 256, 0, s>>>(M, V, frame);
   af::k_pts_create<<<af::grid_cap(ctx->cfg.max_returns, 256, ctx->num_sms, 8), 256, 0, s>>>(M, V);
   af::k_pts_commit<<<1, 1, 0, s>>>(V);
   const float q[3] = {pose[3], pose[7], pose[11]};
   if (n > 0) af::k_pts_views<<<(n + 255) / 256, 256, 0, s>>>(M, ctx->d_ret, n, V, q[0], q[1], q[2], frame);
+  if (exact) {  // trigger (ii): the changed voxels, their draw, the points near the drawn ones
+    const unsigned grid = (unsigned)ctx->num_sms * 4;
+    PT_CUDA(ctx, cudaMemsetAsync(ctx->d_psamp, 0, sizeof(af::PtSample), s));
+    af::k_pts_diff<<<grid, 512, 0, s>>>(M, V);
+    for (int pass = 0; pass < 4; ++pass) {
+      af::k_pts_hist<<<grid, 512, 0, s>>>(M, V, pass);
+      af::k_pts_pick<<<1, 1024, 0, s>>>(V, pass);
+    }
+    af::k_pts_scatter<<<grid, 512, 0, s>>>(M, V);
+  }
   // sensor motion since the motion trigger last fired
   int moved = 0;
   if (ctx->have_q_last) {
