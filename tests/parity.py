@@ -55,3 +55,36 @@ def assert_maps_equal(g: dict, o: dict):
 def to_dev(a, dtype=None):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def near_returns(frames, centres, radius):
+    """Per frame (sensor-frame returns, pose), the returns within `radius` of
+    any centre (world frame): every return that can affect what is sampled
+    there, in stream order."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.asarray(centres, np.float64))
+    out = []
+    for fr in frames:
+        d, _ = tree.query(fr.world, distance_upper_bound=radius)
+        sel = np.isfinite(d)
+        out.append((np.ascontiguousarray(fr.pts[sel]), np.asarray(fr.pose)))
+    return out
+
+
+def oracle_cluster_labels(job):
+    """Oracle labels and best directions of a point cluster, from the returns
+    near it (a process-pool job: config, tool, directions, scans, points and
+    normals as plain values)."""
+    cfg, tool, dirs, scans, pts, nrm = job
+    om = oracle.Map(cfg)
+    for xyz, pose in scans:
+        if len(xyz):
+            om.integrate(xyz, pose)
+    return om.score(tool, dirs, pts, nrm)
+
+
+def stream_frames(job):
+    """Frames 0 .. count - 1 of a workload's stream (a process-pool job)."""
+    from paper_2608_06412_gb300 import workload
+    W, count = job
+    return [workload.pine_frame(W, f) for f in range(count)]

@@ -3,7 +3,8 @@ the same seeded inputs: seeds bit-exact; C and the hard clearance within
 1e-5 m; the adjoint within 1e-3 of the oracle's gradient; the adjoint against
 central finite differences of the GPU's own single-precision C (h = 1e-4) on
 every pair where the oracle shows the difference interval free of the kinks
-of trilinear interpolation; the autograd Function equal to the adjoint;
+of trilinear interpolation, per pair within 1e-3 relative plus what single
+precision lets the difference resolve (measured against the oracle); the autograd Function equal to the adjoint;
 refinement and the per-point best exactly self-consistent and within
 tolerance of the oracle's trajectories; views rebuilt after a new scan."""
 import numpy as np
@@ -121,11 +122,24 @@ def test_adjoint_matches_central_differences(scene):
         ofd = (ocp - ocm) / width
         smooth = ok & (np.abs(ofd - ref_g[:, k]) <= 1e-4 * np.maximum(np.abs(ref_g[:, k]), 1e-2))
         assert smooth.mean() > 0.8
-        d = fd[smooth] - grad[smooth].astype(np.float64)
-        rel = np.linalg.norm(d) / np.linalg.norm(grad[smooth].astype(np.float64))
+        gs = grad[smooth].astype(np.float64)
+        d = fd[smooth] - gs
+        rel = np.linalg.norm(d) / np.linalg.norm(gs)
         assert rel <= 1e-3, (k, rel)
-        per = np.abs(d) / np.maximum(np.abs(grad[smooth]), 1e-2)
-        assert np.percentile(per, 99) <= 1e-2, (k, np.percentile(per, 99))
+        # per pair: rel. err <= 1e-3 up to what single precision lets a central
+        # difference resolve -- the share of the kernel's own rounding of C at
+        # the two ends (|C_fp32 - C_fp64| / width, against the oracle) and the
+        # double-precision difference's distance from the analytic gradient
+        noise = (np.abs(cp.astype(np.float64) - ocp) + np.abs(cm.astype(np.float64) - ocm)) / width
+        resid = np.abs(ofd - ref_g[:, k])
+        bound = 1e-3 * np.abs(gs) + noise[smooth] + resid[smooth]
+        worst = np.argmax(np.abs(d) - bound)
+        assert (np.abs(d) <= bound).all(), (k, d[worst], gs[worst], noise[smooth][worst])
+        # where the difference itself is good to 1e-3 (|grad| >= 1e3 x its
+        # error), the two agree to the bar plus that error
+        big = 1e-3 * np.abs(gs) >= noise[smooth] + resid[smooth]
+        assert big.sum() >= 50, (k, big.sum())
+        assert (np.abs(d[big]) <= 2e-3 * np.abs(gs[big])).all(), k
         smooth_total += smooth.sum()
     assert smooth_total > 0.8 * 3 * ok.sum()
 
