@@ -24,6 +24,8 @@ Other lines, each with the oracle timed beside it on a bounded sample:
   --soft       the differentiable step: 100k points, 20 ascent steps each;
   --points     the stateful layer (triggers, budget, PCA normals, c and a);
   --large      the 40 x 40 m map at 1 cm: 3,000 frames, then every surface point;
+  --large --batched  its eight pine orbits as eight scenes ticked together,
+               against the per-scene path;
 and variants of the default line: --projective, --clamp-signed, --ring
 (the paper's yaw ring; with --points also --c2f), --score-split B.
 """
@@ -1207,9 +1209,133 @@ def run_points(args, local):
     return out
 
 
+LARGE_SCENE_CAPS = dict(hash_capacity=1 << 21, pool_blocks=1 << 20, max_returns=1 << 15,
+                        max_points=1 << 15)
+
+
+def run_large_batched(args, local):
+    """The large map's workload in the batched form: its eight pine orbits
+    (375 frames each, v = 1 cm, tau = 4 cm, K = 256 of G = 512, 1.5 m
+    corridor) as eight scenes, each a 14 x 14 m map box around its pine (the
+    returns whose cubes leave it are dropped, as at any box edge). A tick
+    integrates one frame of every scene and scores that frame's surface
+    points; the same ticks then run through the per-scene path
+    (af_integrate_scan + af_score per scene). Labels and best directions of
+    every tick are compared between the two paths."""
+    import hashlib
+    from paper_2608_06412_gb300 import synth, workload
+    W = workload.large_map()
+    p = W.params
+    frames = workload.large_frames(W, range(p["frames"]))   # spawned workers, before CUDA
+    import torch
+    from paper_2608_06412_gb300 import af
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    npine, per = p["pines"], p["frames_per_pine"]
+    centres = synth.pine_positions(p["seed"], npine, p["ground_half"])
+    scenes = []
+    for c in centres:
+        lo = np.array([c[0] - 7.0, c[1] - 7.0, -0.3])
+        hi = np.array([c[0] + 7.0, c[1] + 7.0, 12.6])
+        dmin, db = synth.domain_bricks(lo, hi, p["v"], margin=0.0)
+        scenes.append(workload.Workload(f"{W.name}_pine", p, W.scene, dmin, db, W.dirs))
+    ticks = min(per, args.steps) if args.steps < per else per
+    warm = 3
+    dx = [[torch.from_numpy(frames[i * per + t][0]).to(dev) for t in range(ticks)]
+          for i in range(npine)]
+    dp = [[torch.from_numpy(frames[i * per + t][3]).to(dev) for t in range(ticks)]
+          for i in range(npine)]
+    dn = [[torch.from_numpy(frames[i * per + t][4]).to(dev) for t in range(ticks)]
+          for i in range(npine)]
+    mmax = max(len(frames[k][3]) for k in range(len(frames)))
+    outs = [(torch.empty(mmax, dtype=torch.uint8, device=dev),
+             torch.empty(mmax, dtype=torch.int16, device=dev)) for _ in range(npine)]
+    stream = torch.cuda.current_stream()
+
+    def run(batched: bool):
+        maps = [af.Map(S.af_config(**LARGE_SCENE_CAPS)) for S in scenes]
+        for m in maps:
+            m.set_tool(W.af_tool(), W.dirs)
+        batch = af.Batch(maps) if batched else None
+        h = hashlib.sha256()
+        ms, t0 = [], None
+        for t in range(ticks):
+            if t == warm:
+                torch.cuda.synchronize()
+                t0 = sum(m.stats()["tests"] for m in maps)
+            items = []
+            for i in range(npine):
+                n = len(dp[i][t])
+                items.append((dx[i][t], frames[i * per + t][1], dp[i][t], dn[i][t],
+                              outs[i][0][:n], outs[i][1][:n]))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if batched:
+                batch.tick(items)
+            else:
+                for m, (xyz, pose, pp, nn, lab, best) in zip(maps, items):
+                    m.integrate_scan(xyz, pose)
+                    m.score(pp, nn, lab, best)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if t >= warm:
+                ms.append(a.elapsed_time(b))
+            for it in items:
+                h.update(it[4].cpu().numpy().tobytes())
+                h.update(it[5].cpu().numpy().tobytes())
+        tests = sum(m.stats()["tests"] for m in maps) - t0
+        status = [m.sync_status() for m in maps]
+        if any(status):
+            raise RuntimeError(f"large map scenes: device status {status}")
+        tuning = batch.tuning() if batched else None
+        if batch:
+            batch.close()
+        blocks = [m.block_count() for m in maps]
+        for m in maps:
+            m.close()
+        return ms, tests, h.hexdigest(), tuning, blocks
+
+    clocks = Clocks(local)
+    clocks.start()
+    clocks.mark(True)
+    msb, testsb, digb, tuning, blocks = run(True)
+    msp, testsp, digp, _, _ = run(False)
+    clocks.mark(False)
+    clk = clocks.stop()
+    steps = len(msb)
+    returns = sum(len(frames[i * per + t][0]) for i in range(npine) for t in range(warm, ticks))
+    return {
+        "metric": "large map, batched: point x orientation tests/s (8 pine scenes per tick)",
+        "value": testsb / (sum(msb) / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warm, "ms_per_step": sum(msb) / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64", "data": "synthetic",
+        "config": {"workload": f"{W.name}_8_scenes", "scenes": npine, "ticks": ticks,
+                   "scene_box_m": "14 x 14 x 12.9 around each pine", "voxel_m": p["v"],
+                   "K": p["K"], "G": len(W.dirs), "per_tick": "one frame of every scene, "
+                   "integrated, then its surface points scored",
+                   "l2": "scene views far larger than L2; no flush"},
+        "latency_ms": {"p50": float(np.percentile(msb, 50)), "p99": float(np.percentile(msb, 99))},
+        "returns_per_s": returns / (sum(msb) / 1e3),
+        "tuning": tuning,
+        "bricks_per_scene": blocks,
+        "per_scene_path": {"value": testsp / (sum(msp) / 1e3), "ms_per_step": sum(msp) / steps,
+                           "latency_ms": {"p50": float(np.percentile(msp, 50)),
+                                          "p99": float(np.percentile(msp, 99))}},
+        "speedup_vs_per_scene": (sum(msp) / steps) / (sum(msb) / steps),
+        "label_agreement": 1.0 if digb == digp else 0.0,
+        "labels_digest": digb[:16],
+        "tests_equal": testsb == testsp,
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+
+
 def main():
     args = _args()
     ws, rank, local = _dist()
+    if args.large and args.batched:
+        print(json.dumps(run_large_batched(args, local)), flush=True)
+        return
     if args.batched:
         out = run_batched(args, local)
         print(json.dumps(out), flush=True)
