@@ -34,6 +34,16 @@
  *    integrations are skipped, the map keeps the last committed scan, and
  *    scoring keeps working on it.
  *  - A context is not thread-safe; use it from one host thread.
+ *  - The library is built twice with the same entry points: libaf.so, and
+ *    libaf_checked.so (compiled with AF_CHECKED), where every pool index,
+ *    plane-word index and run-table index that the integration, bit-view and
+ *    scoring kernels use is checked before the access; a failed check skips
+ *    the access (a read gives 0) and latches AF_ERR_CHECK in the device
+ *    status word, which af_sync_status returns. af_version names the build.
+ *  - Fault injection for tests: when the environment variable
+ *    AF_FAIL_ALLOC_AT holds k >= 0, af_create's k-th device allocation
+ *    (counting from 0) fails as if the device were out of memory: af_create
+ *    frees what it allocated and returns AF_ERR_CUDA.
  */
 #ifndef AF_H
 #define AF_H
@@ -53,7 +63,8 @@ typedef enum {
     AF_ERR_CAPACITY = 2,    /* hash, brick pool or per-call size exceeded */
     AF_ERR_CUDA = 3,        /* a CUDA call failed; see af_last_error       */
     AF_ERR_TIMEOUT = 4,     /* a bounded device wait gave up               */
-    AF_ERR_STATE = 5        /* call out of order (e.g. score before tool)  */
+    AF_ERR_STATE = 5,       /* call out of order (e.g. score before tool)  */
+    AF_ERR_CHECK = 6        /* a bounds check of the checked build failed  */
 } af_status;
 
 /* Per-point labels written by af_score (Fig. 1: green / red / grey). */
@@ -211,7 +222,8 @@ af_status af_frame_host(af_ctx *ctx, const float *h_xyz, uint32_t n, const float
                         uint8_t *h_label, int16_t *h_best, void *stream);
 
 /* Waits for the context's last stream and returns the latched device status
- * (AF_OK or AF_ERR_CAPACITY). Does not clear it. */
+ * (AF_OK, AF_ERR_CAPACITY, or AF_ERR_CHECK in the checked build). Does not
+ * clear it. */
 af_status af_sync_status(af_ctx *ctx);
 
 /* Synchronises and fills *out. */

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 UNSCORED, ACCESSIBLE, BLOCKED = 0, 1, 2
-OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_CHECK = range(7)
 KERNEL_TOOL, KERNEL_CORRIDOR = 0, 1
 STATUS = {0: "AF_OK", 1: "AF_ERR_INVALID_ARG", 2: "AF_ERR_CAPACITY", 3: "AF_ERR_CUDA",
           4: "AF_ERR_TIMEOUT", 5: "AF_ERR_STATE"}
@@ -104,12 +104,16 @@ _lib = None
 
 
 def load(build: bool = True) -> C.CDLL:
-    """Load libaf.so from the package directory (building it if stale)."""
+    """Load libaf.so from the package directory (building it if stale); with
+    the environment variable AF_CHECKED=1, the bounds-checked libaf_checked.so
+    (same entry points; failed checks latch AF_ERR_CHECK)."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB
+        if build:
+            _build.build()
+        path = _build.LIB_CHECKED if os.environ.get("AF_CHECKED") == "1" else _build.LIB
         if not os.path.exists(path):
-            raise RuntimeError(f"libaf.so not found at {path}; run build()")
+            raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run build()")
         lib = C.CDLL(path)
         P, U32, I32, I64 = C.c_void_p, C.c_uint32, C.c_int32, C.c_int64
         sig = {

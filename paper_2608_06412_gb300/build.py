@@ -1,10 +1,13 @@
-"""Builds libaf.so (the sm_103a CUDA library behind include/af.h) in-tree.
+"""Builds libaf.so (the sm_103a CUDA library behind include/af.h) in-tree,
+and its bounds-checked twin libaf_checked.so (the same sources compiled with
+AF_CHECKED: every pool, plane-word and run-table index of the integration,
+bit-view and scoring kernels is checked and a failure latches AF_ERR_CHECK).
 
-Each translation unit is compiled in parallel with nvcc, then linked into
-``paper_2608_06412_gb300/libaf.so``. Floating-point contraction is off on
-both the device (--fmad=false) and the host (-ffp-contract=off) side: the
-integer results of the method are decided by single-precision arithmetic that
-must round exactly as written.
+Each translation unit of both builds is compiled in parallel with nvcc, then
+linked into ``paper_2608_06412_gb300/libaf.so`` and ``libaf_checked.so``.
+Floating-point contraction is off on both the device (--fmad=false) and the
+host (-ffp-contract=off) side: the integer results of the method are decided
+by single-precision arithmetic that must round exactly as written.
 """
 from __future__ import annotations
 
@@ -19,6 +22,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libaf.so")
+LIB_CHECKED = os.path.join(PKG, "libaf_checked.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -40,9 +44,9 @@ def _deps():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB_CHECKED):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_CHECKED))
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
@@ -53,21 +57,23 @@ def flags() -> list:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libaf.so if any source is newer than it; return its path."""
+    """Compile libaf.so and libaf_checked.so if any source is newer than
+    them; return the path of libaf.so."""
     if not force and not _stale():
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD_DIR, exist_ok=True)
     procs = []
-    objs = []
-    for src in _sources():
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        objs.append(obj)
-        cmd = [nvcc, *flags(), "-c", src, "-o", obj]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
-                                            stderr=subprocess.STDOUT, text=True)))
+    objs = {LIB: [], LIB_CHECKED: []}
+    for lib, extra, tag in ((LIB, [], ""), (LIB_CHECKED, ["-DAF_CHECKED"], ".checked")):
+        for src in _sources():
+            obj = os.path.join(BUILD_DIR, os.path.basename(src) + tag + ".o")
+            objs[lib].append(obj)
+            cmd = [nvcc, *flags(), *extra, "-c", src, "-o", obj]
+            if verbose and not extra:
+                cmd.insert(1, "-Xptxas=-v")
+            procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                                stderr=subprocess.STDOUT, text=True)))
     failed = []
     for cmd, p in procs:
         out, _ = p.communicate()
@@ -77,9 +83,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
+    for lib, o in objs.items():
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run([nvcc, ARCH, "-shared", "-o", tmp, *o], check=True)
+        os.replace(tmp, lib)
     return LIB
 
 

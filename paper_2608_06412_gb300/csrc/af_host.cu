@@ -8,6 +8,7 @@
 #include <array>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -98,7 +99,11 @@ static af_status fail(af_ctx* c, af_status s, const char* fmt, ...) {
       return fail((ctx), AF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
   } while (0)
 
-extern "C" const char* af_version(void) { return "libaf 0.1 (sm_103a)"; }
+#ifdef AF_CHECKED
+extern "C" const char* af_version(void) { return "libaf 0.2 (sm_103a, checked)"; }
+#else
+extern "C" const char* af_version(void) { return "libaf 0.2 (sm_103a)"; }
+#endif
 
 extern "C" const char* af_last_error(const af_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
@@ -375,6 +380,9 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   M.row_words = (M.dim_vox[0] + 63) / 64;
   M.row_words_y = (M.dim_vox[1] + 63) / 64;
   M.row_words_z = (M.dim_vox[2] + 63) / 64;
+  M.words_x = (size_t)M.row_words * M.dim_vox[1] * M.dim_vox[2];
+  M.words_y = (size_t)M.row_words_y * M.dim_vox[0] * M.dim_vox[2];
+  M.words_z = (size_t)M.row_words_z * M.dim_vox[0] * M.dim_vox[1];
   M.hmask = cfg->hash_capacity - 1;
   M.pool_blocks = cfg->pool_blocks;
   {
@@ -382,7 +390,15 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
     M.nbmax = ba * ba * ba;
   }
 
+  // fault injection for tests: the k-th allocation fails (AF_FAIL_ALLOC_AT)
+  long fail_at = -1, nalloc = 0;
+  if (const char* f = std::getenv("AF_FAIL_ALLOC_AT")) fail_at = std::strtol(f, nullptr, 10);
   auto alloc = [&](void** p, size_t bytes, int fill) -> af_status {
+    if (nalloc++ == fail_at) {
+      fail(c, AF_ERR_CUDA, "device allocation of %zu bytes failed: injected failure at "
+                           "allocation %ld (AF_FAIL_ALLOC_AT)", bytes, fail_at);
+      return AF_ERR_CUDA;
+    }
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e == cudaSuccess) e = cudaMemset(*p, fill, bytes ? bytes : 16);
     if (e != cudaSuccess) {
@@ -585,6 +601,8 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
   AF_CUDA(ctx, cudaMemcpy(ctx->d_fruns, fruns.data(), fruns.size() * sizeof(int2), cudaMemcpyHostToDevice));
   for (int k = 0; k < 3; ++k) ctx->T.reach[k] = reach[k];
   ctx->T.fruns = ctx->d_fruns;
+  ctx->T.nruns = (int)runs.size();
+  ctx->T.ctl = ctx->M.ctl;
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_dtab, (size_t)G * sizeof(int4)));
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_arm, (size_t)G * 3 * sizeof(short4)));
   AF_CUDA(ctx, cudaMemcpy(ctx->d_dirs, h_dirs, (size_t)G * 12, cudaMemcpyHostToDevice));
@@ -676,6 +694,7 @@ extern "C" af_status af_sync_status(af_ctx* ctx) {
   AF_CUDA(ctx, cudaDeviceSynchronize());
   uint32_t st = 0;
   AF_CUDA(ctx, cudaMemcpy(&st, &ctx->M.ctl->status, 4, cudaMemcpyDeviceToHost));
+  if (st == AF_ERR_CHECK) return fail(ctx, AF_ERR_CHECK, "a bounds check of the checked build failed");
   if (st != 0) return fail(ctx, (af_status)st, "map capacity exceeded; integration stopped");
   return AF_OK;
 }

@@ -83,7 +83,8 @@ __device__ inline void mark_dirty(const MapView& M, uint32_t h, uint32_t blk, ui
   uint32_t base = 0;
   if (nm && lane == first) base = atomicAdd(&M.ctl->dirty_count, (unsigned)__popc(nm));
   base = __shfl_sync(active, base, first);
-  if (need) M.dirty[base + __popc(nm & ((1u << lane) - 1u))] = blk;
+  const uint32_t at = base + __popc(nm & ((1u << lane) - 1u));
+  if (need && check_index(at < M.pool_blocks, M.ctl)) M.dirty[at] = blk;
 }
 
 // Cube bricks of a return: first brick b0 and count nb per axis.
@@ -359,6 +360,7 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
 // bits in shared memory.
 __device__ void bitview_brick(const MapView& M, uint32_t blk) {
   __shared__ unsigned s_ob[16];
+  if (!check_index(blk < M.pool_blocks, M.ctl)) return;  // uniform over the CTA
   const int l = threadIdx.x;
   const int lane = l & 31, wi = l >> 5;
   unsigned char* occ = reinterpret_cast<unsigned char*>(M.occ);
@@ -387,8 +389,10 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
       const size_t y = (size_t)by * 8 + (wi & 1) * 4 + lane;
       const size_t z = (size_t)bz * 8 + (wi >> 1);
       const size_t at = (z * (size_t)M.dim_vox[1] + y) * row_bytes + bx;
-      occ[at] = (unsigned char)(ob >> (8 * lane));
-      known[at] = (unsigned char)(kb >> (8 * lane));
+      if (check_index(at < M.words_x * 8, M.ctl)) {
+        occ[at] = (unsigned char)(ob >> (8 * lane));
+        known[at] = (unsigned char)(kb >> (8 * lane));
+      }
     }
   }
   __syncthreads();
@@ -404,12 +408,14 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
     const size_t X = (size_t)M.dim_vox[0], xa = (size_t)bx * 8 + x;
     if (l < 64) {
       const size_t z = (size_t)bz * 8 + c;
-      reinterpret_cast<unsigned char*>(M.occ_y)[(z * X + xa) * ((size_t)M.row_words_y * 8) + by] =
-          (unsigned char)byte;
+      const size_t at = (z * X + xa) * ((size_t)M.row_words_y * 8) + by;
+      if (check_index(at < M.words_y * 8, M.ctl))
+        reinterpret_cast<unsigned char*>(M.occ_y)[at] = (unsigned char)byte;
     } else {
       const size_t y = (size_t)by * 8 + c;
-      reinterpret_cast<unsigned char*>(M.occ_z)[(y * X + xa) * ((size_t)M.row_words_z * 8) + bz] =
-          (unsigned char)byte;
+      const size_t at = (y * X + xa) * ((size_t)M.row_words_z * 8) + bz;
+      if (check_index(at < M.words_z * 8, M.ctl))
+        reinterpret_cast<unsigned char*>(M.occ_z)[at] = (unsigned char)byte;
     }
   }
   __syncthreads();  // s_ob is rewritten for the CTA's next brick

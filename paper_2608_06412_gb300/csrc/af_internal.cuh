@@ -39,6 +39,7 @@ constexpr float kScale = 1048576.0f;  // 2^20
 
 // Latched device status (values of af_status).
 constexpr uint32_t kStatusCapacity = 2;
+constexpr uint32_t kStatusChecked = 6;  // AF_ERR_CHECK: a bounds check of the checked build
 
 struct Control {
   uint32_t status;       // latched af_status of device-side failures
@@ -108,6 +109,7 @@ struct MapView {
   unsigned long long* occ;
   unsigned long long* known;
   Control* ctl;
+  size_t words_x, words_y, words_z;  // 64-bit words of the x-row views, of occ_y, of occ_z
 };
 
 // Tool tables on the device (built by af_set_tool).
@@ -132,6 +134,8 @@ struct ToolView {
   float cos_max;
   int strict;
   int reach[3];           // largest |offset| per axis over every kernel and arm sample
+  int nruns;              // entries of runs / fruns
+  Control* ctl;           // the map's status word (the checked build's run-index checks)
 };
 
 __host__ __device__ inline uint64_t pack_brick(uint32_t bx, uint32_t by, uint32_t bz) {
@@ -185,6 +189,20 @@ __device__ inline uint32_t lookup_brick(const MapView& M, uint64_t key) {
 
 __device__ inline void latch_status(Control* c, uint32_t code) {
   atomicCAS(&c->status, 0u, code);
+}
+
+// The checked build (libaf_checked.so, -DAF_CHECKED): `ok` is the bounds
+// check of an index about to be used; a failure latches AF_ERR_CHECK and the
+// caller skips the access. In the normal build the check is not compiled.
+__device__ inline bool check_index(bool ok, Control* c) {
+#ifdef AF_CHECKED
+  if (!ok) latch_status(c, kStatusChecked);
+  return ok;
+#else
+  (void)ok;
+  (void)c;
+  return true;
+#endif
 }
 
 // Voxel index of a coordinate, floor(c / v) with c / v rounded in IEEE single

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(512) k_pts_scatter(MapView M, PtView V) {
           const uint32_t b = s_nb[((nx >> 3) - bx + 1) + 3 * (((ny >> 3) - by + 1) + 3 * ((nz >> 3) - bz + 1))];
           if (b == kNoBlock) continue;
           const int32_t id = V.pid[(size_t)b * kBrickVox + vox_slot(nx, ny, nz)];
-          if (id >= 0) V.st[id].queued = 1;
+          if (id >= 0 && check_index((uint32_t)id < V.capacity, M.ctl)) V.st[id].queued = 1;
         }
   }
 }
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) k_pts_views(MapView M, const float4* __re
   const uint32_t blk = lookup_brick(M, pack_brick(r[0] >> 3, r[1] >> 3, r[2] >> 3));
   if (blk == kNoBlock) return;
   const int32_t id = V.pid[(size_t)blk * kBrickVox + vox_slot(r[0], r[1], r[2])];
-  if (id < 0) return;
+  if (id < 0 || !check_index((uint32_t)id < V.capacity, M.ctl)) return;
   PtState* s = V.st + id;
   if (atomicExch(&s->last_scan, frame) == frame) return;  // once per (point, scan)
   s->qsum[0] = __fadd_rn(s->qsum[0], q0);

@@ -51,6 +51,8 @@ __device__ inline unsigned long long row_bits(const unsigned long long* __restri
   }
   const unsigned long long* row = plane + ((size_t)o2 * O1 + o1) * rw;
   const int wa = xa >> 6, wb = xb >> 6, sh = xa & 63;
+  const size_t words = ax == 0 ? M.words_x : (ax == 1 ? M.words_y : M.words_z);
+  if (!check_index(((size_t)o2 * O1 + o1) * rw + wb < words, M.ctl)) return 0ull;
   unsigned long long win = __ldg(row + wa) >> sh;
   if (wb != wa) win |= __ldg(row + wb) << (64 - sh);
   const int n = xb - xa + 1;
@@ -67,6 +69,7 @@ struct RunEntry {
 
 template <bool FAST>
 __device__ inline RunEntry load_run(const ToolView& T, int r) {
+  if (!check_index((unsigned)r < (unsigned)T.nruns, T.ctl)) return {0, 0};  // an empty run
   if (FAST) {
     const int2 f = __ldg(T.fruns + r);
     return {f.x, f.y};
@@ -91,6 +94,11 @@ __device__ inline unsigned long long run_bits(const unsigned long long* __restri
     const int row = (ax == 0 ? P.row : (ax == 1 ? P.rowy : P.rowz)) + e.a;
     const unsigned long long* plane = ax == 0 ? px : (ax == 1 ? py : pz);
     const int wa = xa >> 6, wb = (xa + n - 1) >> 6, sh = xa & 63;
+    const size_t words = ax == 0 ? M.words_x : (ax == 1 ? M.words_y : M.words_z);
+    if (!check_index(row + wa >= 0 && (size_t)(row + wb) < words, M.ctl)) {
+      *len = n;
+      return 0ull;
+    }
     unsigned long long win = __ldg(plane + row + wa) >> sh;
     if (wb != wa) win |= __ldg(plane + row + wb) << (64 - sh);
     if (n < 64) win &= (1ull << n) - 1ull;
@@ -128,6 +136,7 @@ __device__ inline bool bit_at(const unsigned long long* __restrict__ plane, cons
     return false;
   const size_t w = FAST ? (size_t)(P.row + (a.z * M.dim_vox[1] + a.y) * M.row_words + (x >> 6))
                         : ((size_t)z * M.dim_vox[1] + y) * M.row_words + (x >> 6);
+  if (!check_index(w < M.words_x, M.ctl)) return false;
   return (__ldg(plane + w) >> (x & 63)) & 1ull;
 }
 

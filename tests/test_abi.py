@@ -43,6 +43,37 @@ def test_host_errors_are_reported_without_gpu():
     assert lib.af_create(None, None) == 1
 
 
+def test_checked_build_exports_the_same_symbols():
+    """libaf_checked.so (the bounds-checked build) exports every declared
+    entry point and names itself in af_version."""
+    import ctypes as C
+    from paper_2608_06412_gb300 import build as B
+    af.load()
+    lib = C.CDLL(B.LIB_CHECKED)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    lib.af_version.restype = C.c_char_p
+    assert b"checked" in lib.af_version() and b"checked" not in af.load().af_version()
+
+
+def test_injected_allocation_failure():
+    """AF_FAIL_ALLOC_AT=0 makes af_create's first device allocation fail:
+    AF_ERR_CUDA, nothing returned, the injection named in the message. The
+    check comes before the allocation, so no GPU is needed."""
+    import ctypes as C
+    from paper_2608_06412_gb300 import workload
+    lib = af.load()
+    cc = workload.single_frame().af_config()._c()
+    h = C.c_void_p(123)
+    os.environ["AF_FAIL_ALLOC_AT"] = "0"
+    try:
+        st = lib.af_create(C.byref(cc), C.byref(h))
+    finally:
+        del os.environ["AF_FAIL_ALLOC_AT"]
+    assert st == af.ERR_CUDA and not h.value
+    assert b"injected failure at allocation 0" in lib.af_last_error(None)
+
+
 def test_noalloc_rejects_boxes_beyond_its_limit():
     """af_integrate_scan_noalloc rejects a box of more than 2^40 voxels before
     touching the GPU, including boxes whose voxel count would wrap a 64-bit
