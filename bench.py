@@ -26,6 +26,7 @@ Other lines, each with the oracle timed beside it on a bounded sample:
   --large      the 40 x 40 m map at 1 cm: 3,000 frames, then every surface point;
   --large --batched  its eight pine orbits as eight scenes ticked together,
                against the per-scene path;
+  --large --soft     the differentiable step on it (brick-sparse SDF view);
 and variants of the default line: --projective, --clamp-signed, --ring
 (the paper's yaw ring; with --points also --c2f), --score-split B.
 """
@@ -1209,6 +1210,99 @@ def run_points(args, local):
     return out
 
 
+def run_soft_large(args, local):
+    """The differentiable step on the large map (3,000 frames at 1 cm, K = 256
+    of G = 512, 1.5 m corridor): 100k surface points drawn from the stream's
+    points, plain scoring, the start direction of each accessible point, its
+    soft clearance and 20 ascent steps. The box's dense SDF view would need
+    over 2^31 cells, so the brick-sparse view is built (af_soft_set_view 0
+    chooses it); its build is timed once, the step after it."""
+    from paper_2608_06412_gb300 import workload
+    W = workload.large_map()
+    frames = workload.large_frames(W, range(W.params["frames"]))   # spawned workers first
+    import torch
+    from paper_2608_06412_gb300 import af
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m = args.soft_points
+    g = af.Map(W.af_config(**dict(LARGE_CAPS, max_points=max(m, LARGE_CAPS["max_points"]))))
+    g.set_tool(W.af_tool(), W.dirs)
+    for f in frames:
+        g.integrate_scan(torch.from_numpy(f[0]).to(dev), f[1])
+    torch.cuda.synchronize()
+    P = np.concatenate([f[3] for f in frames])
+    N = np.concatenate([f[4] for f in frames])
+    v = np.float64(np.float32(W.params["v"]))
+    ijk = np.floor(P.astype(np.float64) / v).astype(np.int64) + (1 << 20)
+    key = ijk[:, 0] | (ijk[:, 1] << 21) | (ijk[:, 2] << 42)
+    _, first = np.unique(key, return_index=True)
+    sel = np.sort(np.random.default_rng(9).choice(np.sort(first), m, replace=False))
+    Pd = torch.from_numpy(np.ascontiguousarray(P[sel])).to(dev)
+    Nd = torch.from_numpy(np.ascontiguousarray(N[sel])).to(dev)
+    lab = torch.empty(m, dtype=torch.uint8, device=dev)
+    best = torch.empty(m, dtype=torch.int16, device=dev)
+    u0 = torch.empty((m, 3), dtype=torch.float32, device=dev)
+    z = torch.zeros(m, dtype=torch.float32, device=dev)
+    al, be, hh, c0, c, cmin = (torch.empty(m, dtype=torch.float32, device=dev) for _ in range(6))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.score(Pd, Nd, lab, best)
+        g.soft_start(lab, best, out=u0)
+        g.soft_clearance_raw(Pd, u0, z, z, z, 1, out=c0)
+        al.zero_()
+        be.zero_()
+        hh.zero_()
+        g.soft_refine(Pd, u0, al, be, hh, 1, steps=SOFT_STEPS, out=(c, cmin), **SOFT_LR)
+
+    g.profile(True)
+    g.profile_read(reset=True)
+    step()                                   # builds the sparse view
+    torch.cuda.synchronize()
+    build_ms = g.profile_read(reset=True).get("k_views", (0, 0.0))[1]
+    warm, steps = max(args.warmup, 3), max(1, min(args.steps, 20))
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    g.profile_read(reset=True)
+    n_acc = int((lab == af.ACCESSIBLE).sum().item())
+    clocks = Clocks(local)
+    clocks.start()
+    clocks.mark(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(False)
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    prof = g.profile_read(reset=True)
+    assert g.sync_status() == 0
+    evals = n_acc * (SOFT_STEPS + 2)
+    out = {
+        "metric": "large map: " + SOFT_METRIC, "value": evals / (sum(ms) / steps / 1e3),
+        "unit": SOFT_UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": sum(ms) / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"soft_refine_{W.name}_{m}_points", "points": m,
+                   "K": W.params["K"], "G": len(W.dirs), "refine_steps": SOFT_STEPS, **SOFT_LR,
+                   "tau_s": af.TAU_S, "sdf_view": "brick-sparse (automatic: the box's dense "
+                   "view exceeds 2^31 cells)", "l2": "views far larger than L2; no flush"},
+        "accessible_points": n_acc,
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "kernel_ms": {k: round(v[1] / steps, 4) for k, v in prof.items() if v[0]},
+        "sparse_view_build_ms": build_ms,
+        "bricks": g.block_count(),
+        "gpu_launches": int(sum(v[0] for v in prof.values()) / steps),
+        "clocks": clk,
+    }
+    g.close()
+    return out
+
+
 LARGE_SCENE_CAPS = dict(hash_capacity=1 << 21, pool_blocks=1 << 20, max_returns=1 << 15,
                         max_points=1 << 15)
 
@@ -1335,6 +1429,9 @@ def main():
     ws, rank, local = _dist()
     if args.large and args.batched:
         print(json.dumps(run_large_batched(args, local)), flush=True)
+        return
+    if args.large and args.soft:
+        print(json.dumps(run_soft_large(args, local)), flush=True)
         return
     if args.batched:
         out = run_batched(args, local)

@@ -330,10 +330,10 @@ af_status af_batch_get_tuning(af_batch *batch, af_batch_tuning *out);
  *
  * Buffers are device memory owned by the caller; pairs are float32: d_pts
  * (points x 3), d_u0 (n x 3, unit), d_alpha, d_beta, d_h, outputs (n).
- * The first call builds single-precision views of the map (one float per
- * voxel of the box plus 32 bytes per interpolation cell: 36 bytes per voxel
- * of the box, allocated once, AF_ERR_CAPACITY if that fails) and later calls
- * rebuild them when scans were integrated since; the map's updates must be
+ * The first call builds a single-precision view of the map (dense: 36 bytes
+ * per voxel of the box; brick-sparse: 16 KB per brick near an observed one;
+ * see af_soft_set_view; AF_ERR_CAPACITY if it cannot be allocated) and later
+ * calls rebuild it when scans were integrated since; the map's updates must be
  * ordered before the call on `stream`. AF_ERR_STATE without a tool or when
  * no axis sample lies beyond r_s. Asynchronous on `stream`. Non-finite
  * inputs give NaN outputs.
@@ -384,6 +384,19 @@ af_status af_soft_clearance_adjoint(af_ctx *ctx, const float *d_pts, uint32_t pe
 af_status af_soft_refine(af_ctx *ctx, const float *d_pts, uint32_t per_point, const float *d_u0,
                          float *d_alpha, float *d_beta, float *d_h, uint64_t n, float tau_s,
                          const af_refine *R, float *d_c, float *d_cmin, void *stream);
+
+/* The SDF view the soft calls sample (the same values either way, so the
+ * same results bit for bit): mode 1, dense -- one FP32 value per voxel of the
+ * map box plus a 32-byte corner record per interpolation cell (36 bytes per
+ * box voxel; boxes under 2^31 cells); mode 2, brick-sparse -- a 4-byte slot
+ * per brick of the box (plus one layer below it) and 16 KB of corner records
+ * for every brick within one brick below an allocated brick on each axis
+ * (every cell whose corners touch an observed voxel; the others read tau),
+ * sized by the map instead of the box, one more dependent load per sample;
+ * mode 0 (default): dense when it fits (under 2^31 cells and within half
+ * the free device memory), else sparse. Frees the current views; the next
+ * soft call builds the chosen one. Synchronous. */
+af_status af_soft_set_view(af_ctx *ctx, int32_t mode);
 
 /* Per point of n pairs (per_point each, as above): the index within its
  * pairs of the largest d_c (lowest index on ties, -1 if all are NaN) ->

@@ -30,7 +30,7 @@ EXPORTS = ("af_version", "af_create", "af_destroy", "af_integrate_scan", "af_set
            "af_soft_clearance", "af_soft_clearance_adjoint", "af_soft_refine", "af_soft_best",
            "af_soft_start", "af_points_enable", "af_points_frame", "af_points_drain",
            "af_points_stats", "af_points_export", "af_integrate_scan_projective",
-           "af_set_score_split", "af_probe_l2_read", "af_last_error")
+           "af_set_score_split", "af_probe_l2_read", "af_soft_set_view", "af_last_error")
 NOALLOC_MAX_RETURNS = 65536
 #: Kernel names in the order of af_profile's arrays.
 KERNELS = ("k_alloc", "k_integrate", "k_bitview", "k_score", "k_views", "k_soft",
@@ -124,6 +124,7 @@ def load(build: bool = True) -> C.CDLL:
             "af_integrate_scan_projective": (C.c_int, [P, P, U32, P, U32, P]),
             "af_set_score_split": (C.c_int, [P, C.c_int32]),
             "af_probe_l2_read": (C.c_int, [C.c_uint64, U32, U32, C.POINTER(C.c_double)]),
+            "af_soft_set_view": (C.c_int, [P, C.c_int32]),
             "af_set_tool": (C.c_int, [P, C.POINTER(_Tool), P, U32]),
             "af_score": (C.c_int, [P, P, P, U32, P, P, P]),
             "af_frame_host": (C.c_int, [P, P, U32, P, P, P, U32, P, P, P]),
@@ -456,6 +457,10 @@ class Map:
                                       _dev_ptr(u0, torch.float32, (3,)) if m else C.c_void_p(0),
                                       _stream_ptr(stream)), self._h)
         return u0
+
+    def soft_set_view(self, mode: int):
+        """af_soft_set_view: 0 automatic, 1 dense, 2 brick-sparse SDF view."""
+        _check(self._lib.af_soft_set_view(self._h, int(mode)), self._h)
 
     def soft_start(self, label, best, out=None, stream=None):
         """af_soft_start: (m, 3) start directions of refinement -- the best

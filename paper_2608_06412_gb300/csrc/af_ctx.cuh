@@ -35,6 +35,13 @@ struct af_ctx {
   // map has changed since)
   float* d_dense = nullptr;
   float4* d_cells = nullptr;
+  uint32_t* d_bgrid = nullptr;   // the brick-sparse view: slot per grid brick
+  uint32_t* d_skeys = nullptr;   // grid brick of every slot
+  uint32_t* d_nslots = nullptr;
+  float4* d_scells = nullptr;    // 512 cell records per slot
+  uint32_t scells_cap = 0;
+  int soft_mode = 0;             // af_soft_set_view: 0 automatic, 1 dense, 2 sparse
+  bool views_sparse = false;     // the view built is the sparse one
   bool views_valid = false;
   uint32_t views_frame = 0;
   float* d_table = nullptr;  // seed directions, and their host copy

@@ -49,6 +49,10 @@ cudaError_t launch_soft_start(const uint8_t* label, const int16_t* best, uint32_
                               const float* dirs, int G, float* u0, int num_sms,
                               cudaStream_t stream);
 cudaError_t launch_pts_snapshot(af_ctx* ctx, cudaStream_t stream);
+cudaError_t launch_sview_mark(const MapView& M, int num_sms, uint32_t* bgrid, size_t gcount,
+                              int gx, int gy, uint32_t* keys, uint32_t* nslots, cudaStream_t stream);
+cudaError_t launch_sview_fill(const MapView& M, int num_sms, const uint32_t* keys, uint32_t nslots,
+                              int gx, int gy, float4* cells, cudaStream_t stream);
 }  // namespace af
 
 using af::MapView;
@@ -306,6 +310,10 @@ static void free_all(af_ctx* c) {
   cudaFree(c->d_scount);
   cudaFree(c->d_dense);
   cudaFree(c->d_cells);
+  cudaFree(c->d_bgrid);
+  cudaFree(c->d_skeys);
+  cudaFree(c->d_nslots);
+  cudaFree(c->d_scells);
   cudaFree(c->d_table);
   cudaFree(c->d_img);
   for (void* p : {(void*)c->d_pid, (void*)c->d_pst, (void*)c->d_pviews, (void*)c->d_pnew,
@@ -789,33 +797,110 @@ extern "C" af_status af_profile_read(af_ctx* ctx, af_profile* out, int reset) {
 // The differentiable form
 // ---------------------------------------------------------------------------
 
-// Builds (or rebuilds, if the map changed since) the dense and cell views.
+// Whether the dense views of the map box fit: fewer than 2^31 cells, and
+// 36 bytes per box voxel within half the device's free memory.
+static bool dense_views_fit(const af_ctx* ctx) {
+  const MapView& M = ctx->M;
+  const uint64_t cells = ((uint64_t)M.dim_vox[0] + 1) * (M.dim_vox[1] + 1) * (M.dim_vox[2] + 1);
+  if (cells >= (1ull << 31)) return false;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cells * 36ull <= free_b / 2;
+}
+
+// Builds (or rebuilds, if the map changed since) the SDF views: the dense
+// view of the box and its cell records, or the brick-sparse cell records
+// (the view chosen by af_soft_set_view; automatic: dense when it fits).
 static af_status ensure_views(af_ctx* ctx, cudaStream_t s) {
   const MapView& M = ctx->M;
-  bool fill = false;
-  if (!ctx->d_cells) {
-    const size_t nd = (size_t)M.dim_vox[0] * M.dim_vox[1] * M.dim_vox[2];
-    const size_t nc = ((size_t)M.dim_vox[0] + 1) * (M.dim_vox[1] + 1) * (M.dim_vox[2] + 1);
-    if (cudaMalloc(&ctx->d_dense, nd * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_cells, nc * 2 * sizeof(float4)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(ctx->d_dense);
-      ctx->d_dense = nullptr;
-      ctx->d_cells = nullptr;
-      return fail(ctx, AF_ERR_CAPACITY,
-                  "soft clearance: cannot allocate the SDF views (%zu + %zu bytes) of the map box",
-                  nd * sizeof(float), nc * 2 * sizeof(float4));
+  if (!ctx->d_cells && !ctx->d_bgrid)
+    ctx->views_sparse = ctx->soft_mode == 2 || (ctx->soft_mode == 0 && !dense_views_fit(ctx));
+  const bool stale = !ctx->views_valid || ctx->views_frame != ctx->frame;
+  if (!ctx->views_sparse) {
+    bool fill = false;
+    if (!ctx->d_cells) {
+      const size_t nd = (size_t)M.dim_vox[0] * M.dim_vox[1] * M.dim_vox[2];
+      const size_t nc = ((size_t)M.dim_vox[0] + 1) * (M.dim_vox[1] + 1) * (M.dim_vox[2] + 1);
+      if (nc >= (1ull << 31))
+        return fail(ctx, AF_ERR_CAPACITY, "soft clearance: the map box has too many cells for the dense SDF view");
+      if (cudaMalloc(&ctx->d_dense, nd * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&ctx->d_cells, nc * 2 * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->d_dense);
+        ctx->d_dense = nullptr;
+        ctx->d_cells = nullptr;
+        return fail(ctx, AF_ERR_CAPACITY,
+                    "soft clearance: cannot allocate the SDF views (%zu + %zu bytes) of the map box",
+                    nd * sizeof(float), nc * 2 * sizeof(float4));
+      }
+      fill = true;
     }
-    fill = true;
+    if (fill || stale) {
+      AF_CUDA(ctx, timed(ctx, 4, s, [&] {
+        return af::launch_views(M, ctx->num_sms, fill, ctx->d_dense, ctx->d_cells, s);
+      }));
+    }
+  } else {
+    const int gx = M.dim_vox[0] / 8 + 1, gy = M.dim_vox[1] / 8 + 1, gz = M.dim_vox[2] / 8 + 1;
+    const size_t gcount = (size_t)gx * gy * gz;
+    if (gcount >= (1ull << 32))
+      return fail(ctx, AF_ERR_CAPACITY, "soft clearance: the map box has too many bricks for the sparse view");
+    if (!ctx->d_bgrid) {
+      if (cudaMalloc((void**)&ctx->d_bgrid, gcount * 4) != cudaSuccess ||
+          cudaMalloc((void**)&ctx->d_skeys, (size_t)ctx->cfg.pool_blocks * 8 * 4) != cudaSuccess ||
+          cudaMalloc((void**)&ctx->d_nslots, 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->d_bgrid);
+        cudaFree(ctx->d_skeys);
+        ctx->d_bgrid = nullptr;
+        ctx->d_skeys = nullptr;
+        ctx->d_nslots = nullptr;
+        return fail(ctx, AF_ERR_CAPACITY, "soft clearance: cannot allocate the sparse view's brick grid");
+      }
+    }
+    if (stale) {
+      AF_CUDA(ctx, timed(ctx, 4, s, [&] {
+        return af::launch_sview_mark(M, ctx->num_sms, ctx->d_bgrid, gcount, gx, gy, ctx->d_skeys,
+                                     ctx->d_nslots, s);
+      }));
+      uint32_t nslots = 0;
+      AF_CUDA(ctx, cudaMemcpyAsync(&nslots, ctx->d_nslots, 4, cudaMemcpyDeviceToHost, s));
+      AF_CUDA(ctx, cudaStreamSynchronize(s));
+      if (nslots > ctx->scells_cap) {  // the records of every slot, 16 KB each
+        cudaFree(ctx->d_scells);
+        ctx->d_scells = nullptr;
+        ctx->scells_cap = 0;
+        const size_t bytes = (size_t)nslots * af::kBrickVox * 2 * sizeof(float4);
+        if (cudaMalloc((void**)&ctx->d_scells, bytes) != cudaSuccess) {
+          cudaGetLastError();
+          ctx->views_valid = false;
+          return fail(ctx, AF_ERR_CAPACITY, "soft clearance: cannot allocate %zu bytes of sparse cell records", bytes);
+        }
+        ctx->scells_cap = nslots;
+      }
+      AF_CUDA(ctx, timed(ctx, 4, s, [&] {
+        return af::launch_sview_fill(M, ctx->num_sms, ctx->d_skeys, nslots, gx, gy, ctx->d_scells, s);
+      }));
+    }
   }
-  if (fill || !ctx->views_valid || ctx->views_frame != ctx->frame) {
-    AF_CUDA(ctx, timed(ctx, 4, s, [&] {
-      return af::launch_views(M, ctx->num_sms, fill, ctx->d_dense, ctx->d_cells, s);
-    }));
-    ctx->views_valid = true;
-    ctx->views_frame = ctx->frame;
-  }
+  ctx->views_valid = true;
+  ctx->views_frame = ctx->frame;
   return AF_OK;
+}
+
+// The view fields of S after ensure_views.
+static void view_fields(const af_ctx* ctx, af::SoftView* S) {
+  const MapView& M = ctx->M;
+  S->sparse = ctx->views_sparse ? 1 : 0;
+  S->cells = ctx->views_sparse ? ctx->d_scells : ctx->d_cells;
+  S->bgrid = ctx->d_bgrid;
+  for (int k = 0; k < 3; ++k) {
+    S->glo[k] = M.dom_vox[k] - 8;
+    S->gdim[k] = M.dim_vox[k] / 8 + 1;
+  }
 }
 
 // The axis samples of the tool, decided in single precision: j = j0..J with
@@ -860,9 +945,8 @@ static af_status soft_view(af_ctx* ctx, float tau_s, af::SoftView* S) {
   const double E = ((double)ctx->cfg.truncation + 1e-3 + mx - mnm) * 1.4426950408889634 / (double)tau_s;
   S->fixed = E <= 96.0 ? 1 : 0;
   S->ref = (float)-mx;
-  const uint64_t cells = (uint64_t)S->ncell[0] * S->ncell[1] * S->ncell[2];
-  if (cells >= (1ull << 31))
-    return fail(ctx, AF_ERR_CAPACITY, "soft clearance: the map box has too many cells for the SDF view");
+  S->sparse = 0;
+  S->bgrid = nullptr;
   return AF_OK;
 }
 
@@ -920,7 +1004,7 @@ extern "C" af_status af_soft_clearance(af_ctx* ctx, const float* d_pts, uint32_t
   if ((st = soft_view(ctx, tau_s, &S)) != AF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = ensure_views(ctx, s)) != AF_OK) return st;
-  S.cells = ctx->d_cells;
+  view_fields(ctx, &S);
   AF_CUDA(ctx, timed(ctx, 5, s, [&] {
     return af::launch_soft(S, false, d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n, nullptr,
                            d_c, d_cmin, nullptr, nullptr, nullptr, ctx->num_sms, s);
@@ -942,7 +1026,7 @@ extern "C" af_status af_soft_clearance_adjoint(af_ctx* ctx, const float* d_pts, 
   if ((st = soft_view(ctx, tau_s, &S)) != AF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = ensure_views(ctx, s)) != AF_OK) return st;
-  S.cells = ctx->d_cells;
+  view_fields(ctx, &S);
   AF_CUDA(ctx, timed(ctx, 6, s, [&] {
     return af::launch_soft(S, true, d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n, d_gc, d_c,
                            nullptr, d_ga, d_gb, d_gh, ctx->num_sms, s);
@@ -966,13 +1050,35 @@ extern "C" af_status af_soft_refine(af_ctx* ctx, const float* d_pts, uint32_t pe
   if ((st = soft_view(ctx, tau_s, &S)) != AF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = ensure_views(ctx, s)) != AF_OK) return st;
-  S.cells = ctx->d_cells;
+  view_fields(ctx, &S);
   const af::RefineArgs A{(int)R->steps, R->lr_dir, R->lr_h, R->h_max};
   AF_CUDA(ctx, timed(ctx, 7, s, [&] {
     return af::launch_soft_refine(S, A, d_pts, per_point, d_u0, d_alpha, d_beta, d_h, n, d_c,
                                   d_cmin, ctx->num_sms, s);
   }));
   ctx->last_stream = s;
+  return AF_OK;
+}
+
+extern "C" af_status af_soft_set_view(af_ctx* ctx, int32_t mode) {
+  if (!ctx) return fail(nullptr, AF_ERR_INVALID_ARG, "af_soft_set_view: NULL context");
+  if (mode < 0 || mode > 2) return fail(ctx, AF_ERR_INVALID_ARG, "af_soft_set_view: mode must be 0, 1 or 2");
+  AF_CUDA(ctx, cudaDeviceSynchronize());
+  cudaFree(ctx->d_dense);
+  cudaFree(ctx->d_cells);
+  cudaFree(ctx->d_bgrid);
+  cudaFree(ctx->d_skeys);
+  cudaFree(ctx->d_nslots);
+  cudaFree(ctx->d_scells);
+  ctx->d_dense = nullptr;
+  ctx->d_cells = nullptr;
+  ctx->d_bgrid = nullptr;
+  ctx->d_skeys = nullptr;
+  ctx->d_nslots = nullptr;
+  ctx->d_scells = nullptr;
+  ctx->scells_cap = 0;
+  ctx->views_valid = false;
+  ctx->soft_mode = mode;
   return AF_OK;
 }
 

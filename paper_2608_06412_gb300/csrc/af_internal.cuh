@@ -239,9 +239,14 @@ struct Pose {
 // What the soft-clearance kernels read: the cell view of the map and the
 // axis samples of the tool. Built per call by the host.
 struct SoftView {
-  const float4* cells;  // ncell[0] * ncell[1] * ncell[2] cells, 2 float4 each
+  const float4* cells;  // dense: ncell[0] * ncell[1] * ncell[2] cells, 2 float4 each;
+                        // sparse: 512 cells (2 float4 each) per slot of bgrid
   int lo[3];            // absolute voxel index of the lowest cell's low corner
   int ncell[3];         // cells per axis: box voxels + 1
+  int sparse;           // 1: the brick-sparse view
+  const uint32_t* bgrid;  // sparse: per grid brick, the slot of its cells (kNoBlock: all tau)
+  int glo[3];           // sparse: absolute voxel index of the grid's first brick corner
+  int gdim[3];          // sparse: grid bricks per axis (box bricks + the layer below)
   float v, tau;
   float r, r_corr;      // margins: tool, corridor
   int j0, jt, J;        // samples j0..J; tool margin for j <= jt

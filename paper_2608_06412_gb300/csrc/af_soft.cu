@@ -31,6 +31,7 @@
 // and exp2 / log2 freely.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -155,10 +156,13 @@ __device__ inline Dir make_dir(const SoftView& S, const float u0[3], const float
   return d;
 }
 
-// Cell record index of sample j: false when the cell lies outside the view
-// (all corners read tau). f receives the fractional position in the cell.
+// Cell of sample j: false when the cell lies outside the view (all corners
+// read tau). f receives the fractional position in the cell; *idx the record
+// index (dense view) or the cell's brick in the brick grid, *loc then its cell
+// within the brick (sparse view).
+template <bool SPARSE>
 __device__ inline bool sample_cell(const SoftView& S, const PointCell& pc, const Dir& d, int j,
-                                   float f[3], uint32_t* idx) {
+                                   float f[3], uint32_t* idx, uint32_t* loc) {
   const float t = __fadd_rn(d.e, (float)j);
   int c[3];
   bool in = pc.ok;
@@ -168,11 +172,20 @@ __device__ inline bool sample_cell(const SoftView& S, const PointCell& pc, const
     const float fl = floorf(l);
     f[i] = l - fl;  // exact
     const bool ok = fabsf(l) < 1.0e7f;
-    c[i] = ok ? (int)pc.I[i] + (int)fl - S.lo[i] : -1;
-    in = in && ok && (unsigned)c[i] < (unsigned)S.ncell[i];
+    const int base = SPARSE ? S.glo[i] : S.lo[i];
+    const int lim = SPARSE ? 8 * S.gdim[i] : S.ncell[i];
+    c[i] = ok ? (int)pc.I[i] + (int)fl - base : -1;
+    in = in && ok && (unsigned)c[i] < (unsigned)lim;
   }
-  *idx = ((uint32_t)c[2] * (uint32_t)S.ncell[1] + (uint32_t)c[1]) * (uint32_t)S.ncell[0] +
-         (uint32_t)c[0];
+  if (SPARSE) {
+    *idx = ((uint32_t)(c[2] >> 3) * (uint32_t)S.gdim[1] + (uint32_t)(c[1] >> 3)) *
+               (uint32_t)S.gdim[0] + (uint32_t)(c[0] >> 3);
+    *loc = (uint32_t)((c[0] & 7) | ((c[1] & 7) << 3) | ((c[2] & 7) << 6));
+  } else {
+    *idx = ((uint32_t)c[2] * (uint32_t)S.ncell[1] + (uint32_t)c[1]) * (uint32_t)S.ncell[0] +
+           (uint32_t)c[0];
+    *loc = 0;
+  }
   return in;
 }
 
@@ -291,7 +304,7 @@ struct Softmin {
 };
 
 // One corner record, 32 bytes, in one 256-bit read-only load.
-__device__ inline void load_cell(const SoftView& S, uint32_t idx, float4& lo, float4& hi) {
+__device__ inline void load_cell(const SoftView& S, size_t idx, float4& lo, float4& hi) {
   const float4* p = S.cells + 2 * (size_t)idx;
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z),
@@ -326,7 +339,7 @@ constexpr int kInFlightRefine = 4;
 // C of one pair and, with GRAD, dC / d(alpha, beta, h); *cmin = min_j phi_j.
 // Called by all kLanes lanes of the pair's group (lane g of it); with
 // `live` false the lane samples nothing.
-template <bool GRAD, bool FIXED, int NF>
+template <bool GRAD, bool FIXED, bool SPARSE, int NF>
 __device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const Dir& d,
                                   const float t1[3], const float t2[3], bool live, int g,
                                   float* ga, float* gb, float* gh, float* cmin) {
@@ -334,17 +347,29 @@ __device__ inline float soft_eval(const SoftView& S, const PointCell& pc, const 
   if (live) {
     for (int j = S.j0 + g; j <= S.J; j += NF * kLanes) {
       float f[NF][3];
-      uint32_t id[NF];
+      uint32_t id[NF], loc[NF];
+      size_t rec[NF];
       bool has[NF], in[NF];
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
         has[q] = j + q * kLanes <= S.J;
-        in[q] = has[q] && sample_cell(S, pc, d, j + q * kLanes, f[q], &id[q]);
+        in[q] = has[q] && sample_cell<SPARSE>(S, pc, d, j + q * kLanes, f[q], &id[q], &loc[q]);
+        rec[q] = id[q];
+      }
+      if (SPARSE) {  // the slots of the cells' bricks first, then the records
+        uint32_t slot[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) slot[q] = in[q] ? __ldg(S.bgrid + id[q]) : kNoBlock;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+          in[q] = in[q] && slot[q] != kNoBlock;
+          rec[q] = (size_t)slot[q] * kBrickVox + loc[q];
+        }
       }
       float4 lo[NF], hi[NF];
 #pragma unroll
       for (int q = 0; q < NF; ++q)
-        if (in[q]) load_cell(S, id[q], lo[q], hi[q]);
+        if (in[q]) load_cell(S, rec[q], lo[q], hi[q]);
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
         if (!has[q]) break;
@@ -416,7 +441,7 @@ struct GroupWalk {
   }
 };
 
-template <bool GRAD, bool FIXED>
+template <bool GRAD, bool FIXED, bool SPARSE>
 __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restrict__ pts,
                                               uint32_t per_point, const float* __restrict__ u0,
                                               const float* __restrict__ alpha,
@@ -438,8 +463,8 @@ __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restric
     const Dir d = make_dir(S, u, t1, t2, __ldg(alpha + i), __ldg(beta + i), __ldg(hh + i));
     const bool fin = pc.finite && d.finite;
     float da, db, dh, mn;
-    float C = soft_eval<GRAD, FIXED, kInFlightField>(S, pc, d, t1, t2, fin && act, w.g, &da, &db,
-                                                     &dh, &mn);
+    float C = soft_eval<GRAD, FIXED, SPARSE, kInFlightField>(S, pc, d, t1, t2, fin && act, w.g,
+                                                             &da, &db, &dh, &mn);
     if (!act || w.g != 0) continue;
     if (!fin) C = mn = da = db = dh = NAN;
     if (c) c[i] = C;
@@ -455,7 +480,7 @@ __global__ void __launch_bounds__(128) k_soft(SoftView S, const float* __restric
 
 // `steps` ascent steps on C per pair in registers, then C at the final state.
 // The group's lanes update identical copies of (alpha, beta, h).
-template <bool FIXED>
+template <bool FIXED, bool SPARSE>
 __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
                                                      const float* __restrict__ pts,
                                                      uint32_t per_point,
@@ -482,7 +507,8 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
       const Dir d = make_dir(S, u, t1, t2, al, be, h);
       const bool live = fin && act && d.finite;
       float da, db, dh, mn;
-      soft_eval<true, FIXED, kInFlightRefine>(S, pc, d, t1, t2, live, w.g, &da, &db, &dh, &mn);
+      soft_eval<true, FIXED, SPARSE, kInFlightRefine>(S, pc, d, t1, t2, live, w.g, &da, &db, &dh,
+                                                      &mn);
       if (live) {
         al = __fmaf_rn(R.lr_dir, da, al);
         be = __fmaf_rn(R.lr_dir, db, be);
@@ -492,9 +518,8 @@ __global__ void __launch_bounds__(128) k_soft_refine(SoftView S, RefineArgs R,
     const Dir d = make_dir(S, u, t1, t2, al, be, h);
     const bool ok = fin && d.finite;
     float mn;
-    float C = soft_eval<false, FIXED, kInFlightRefine>(S, pc, d, t1, t2, ok && act, w.g, nullptr,
-                                                        nullptr, nullptr,
-                                      &mn);
+    float C = soft_eval<false, FIXED, SPARSE, kInFlightRefine>(S, pc, d, t1, t2, ok && act, w.g,
+                                                                nullptr, nullptr, nullptr, &mn);
     if (!act || w.g != 0) continue;
     if (!ok) C = mn = al = be = h = NAN;
     alpha[i] = al;
@@ -559,6 +584,98 @@ static unsigned grid_for(size_t n, int threads, int num_sms, int per_sm) {
   return (unsigned)(want < cap ? (want ? want : 1) : cap);
 }
 
+// ---- the brick-sparse view ----
+//
+// A cell (low corner c, corners c + {0,1}^3) has corners in the bricks of c
+// and the ones above it on each axis, so a cell with a corner in an
+// allocated brick B has its low corner in B - e for some e in {0,1}^3; every
+// other cell reads tau at all corners. The grid covers the box's bricks and
+// one layer below (cells whose low corner lies one voxel below the box);
+// each brick of {B - e} gets a slot of 512 corner records, the others none.
+
+// Marks every grid brick B - e (B allocated, e in {0,1}^3) with a slot; one
+// thread per (allocated brick, e).
+__global__ void __launch_bounds__(256) k_sview_mark(MapView M, uint32_t* __restrict__ bgrid,
+                                                    int gx, int gy, uint32_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ nslots) {
+  const uint32_t count = min(__ldcg(&M.ctl->pool_count), M.pool_blocks);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count * 8u;
+       i += gridDim.x * blockDim.x) {
+    const uint64_t key = M.bkey[i >> 3];
+    const int e = (int)(i & 7u);
+    // grid coordinates: box-relative brick + 1 (the layer below the box is 0)
+    const int x = (int)(key & 0x1FFFFF) + 1 - (e & 1), y = (int)((key >> 21) & 0x1FFFFF) + 1 - ((e >> 1) & 1),
+              z = (int)(key >> 42) + 1 - (e >> 2);
+    const uint32_t t = ((uint32_t)z * (uint32_t)gy + (uint32_t)y) * (uint32_t)gx + (uint32_t)x;
+    if (atomicCAS(bgrid + t, kNoBlock, kNoBlock - 1u) == kNoBlock) {
+      const uint32_t s = atomicAdd(nslots, 1u);
+      keys[s] = t;
+      bgrid[t] = s;
+    }
+  }
+}
+
+// The 512 corner records of every slot: one CTA of 512 threads per slot, the
+// pool indices of the 8 bricks its cells' corners can lie in looked up once.
+__global__ void __launch_bounds__(512) k_sview_fill(MapView M, const uint32_t* __restrict__ keys,
+                                                    uint32_t nslots, int gx, int gy,
+                                                    float4* __restrict__ cells) {
+  __shared__ uint32_t s_nb[8];
+  const int l = threadIdx.x;
+  const int X = M.dim_vox[0], Y = M.dim_vox[1], Z = M.dim_vox[2];
+  for (uint32_t s = blockIdx.x; s < nslots; s += gridDim.x) {
+    const uint32_t t = keys[s];
+    // box-relative brick of the slot's low corners
+    const int bx = (int)(t % (uint32_t)gx) - 1, by = (int)((t / (uint32_t)gx) % (uint32_t)gy) - 1,
+              bz = (int)(t / ((uint32_t)gx * (uint32_t)gy)) - 1;
+    __syncthreads();  // s_nb of the previous slot is no longer read
+    if (l < 8) {
+      const int x = bx + (l & 1), y = by + ((l >> 1) & 1), z = bz + (l >> 2);
+      s_nb[l] = (x >= 0 && y >= 0 && z >= 0 && x * 8 < X && y * 8 < Y && z * 8 < Z)
+                    ? lookup_brick(M, pack_brick(x, y, z))
+                    : kNoBlock;
+    }
+    __syncthreads();
+    const int vx = bx * 8 + (l & 7), vy = by * 8 + ((l >> 3) & 7), vz = bz * 8 + (l >> 6);
+    float c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int x = vx + (k & 1), y = vy + ((k >> 1) & 1), z = vz + (k >> 2);
+      float d = M.tau;  // outside the box, unallocated, or w = 0
+      if (x >= 0 && y >= 0 && z >= 0 && x < X && y < Y && z < Z) {
+        const uint32_t b = s_nb[((x >> 3) - bx) | (((y >> 3) - by) << 1) | (((z >> 3) - bz) << 2)];
+        if (b != kNoBlock) {
+          const unsigned long long word =
+              __ldcg(M.vox + (size_t)b * kBrickVox + ((x & 7) | ((y & 7) << 3) | ((z & 7) << 6)));
+          const unsigned long long w = word & kWMask;
+          if (w) d = __double2float_rn((double)word_S(word) / ((double)w * 1048576.0));
+        }
+      }
+      c[k] = d;
+    }
+    float4* rec = cells + 2 * ((size_t)s * kBrickVox + l);
+    rec[0] = make_float4(c[0], c[1], c[2], c[3]);
+    rec[1] = make_float4(c[4], c[5], c[6], c[7]);
+  }
+}
+
+cudaError_t launch_sview_mark(const MapView& M, int num_sms, uint32_t* bgrid, size_t gcount,
+                              int gx, int gy, uint32_t* keys, uint32_t* nslots, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(bgrid, 0xFF, gcount * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nslots, 0, 4, stream);
+  if (e != cudaSuccess) return e;
+  k_sview_mark<<<num_sms * 8, 256, 0, stream>>>(M, bgrid, gx, gy, keys, nslots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sview_fill(const MapView& M, int num_sms, const uint32_t* keys, uint32_t nslots,
+                              int gx, int gy, float4* cells, cudaStream_t stream) {
+  if (nslots == 0) return cudaSuccess;
+  k_sview_fill<<<(unsigned)std::min<uint32_t>(nslots, (uint32_t)num_sms * 4), 512, 0, stream>>>(
+      M, keys, nslots, gx, gy, cells);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_views(const MapView& M, int num_sms, bool fill, float* dense, float4* cells,
                          cudaStream_t stream) {
   const size_t nd = (size_t)M.dim_vox[0] * M.dim_vox[1] * M.dim_vox[2];
@@ -584,9 +701,11 @@ cudaError_t launch_soft(const SoftView& S, bool grad, const float* pts, uint32_t
                         float* gb, float* gh, int num_sms, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   const unsigned g = grid_for(n * kLanes, 128, num_sms, 16);
-#define AF_SOFT_LAUNCH(GR, FX)                                                                 \
-  k_soft<GR, FX><<<g, 128, 0, stream>>>(S, pts, per_point, u0, al, be, h, n, gc, c, cmin, ga,  \
-                                        gb, gh)
+#define AF_SOFT_LAUNCH(GR, FX)                                                                  \
+  (S.sparse ? k_soft<GR, FX, true><<<g, 128, 0, stream>>>(S, pts, per_point, u0, al, be, h, n, gc, \
+                                                         c, cmin, ga, gb, gh)                    \
+            : k_soft<GR, FX, false><<<g, 128, 0, stream>>>(S, pts, per_point, u0, al, be, h, n,   \
+                                                          gc, c, cmin, ga, gb, gh))
   if (grad && S.fixed)
     AF_SOFT_LAUNCH(true, true);
   else if (grad)
@@ -605,10 +724,17 @@ cudaError_t launch_soft_refine(const SoftView& S, const RefineArgs& R, const flo
                                cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   const unsigned g = grid_for(n * kLanes, 128, num_sms, 16);
-  if (S.fixed)
-    k_soft_refine<true><<<g, 128, 0, stream>>>(S, R, pts, per_point, u0, al, be, h, n, c, cmin);
+#define AF_REFINE_LAUNCH(FX, SP) \
+  k_soft_refine<FX, SP><<<g, 128, 0, stream>>>(S, R, pts, per_point, u0, al, be, h, n, c, cmin)
+  if (S.fixed && S.sparse)
+    AF_REFINE_LAUNCH(true, true);
+  else if (S.fixed)
+    AF_REFINE_LAUNCH(true, false);
+  else if (S.sparse)
+    AF_REFINE_LAUNCH(false, true);
   else
-    k_soft_refine<false><<<g, 128, 0, stream>>>(S, R, pts, per_point, u0, al, be, h, n, c, cmin);
+    AF_REFINE_LAUNCH(false, false);
+#undef AF_REFINE_LAUNCH
   return cudaGetLastError();
 }
 

@@ -6,7 +6,10 @@ voxel hit); sampled voxel clusters and point clusters are checked bit for
 bit against an oracle built from only the returns that can affect them: a
 voxel's state depends on returns whose cube holds it or whose cleared band
 reaches it (within 0.15 m), a point's label on voxels within its kernels'
-reach (L + L_c + r = 1.8 m), so on returns within 2.0 m."""
+reach (L + L_c + r = 1.8 m), so on returns within 2.0 m. The soft clearance
+and its refinement run on the brick-sparse SDF view (the box's dense view
+would need over 2^31 cells) and are checked against the oracle on a sampled
+point cluster."""
 import numpy as np
 import pytest
 
@@ -117,3 +120,43 @@ def test_sampled_points_labels(large):
     np.testing.assert_array_equal(lab[near], ol)
     np.testing.assert_array_equal(best[near], ob)
     assert (ol == af.ACCESSIBLE).sum() >= 4 and (ol == af.BLOCKED).sum() >= 4
+
+
+def test_sampled_soft_refinement_sparse_view(large):
+    """The differentiable step on the large map: the dense view does not fit
+    the 40 x 40 m box at 1 cm, so the brick-sparse one is built; C before and
+    after 20 ascent steps from the best table direction of a cluster of
+    accessible points, within 1e-5 m of the oracle's trajectories."""
+    import torch
+    W, frames, g, P, N, lab, best = large
+    M = W.af_config(**CAPS)
+    cells = 1
+    for k in range(3):
+        cells *= 8 * M.domain_bricks[k] + 1
+    assert cells >= 1 << 31                      # automatic choice: the sparse view
+    rng = np.random.default_rng(13)
+    acc = np.nonzero(lab == af.ACCESSIBLE)[0]
+    seed = rng.choice(acc)
+    near = acc[np.argsort(np.linalg.norm(P[acc] - P[seed], axis=1))[:24]]
+    Pd, Nd = to_dev(P[near]), to_dev(N[near])
+    l, b = g.score(Pd, Nd)
+    u0 = g.soft_start(l, b)
+    z = torch.zeros(len(near), dtype=torch.float32, device="cuda")
+    c0 = g.soft_clearance_raw(Pd, u0, z, z, z, 1).cpu().numpy()
+    al, be, hh = z.clone(), z.clone(), z.clone()
+    c, cmin = g.soft_refine(Pd, u0, al, be, hh, 1, steps=20, lr_dir=0.05, lr_h=0.005, h_max=0.05)
+    c, cmin, hh = c.cpu().numpy(), cmin.cpu().numpy(), hh.cpu().numpy()
+    assert g.sync_status() == 0
+    om = _oracle_near(W, frames, P[near].astype(np.float64), POINT_RADIUS + 0.05)
+    tool = oracle_tool(W)
+    pts, dirs0 = P[near], W.dirs[best[near]]
+    zz = np.zeros(len(near), np.float32)
+    oc0, _ = om.soft_clearance(tool, pts, 1, dirs0, zz, zz, zz, af.TAU_S)
+    np.testing.assert_allclose(c0, oc0, rtol=0, atol=1e-5)
+    ra, rb, rh, rc, rm = om.soft_refine(tool, pts, 1, dirs0, zz, zz, zz, 20, 0.05, 0.005, 0.05)
+    close = np.abs(c - rc) <= 1e-5
+    # a trajectory may part from the oracle's at a kink met within rounding
+    assert close.sum() >= len(close) - 1, np.abs(c - rc)
+    assert (np.abs(cmin - rm)[close] <= 1e-5).all()
+    assert (np.abs(hh - rh)[close] <= 1e-4).all()
+    assert np.ptp(c0) > 0                        # the samples read the map, not only tau

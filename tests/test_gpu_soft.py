@@ -6,7 +6,8 @@ every pair where the oracle shows the difference interval free of the kinks
 of trilinear interpolation, per pair within 1e-3 relative plus what single
 precision lets the difference resolve (measured against the oracle); the autograd Function equal to the adjoint;
 refinement and the per-point best exactly self-consistent and within
-tolerance of the oracle's trajectories; views rebuilt after a new scan."""
+tolerance of the oracle's trajectories; views rebuilt after a new scan; the
+brick-sparse view giving the dense view's results bit for bit."""
 import numpy as np
 import pytest
 
@@ -279,3 +280,27 @@ def test_start_from_plain_best(scene):
     ra, rb, rh, rc, rm = om.soft_refine(oracle_tool(W), P[acc], 1, W.dirs[best_h[acc]],
                                         z[acc], z[acc], z[acc], 20, 0.05, 0.005, 0.05)
     assert (np.abs(c[acc] - rc) <= 1e-5).mean() >= 0.99
+
+
+def test_sparse_view_equals_dense(scene):
+    """The brick-sparse SDF view holds the same corner values as the dense
+    one, so clearance, adjoint and refinement are identical bit for bit."""
+    import torch
+    W, fr, g, om, P, N, table, u0, al, be, h = scene
+    g2 = af.Map(W.af_config(**CAPS))
+    g2.set_tool(W.af_tool(), W.dirs)
+    g2.integrate_scan(to_dev(fr.pts), fr.pose)
+    g2.soft_set_view(2)
+    g.soft_set_view(1)
+    args = (_gpu(P), _gpu(u0), _gpu(al), _gpu(be), _gpu(h), K, TAU_S)
+    out = []
+    for m in (g, g2):
+        c = m.soft_clearance_raw(*args)
+        adj = m.soft_clearance_adjoint(*args)
+        a2, b2, h2 = _gpu(np.where(np.isfinite(al), al, 0)), _gpu(be), _gpu(h)
+        rc, rm = m.soft_refine(_gpu(P), _gpu(u0), a2, b2, h2, K, steps=5)
+        out.append([c, *adj, rc, rm, a2, b2, h2])
+    for x, y in zip(*out):
+        assert torch.equal(torch.nan_to_num(x, nan=7.0), torch.nan_to_num(y, nan=7.0))
+    assert g.sync_status() == 0 and g2.sync_status() == 0
+    g.soft_set_view(0)
