@@ -68,6 +68,9 @@ def _args():
     ap.add_argument("--points", action="store_true",
                     help="the stateful point layer over the pine stream")
     ap.add_argument("--points-budget", type=int, default=16384)
+    ap.add_argument("--points-trigger", choices=("sampled", "all", "brick"), default="sampled",
+                    help="--points: changed voxels within r_u drawn 256 per frame (the paper's), "
+                         "all of them, or the brick rule")
     ap.add_argument("--large", action="store_true",
                     help="the large map: 3,000 frames at 1 cm, then every surface point, K = 256")
     ap.add_argument("--score-split", type=int, default=None,
@@ -1121,6 +1124,11 @@ def run_large(args, local):
     return out
 
 
+# the neighbourhood trigger of Sec. 3.5 (ii): 256 changed voxels drawn per
+# frame (the paper's), all of them, or the brick rule
+POINTS_TRIGGERS = {"sampled": {}, "all": dict(trig_sample=0), "brick": dict(trig_exact=0)}
+
+
 def run_points(args, local):
     """The stateful point layer (Sec. 3.4, 3.5) over the pine stream: each
     step integrates one frame and updates the point set -- new points,
@@ -1139,13 +1147,14 @@ def run_points(args, local):
         tool.cos_theta_max = synth.COS_70
         dirs = synth.yaw_ring(180)
     c2f = dict(c2f_stride=10, c2f_half=12, c2f_radius=0.3) if args.c2f else {}
+    trig = POINTS_TRIGGERS[args.points_trigger]
     caps = dict(workload.BENCH_CAPS, clamp_signed=int(args.clamp_signed))
 
     def layer():
         m = af.Map(W.af_config(**caps))
         m.set_tool(tool, dirs)
         m.points_enable(af.PointsConfig(trig_tsdf=2 * W.params["v"], budget=args.points_budget,
-                                        capacity=1 << 21, **c2f))
+                                        capacity=1 << 21, **c2f, **trig))
         return m
     g = layer()
     d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
@@ -1187,6 +1196,7 @@ def run_points(args, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
         "data": "synthetic",
         "config": {"workload": W.name, "budget": args.points_budget,
+                   "trigger": args.points_trigger,
                    "directions": "yaw ring, 70 deg cone" if args.ring else "Fibonacci sphere",
                    "G": len(dirs), "search": "coarse-to-fine" if args.c2f else "full",
                    "clamp": "[-tau, tau]" if args.clamp_signed else "[0, tau]",

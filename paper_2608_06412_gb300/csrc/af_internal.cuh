@@ -289,7 +289,7 @@ struct PtCounters {
 };
 
 // The draw of changed voxels for the neighbourhood trigger: a radix
-// selection of the `trig_sample` smallest hashes, 16 bits per pass.
+// selection of the `trig_sample` smallest hashes, 11 bits per pass.
 struct PtSample {
   unsigned long long prefix;  // high bits of the selected bound found so far
   unsigned long long t;       // the largest hash drawn (all ones: every changed voxel)
@@ -307,7 +307,7 @@ struct PtView {
   unsigned long long* snapw;  // per dirty brick of the frame: its 512 voxel words before the scan
   uint32_t* snapc;            // ... and its 16 cleared-mark words
   uint32_t* chgmask;          // per dirty brick: 512 bits, voxels whose state changed
-  uint32_t* hist;             // 65536 bins of the draw's radix selection
+  uint32_t* hist;             // 2048 bins of the draw's radix selection
   PtSample* samp;
   int trig_exact;             // 1: changed voxels within trig_radius; 0: touched bricks
   int trig_radius;

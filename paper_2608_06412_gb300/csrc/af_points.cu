@@ -16,7 +16,7 @@
 //  k_pts_views    once per (point, scan): sensor sum and stored viewpoints
 //  k_pts_diff     per touched brick: the voxels whose stored state changed
 //  k_pts_hist / k_pts_pick
-//                 the draw: radix selection, 16 bits per pass, of the
+//                 the draw: radix selection, 11 bits per pass, of the
 //                 trig_sample smallest hashes of the changed voxels
 //  k_pts_scatter  every drawn changed voxel queues the points within r_u
 //  k_pts_trigger  one thread per point: TSDF change, brick rule, sensor
@@ -174,29 +174,47 @@ __global__ void __launch_bounds__(512) k_pts_diff(MapView M, PtView V) {
   }
 }
 
-// One pass of the draw: histogram of the 16-bit digit at `shift` of the
-// hashes of the changed voxels whose higher bits equal the prefix so far.
+// The draw's radix selection: digits of kDrawBits bits from the top of the
+// hash down (the last one narrower), at most kDrawPasses passes; it stops as
+// soon as a digit's bin holds exactly the draws still missing.
+constexpr int kDrawBits = 11;
+constexpr int kDrawBins = 1 << kDrawBits;
+constexpr int kDrawPasses = (64 + kDrawBits - 1) / kDrawBits;
+
+__device__ inline int draw_hi(int pass) { return 64 - kDrawBits * pass; }  // bits above the digit
+__device__ inline int draw_lo(int pass) { return max(0, 64 - kDrawBits * (pass + 1)); }
+
+// One pass of the draw: histogram (per CTA in shared memory, then merged) of
+// this pass's digit of the hashes of the changed voxels whose higher bits
+// equal the prefix found so far.
 __global__ void __launch_bounds__(512) k_pts_hist(MapView M, PtView V, int pass) {
+  __shared__ uint32_t s_hist[kDrawBins];
   const uint32_t k = V.trig_sample;
-  if (V.samp->done || k == 0 || V.C->nchanged <= k) return;
+  if (V.samp->done || k == 0 || V.C->nchanged <= k) return;  // uniform
   const unsigned long long prefix = V.samp->prefix;
-  const int shift = 48 - 16 * pass;
+  const int hi = draw_hi(pass), lo = draw_lo(pass);
+  const unsigned long long dmask = (1ull << (hi - lo)) - 1ull;
   const int l = threadIdx.x, lane = l & 31, wi = l >> 5;
+  for (int b = l; b < kDrawBins; b += 512) s_hist[b] = 0u;
+  __syncthreads();
   const uint32_t nd = min(__ldcg(&M.ctl->dirty_count), V.C->nsnap);
   for (uint32_t d = blockIdx.x; d < nd; d += gridDim.x) {
     if (!((V.chgmask[(size_t)d * 16 + wi] >> lane) & 1u)) continue;
     int x, y, z;
     brick_voxel(M, M.dirty[d], l, &x, &y, &z);
     const unsigned long long h = mix64(draw_key(M, x, y, z) ^ V.salt);
-    if (pass > 0 && (h >> (shift + 16)) != prefix) continue;
-    atomicAdd(V.hist + ((h >> shift) & 0xFFFFull), 1u);
+    if (pass > 0 && (h >> hi) != prefix) continue;
+    atomicAdd(s_hist + ((h >> lo) & dmask), 1u);
   }
+  __syncthreads();
+  for (int b = l; b < kDrawBins; b += 512)
+    if (s_hist[b]) atomicAdd(V.hist + b, s_hist[b]);
 }
 
-// Picks the digit of this pass (one CTA of 1024 threads, 64 bins each) and
-// clears the histogram for the next pass. After the fourth pass the prefix
-// is the trig_sample-th smallest hash, the largest one drawn (hashes of
-// distinct voxels never tie: mix64 is a bijection).
+// Picks this pass's digit (one CTA, 2 bins per thread) and clears the
+// histogram. When the digit's bin holds exactly the draws still missing, or
+// after the last pass, t is final: every hash up to t is drawn, trig_sample
+// of them (hashes of distinct voxels never tie: mix64 is a bijection).
 __global__ void __launch_bounds__(1024) k_pts_pick(PtView V, int pass) {
   __shared__ uint32_t part[1024];
   PtSample* S = V.samp;
@@ -210,8 +228,8 @@ __global__ void __launch_bounds__(1024) k_pts_pick(PtView V, int pass) {
     }
   } else if (!S->done) {
     const uint32_t need = k - S->below;
-    uint32_t sum = 0;
-    for (int j = 0; j < 64; ++j) sum += V.hist[tid * 64 + j];
+    const uint32_t h0 = V.hist[2 * tid], h1 = V.hist[2 * tid + 1];
+    const uint32_t sum = h0 + h1;
     part[tid] = sum;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan
@@ -222,24 +240,21 @@ __global__ void __launch_bounds__(1024) k_pts_pick(PtView V, int pass) {
     }
     const uint32_t excl = part[tid] - sum;
     if (excl < need && need <= part[tid]) {
-      uint32_t c = excl;
-      for (int j = 0; j < 64; ++j) {
-        const uint32_t hv = V.hist[tid * 64 + j];
-        if (c + hv >= need) {
-          S->below += c;
-          S->prefix = (S->prefix << 16) | (unsigned long long)(tid * 64 + j);
-          if (pass == 3) {
-            S->t = S->prefix;
-            S->done = 1;
-          }
-          break;
-        }
-        c += hv;
+      const bool first = excl + h0 >= need;
+      const uint32_t dg = 2 * tid + (first ? 0 : 1), before = excl + (first ? 0u : h0);
+      const uint32_t cnt = first ? h0 : h1;
+      const int hi = draw_hi(pass), lo = draw_lo(pass);
+      S->below += before;
+      S->prefix = (S->prefix << (hi - lo)) | (unsigned long long)dg;
+      if (before + cnt == need || lo == 0) {
+        S->t = lo == 0 ? S->prefix : ((S->prefix << lo) | ((1ull << lo) - 1ull));
+        S->done = 1;
       }
     }
   }
   __syncthreads();
-  for (int j = 0; j < 64; ++j) V.hist[tid * 64 + j] = 0u;
+  V.hist[2 * tid] = 0u;
+  V.hist[2 * tid + 1] = 0u;
 }
 
 // Every drawn changed voxel (hash <= t) queues the points within r_u of it;
@@ -912,7 +927,7 @@ extern "C" af_status af_points_enable(af_ctx* ctx, const af_points_config* cfg) 
     if (e == cudaSuccess) e = alloc((void**)&ctx->d_psnapw, B * af::kBrickVox * 8, 0);
     if (e == cudaSuccess) e = alloc((void**)&ctx->d_psnapc, B * 16 * 4, 0);
     if (e == cudaSuccess) e = alloc((void**)&ctx->d_pchgmask, B * 16 * 4, 0);
-    if (e == cudaSuccess) e = alloc((void**)&ctx->d_phist, 65536 * 4, 0);
+    if (e == cudaSuccess) e = alloc((void**)&ctx->d_phist, af::kDrawBins * 4, 0);
     if (e == cudaSuccess) e = alloc((void**)&ctx->d_psamp, sizeof(af::PtSample), 0);
   }
   if (e == cudaSuccess) e = alloc((void**)&ctx->d_psel, P * 4, 0);
@@ -976,7 +991,7 @@ extern "C" af_status af_points_frame(af_ctx* ctx, const float* d_xyz, uint32_t n
     const unsigned grid = (unsigned)ctx->num_sms * 4;
     PT_CUDA(ctx, cudaMemsetAsync(ctx->d_psamp, 0, sizeof(af::PtSample), s));
     af::k_pts_diff<<<grid, 512, 0, s>>>(M, V);
-    for (int pass = 0; pass < 4; ++pass) {
+    for (int pass = 0; pass < af::kDrawPasses; ++pass) {
       af::k_pts_hist<<<grid, 512, 0, s>>>(M, V, pass);
       af::k_pts_pick<<<1, 1024, 0, s>>>(V, pass);
     }
