@@ -8,10 +8,12 @@
 //              so one probe per distinct key per warp reaches L2. The pool
 //              index of each cube brick goes into a per-return brick table,
 //              and the brick is marked dirty.
-//  k_integrate one CTA per tile of 16 returns, one thread per cube offset: the
+//  k_integrate one CTA per tile of 8 returns, one thread per cube offset: the
 //              tile's brick tables are loaded once (bricks created by this
-//              scan are looked up here), then each thread walks the tile's
-//              returns for its offset, computes d and adds
+//              scan are looked up here), and the per-axis terms of every
+//              return's sums (squares, products, brick / slot codes) are
+//              computed once into shared memory; then each thread walks the
+//              tile's returns for its offset, computes d and adds
 //              (round(d 2^20) << 20) | 1 to the voxel word with one 64-bit
 //              atomic; integer addition makes the result order-independent.
 //              The cleared-band marks follow, off the barrier path.
@@ -203,6 +205,13 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   __shared__ int4 s_b0[T];         // first brick of the cube
   __shared__ float s_bb[T];        // |p - q|^2 as rounded in single precision
   __shared__ uint32_t s_blk[T][NB];
+  // Per return, axis and cube offset k (voxel rel + k - MR on that axis),
+  // the rounded per-axis terms of the three sums the arithmetic needs --
+  // (x - p)^2, (x - p)(p - q), (x - q)^2 -- and the brick / voxel-slot code
+  // of that coordinate: a pair then adds three terms per sum in the order
+  // written (x, y, z), so every rounding is the same as computing it whole.
+  __shared__ float s_aa[T][3][W], s_ab[T][3][W], s_cc[T][3][W];
+  __shared__ int s_code[T][3][W];
 
   if (__ldcg(&M.ctl->status) != 0u) return;  // sticky capacity error: skip the scan
   __syncthreads();  // a previous tile of this CTA may still read the tables
@@ -259,41 +268,53 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   }
   __syncthreads();
 
+  // per-axis terms of every (return, axis, offset)
+  const float v = M.v, tau = M.tau, cone = M.cone_cos;
+  for (int e = tid; e < T * 3 * W; e += NT) {
+    const int t = e / (3 * W), ax = (e / W) % 3, k = e % W;
+    const float4 p = s_p[t];
+    if (p.w == 0.f) continue;
+    const int4 rel = s_rel[t];
+    const int4 b0 = s_b0[t];
+    const int j = (ax == 0 ? rel.x : (ax == 1 ? rel.y : rel.z)) + k - MR;  // box-relative voxel
+    const float pa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+    const float x = voxel_centre(j + M.dom_vox[ax], v);
+    const float a = __fsub_rn(x, pa), b = __fsub_rn(pa, q[ax]), c = __fsub_rn(x, q[ax]);
+    s_aa[t][ax][k] = __fmul_rn(a, a);
+    s_ab[t][ax][k] = __fmul_rn(a, b);
+    s_cc[t][ax][k] = __fmul_rn(c, c);
+    // brick offset within the tile's brick table (weight 1, BA, BA^2) in the
+    // high half, the voxel's slot bits within its brick in the low half
+    const int bk = (j >> 3) - (ax == 0 ? b0.x : (ax == 1 ? b0.y : b0.z));
+    s_code[t][ax][k] = ((bk * (ax == 0 ? 1 : (ax == 1 ? BA : BA * BA))) << 16) | ((j & 7) << (3 * ax));
+  }
+  __syncthreads();
+
   // This thread's cube offsets (ox fastest, so neighbouring threads update
-  // neighbouring voxel words).
-  int ox[OPT], oy[OPT], oz[OPT];
+  // neighbouring voxel words), as indices k = o + MR.
+  int kx[OPT], ky[OPT], kz[OPT];
 #pragma unroll
   for (int s = 0; s < OPT; ++s) {
     const int o = tid + s * NT;
-    ox[s] = o % W - MR;
-    oy[s] = (o / W) % W - MR;
-    oz[s] = o / (W * W) - MR;
+    kx[s] = o % W;
+    ky[s] = (o / W) % W;
+    kz[s] = o / (W * W);
   }
 
-  const float v = M.v, tau = M.tau, cone = M.cone_cos;
   for (int t = 0; t < T; ++t) {
     const float4 p = s_p[t];
     if (p.w == 0.f) continue;  // uniform across the block
-    const int4 rel = s_rel[t];
-    const int4 b0 = s_b0[t];
-    const float range = __int_as_float(rel.w);
+    const float range = __int_as_float(s_rel[t].w);
     const float bb = s_bb[t];
-    const float bq0 = __fsub_rn(p.x, q0), bq1 = __fsub_rn(p.y, q1), bq2 = __fsub_rn(p.z, q2);
 #pragma unroll
     for (int s = 0; s < OPT; ++s) {
       if (tid + s * NT >= C) break;
-      const int jx = rel.x + ox[s], jy = rel.y + oy[s], jz = rel.z + oz[s];
-      // voxel centre x (absolute index)
-      const float x0 = voxel_centre(jx + M.dom_vox[0], v);
-      const float x1 = voxel_centre(jy + M.dom_vox[1], v);
-      const float x2 = voxel_centre(jz + M.dom_vox[2], v);
       // behind-surface cone: theta between x - p and p - q; excluded iff
       // RN(dot / RN(RN(sqrt(aa)) * range)) > cone
-      const float a0 = __fsub_rn(x0, p.x), a1 = __fsub_rn(x1, p.y), a2 = __fsub_rn(x2, p.z);
-      const float aa = __fadd_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(a1, a1)), __fmul_rn(a2, a2));
+      const float aa = __fadd_rn(__fadd_rn(s_aa[t][0][kx[s]], s_aa[t][1][ky[s]]), s_aa[t][2][kz[s]]);
       if (aa > 0.f) {
         const float dot =
-            __fadd_rn(__fadd_rn(__fmul_rn(a0, bq0), __fmul_rn(a1, bq1)), __fmul_rn(a2, bq2));
+            __fadd_rn(__fadd_rn(s_ab[t][0][kx[s]], s_ab[t][1][ky[s]]), s_ab[t][2][kz[s]]);
         // dot <= 0 makes the rounded cosine <= 0, so with cone >= 0 it is kept
         if (dot > 0.f || cone < 0.f) {
           bool decided = false;
@@ -306,8 +327,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
         }
       }
       // d = |p - q| - |x - q|, clamped to [0, tau] ([-tau, tau] in the ablation)
-      const float c0 = __fsub_rn(x0, q0), c1 = __fsub_rn(x1, q1), c2 = __fsub_rn(x2, q2);
-      const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
+      const float cc = __fadd_rn(__fadd_rn(s_cc[t][0][kx[s]], s_cc[t][1][ky[s]]), s_cc[t][2][kz[s]]);
       float d;
       if (cc >= bb && !M.clamp_signed) {
         d = 0.f;  // |x - q| >= |p - q|: the rounded difference is <= 0
@@ -318,12 +338,13 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
         d = d < M.dlo ? M.dlo : d;
         d = d > tau ? tau : d;
       }
-      const long long dq = __float2ll_rn(__fmul_rn(d, kScale));
-      const int bl = ((jx >> 3) - b0.x) + BA * (((jy >> 3) - b0.y) + BA * ((jz >> 3) - b0.z));
-      const uint32_t blk = s_blk[t][bl];
+      // |d| <= tau <= 1 m, so |d 2^20| < 2^31: the 32-bit conversion rounds
+      // exactly as a 64-bit one would, and stays off the FP64 pipe
+      const long long dq = (long long)__float2int_rn(__fmul_rn(d, kScale));
+      const int code = s_code[t][0][kx[s]] + s_code[t][1][ky[s]] + s_code[t][2][kz[s]];
+      const uint32_t blk = s_blk[t][code >> 16];
       if (blk >= M.pool_blocks) continue;
-      const int l = (jx & 7) | ((jy & 7) << 3) | ((jz & 7) << 6);
-      atomicAdd(M.vox + (size_t)blk * kBrickVox + l, make_word(dq, 1ull));
+      atomicAdd(M.vox + (size_t)blk * kBrickVox + (code & 0xFFFF), make_word(dq, 1ull));
     }
   }
 
@@ -343,8 +364,9 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   }
 }
 
-// Tiles of 16 returns for the single-map path.
-constexpr int kTile = 16;
+// Tiles of 8 returns for the single-map path (measured against 12, 16, 20,
+// 26 and 32 on the pine stream: the finest grid balances the last wave best).
+constexpr int kTile = 8;
 
 template <int W>
 __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
