@@ -193,7 +193,9 @@ af_status af_set_tool(af_ctx *ctx, const af_tool *tool, const float *h_dirs, uin
  *                        minimum scores), -1 if unscored or no candidate.
  * A direction's score is n_c + 1 when an arm sample is occupied or unknown or
  * the corridor holds an occupied voxel, else min(#occupied tool voxels, n_c).
- * Requires af_set_tool (else AF_ERR_STATE). Asynchronous on `stream`.
+ * Requires af_set_tool (else AF_ERR_STATE). Asynchronous on `stream`. Calls
+ * on one context must not overlap on different streams: the scorer takes
+ * points from a counter that the context owns.
  */
 af_status af_score(af_ctx *ctx, const float *d_pts, const float *d_normals, uint32_t m,
                    uint8_t *d_label, int16_t *d_best, void *stream);

@@ -440,7 +440,7 @@ extern "C" af_status af_create(const af_config* cfg, af_ctx** out) {
   if (st == AF_OK) st = alloc((void**)&c->d_best, Pm * 2, 0);
   if (st == AF_OK) st = alloc((void**)&c->d_over, Pm * sizeof(int2), 0);
   if (st == AF_OK) st = alloc((void**)&c->d_sres, Pm * 4, 0);
-  if (st == AF_OK) st = alloc((void**)&c->d_scount, 4, 0);
+  if (st == AF_OK) st = alloc((void**)&c->d_scount, 16, 0);  // split count, staged counters
   c->split_cap = (uint32_t)Pm;
   if (st == AF_OK && cudaMallocHost((void**)&c->h_status, 64) != cudaSuccess)
     st = fail(c, AF_ERR_CUDA, "pinned allocation failed");
@@ -545,7 +545,7 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
 
   const double v = (double)ctx->cfg.voxel_size, tau = (double)ctx->cfg.truncation;
   int reach[3] = {0, 0, 0};
-  std::vector<short4> runs;
+  std::vector<short4> runs, cruns;  // tool runs of every direction, then corridor runs
   std::vector<int4> dtab(G);
   std::vector<short4> arm(3 * G);
   for (uint32_t g = 0; g < G; ++g) {
@@ -562,9 +562,9 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
     dtab[g].x = (int)runs.size();
     to_runs(tool_o, v, u, ax, &runs);
     dtab[g].y = (int)runs.size();
-    dtab[g].z = (int)runs.size();
-    to_runs(corr_o, v, u, tool->corridor_strict ? 0 : ax, &runs);
-    dtab[g].w = (int)runs.size();
+    dtab[g].z = (int)cruns.size();
+    to_runs(corr_o, v, u, tool->corridor_strict ? 0 : ax, &cruns);
+    dtab[g].w = (int)cruns.size();
     for (const std::vector<Offset>* o : {&tool_o, &corr_o})
       for (const Offset& x : *o) {
         reach[0] = std::max(reach[0], std::abs(x.x));
@@ -576,6 +576,12 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
     for (int k = 0; k < 3; ++k)
       arm[3 * g + k] = make_short4((short)a[3 * k], (short)a[3 * k + 1], (short)a[3 * k + 2], 0);
   }
+  const int ntool = (int)runs.size();
+  for (uint32_t g = 0; g < G; ++g) {
+    dtab[g].z += ntool;
+    dtab[g].w += ntool;
+  }
+  runs.insert(runs.end(), cruns.begin(), cruns.end());
   if (runs.empty()) runs.push_back(make_short4(0, 1, 0, 0));  // keep the buffer non-empty
   // Fast-path form of the runs: the plane-word offset of the run's row relative to
   // the point's row, valid while every plane index fits in 31 bits. `reach` bounds
@@ -609,6 +615,7 @@ extern "C" af_status af_set_tool(af_ctx* ctx, const af_tool* tool, const float* 
   AF_CUDA(ctx, cudaMemcpy(ctx->d_fruns, fruns.data(), fruns.size() * sizeof(int2), cudaMemcpyHostToDevice));
   for (int k = 0; k < 3; ++k) ctx->T.reach[k] = reach[k];
   ctx->T.fruns = ctx->d_fruns;
+  ctx->T.ntool = ntool;
   ctx->T.nruns = (int)runs.size();
   ctx->T.ctl = ctx->M.ctl;
   AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_dtab, (size_t)G * sizeof(int4)));
@@ -648,7 +655,8 @@ extern "C" af_status af_score(af_ctx* ctx, const float* d_pts, const float* d_no
     AF_CUDA(ctx, cudaMalloc((void**)&ctx->d_sres, (size_t)m * 4));
     ctx->split_cap = m;
   }
-  const af::ScoreSplit S{ctx->d_over, ctx->d_sres, ctx->d_scount, ctx->score_budget};
+  const af::ScoreSplit S{ctx->d_over, ctx->d_sres, ctx->d_scount, ctx->score_budget,
+                         ctx->d_scount + 1};
   if (m > 0)
     AF_CUDA(ctx, timed(ctx, 3, s, [&] {
               return af::launch_score(ctx->M, ctx->T, d_pts, d_normals, m, d_label, d_best, S,

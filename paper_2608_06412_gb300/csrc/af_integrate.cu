@@ -183,6 +183,13 @@ __device__ inline float sqrt_approx(float x) { return x * rsqrtf(x); }
 
 constexpr float kMargin = 1.52587890625e-05f;  // 2^-16
 
+// The exact cone decision, RN(dot / RN(RN(sqrt(aa)) range)) > cone, out of
+// line: it runs only within 2^-16 of the threshold, so divergent lanes call it
+// instead of every lane carrying its instructions.
+__device__ __noinline__ bool cone_excludes_exact(float dot, float aa, float range, float cone) {
+  return __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range)) > cone;
+}
+
 template <int W>
 struct CubeShape {
   static constexpr int C = W * W * W;                                 // offsets
@@ -204,14 +211,15 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
   __shared__ int4 s_b0[T];         // first brick of the cube
   __shared__ float s_bb[T];        // |p - q|^2 as rounded in single precision
+  __shared__ float s_ir[T];        // RN(1 / |p - q|), for the approximate cone test
   __shared__ uint32_t s_blk[T][NB];
   // Per return, axis and cube offset k (voxel rel + k - MR on that axis),
   // the rounded per-axis terms of the three sums the arithmetic needs --
   // (x - p)^2, (x - p)(p - q), (x - q)^2 -- and the brick / voxel-slot code
-  // of that coordinate: a pair then adds three terms per sum in the order
-  // written (x, y, z), so every rounding is the same as computing it whole.
-  __shared__ float s_aa[T][3][W], s_ab[T][3][W], s_cc[T][3][W];
-  __shared__ int s_code[T][3][W];
+  // of that coordinate (as float bits), one 16-byte record: a pair then adds
+  // three terms per sum in the order written (x, y, z), so every rounding is
+  // the same as computing it whole.
+  __shared__ float4 s_term[T][3][W];
 
   if (__ldcg(&M.ctl->status) != 0u) return;  // sticky capacity error: skip the scan
   __syncthreads();  // a previous tile of this CTA may still read the tables
@@ -223,11 +231,12 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     const uint32_t k = r0 + tid;
     float4 p = k < n ? ret[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     int4 rel = make_int4(0, 0, 0, 0), b0 = make_int4(0, 0, 0, 0);
-    float bb = 0.f;
+    float bb = 0.f, ir = 0.f;
     if (p.w != 0.f) {
       const float b[3] = {__fsub_rn(p.x, q0), __fsub_rn(p.y, q1), __fsub_rn(p.z, q2)};
       bb = __fadd_rn(__fadd_rn(__fmul_rn(b[0], b[0]), __fmul_rn(b[1], b[1])), __fmul_rn(b[2], b[2]));
       const float range = __fsqrt_rn(bb);
+      ir = __frcp_rn(range);
       int i[3];
       voxel_index(p.x, M, &i[0]);
       voxel_index(p.y, M, &i[1]);
@@ -240,6 +249,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     s_rel[tid] = rel;
     s_b0[tid] = b0;
     s_bb[tid] = bb;
+    s_ir[tid] = ir;
   }
   // The tile's brick tables; bricks created by this scan are looked up now.
   for (int e = tid; e < T * NB; e += NT) {
@@ -280,13 +290,12 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     const float pa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
     const float x = voxel_centre(j + M.dom_vox[ax], v);
     const float a = __fsub_rn(x, pa), b = __fsub_rn(pa, q[ax]), c = __fsub_rn(x, q[ax]);
-    s_aa[t][ax][k] = __fmul_rn(a, a);
-    s_ab[t][ax][k] = __fmul_rn(a, b);
-    s_cc[t][ax][k] = __fmul_rn(c, c);
     // brick offset within the tile's brick table (weight 1, BA, BA^2) in the
     // high half, the voxel's slot bits within its brick in the low half
     const int bk = (j >> 3) - (ax == 0 ? b0.x : (ax == 1 ? b0.y : b0.z));
-    s_code[t][ax][k] = ((bk * (ax == 0 ? 1 : (ax == 1 ? BA : BA * BA))) << 16) | ((j & 7) << (3 * ax));
+    const int code = ((bk * (ax == 0 ? 1 : (ax == 1 ? BA : BA * BA))) << 16) | ((j & 7) << (3 * ax));
+    s_term[t][ax][k] = make_float4(__fmul_rn(a, a), __fmul_rn(a, b), __fmul_rn(c, c),
+                                   __int_as_float(code));
   }
   __syncthreads();
 
@@ -305,29 +314,30 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     const float4 p = s_p[t];
     if (p.w == 0.f) continue;  // uniform across the block
     const float range = __int_as_float(s_rel[t].w);
-    const float bb = s_bb[t];
+    const float bb = s_bb[t], ir = s_ir[t];
 #pragma unroll
     for (int s = 0; s < OPT; ++s) {
       if (tid + s * NT >= C) break;
+      const float4 tx = s_term[t][0][kx[s]], ty = s_term[t][1][ky[s]], tz = s_term[t][2][kz[s]];
+      const float aa = __fadd_rn(__fadd_rn(tx.x, ty.x), tz.x);
       // behind-surface cone: theta between x - p and p - q; excluded iff
       // RN(dot / RN(RN(sqrt(aa)) * range)) > cone
-      const float aa = __fadd_rn(__fadd_rn(s_aa[t][0][kx[s]], s_aa[t][1][ky[s]]), s_aa[t][2][kz[s]]);
       if (aa > 0.f) {
-        const float dot =
-            __fadd_rn(__fadd_rn(s_ab[t][0][kx[s]], s_ab[t][1][ky[s]]), s_ab[t][2][kz[s]]);
+        const float dot = __fadd_rn(__fadd_rn(tx.y, ty.y), tz.y);
         // dot <= 0 makes the rounded cosine <= 0, so with cone >= 0 it is kept
         if (dot > 0.f || cone < 0.f) {
           bool decided = false;
           if (aa > 1e-20f) {
-            const float ca = __fdividef(dot, sqrt_approx(aa) * range);
+            // a few ulp from the exact cosine (rsqrtf, two products, RN(1 / range))
+            const float ca = dot * rsqrtf(aa) * ir;
             if (ca > cone + kMargin) continue;  // certainly excluded
             decided = ca < cone - kMargin;      // certainly kept
           }
-          if (!decided && __fdiv_rn(dot, __fmul_rn(__fsqrt_rn(aa), range)) > cone) continue;
+          if (!decided && cone_excludes_exact(dot, aa, range, cone)) continue;
         }
       }
       // d = |p - q| - |x - q|, clamped to [0, tau] ([-tau, tau] in the ablation)
-      const float cc = __fadd_rn(__fadd_rn(s_cc[t][0][kx[s]], s_cc[t][1][ky[s]]), s_cc[t][2][kz[s]]);
+      const float cc = __fadd_rn(__fadd_rn(tx.z, ty.z), tz.z);
       float d;
       if (cc >= bb && !M.clamp_signed) {
         d = 0.f;  // |x - q| >= |p - q|: the rounded difference is <= 0
@@ -341,7 +351,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
       // |d| <= tau <= 1 m, so |d 2^20| < 2^31: the 32-bit conversion rounds
       // exactly as a 64-bit one would, and stays off the FP64 pipe
       const long long dq = (long long)__float2int_rn(__fmul_rn(d, kScale));
-      const int code = s_code[t][0][kx[s]] + s_code[t][1][ky[s]] + s_code[t][2][kz[s]];
+      const int code = __float_as_int(tx.w) + __float_as_int(ty.w) + __float_as_int(tz.w);
       const uint32_t blk = s_blk[t][code >> 16];
       if (blk >= M.pool_blocks) continue;
       atomicAdd(M.vox + (size_t)blk * kBrickVox + (code & 0xFFFF), make_word(dq, 1ull));

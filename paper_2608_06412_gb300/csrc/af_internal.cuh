@@ -121,6 +121,8 @@ struct ScoreSplit {
   uint32_t* res;     // packed (score << 16 | direction) of the search so far
   uint32_t* count;   // points handed off
   int budget;        // directions past the arm screen before a hand-off; < 0: never
+  uint32_t* work;    // the staged scorer's next-point and finished-warp counters (zero
+                     // between launches)
 };
 
 struct ToolView {
@@ -129,6 +131,7 @@ struct ToolView {
   const int2* fruns;      // the same runs as (row delta in plane words, dx0 | len << 16)
   const int4* dtab;       // per direction: tool runs [x, y), corridor runs [z, w)
   const short4* arm;      // G x 3 arm-sample offsets
+  int ntool;              // every direction's tool runs come first: runs [0, ntool)
   int G;
   int n_c;
   float cos_max;

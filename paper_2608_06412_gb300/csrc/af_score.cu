@@ -1,6 +1,10 @@
 // af_score.cu -- accessibility scoring on sm_103a (Sec. 3.4, 3.5 of the paper).
 //
-// One warp per surface point. The lanes first evaluate the normal filter for
+// One warp per surface point. The plain form (k_score_staged) is a persistent
+// grid whose CTAs first copy the direction table, the arm offsets and the
+// tool runs into shared memory; the batched form and tables too large to
+// stage read them through the read-only path (k_score, k_score_batch).
+// The lanes first evaluate the normal filter for
 // 32 directions at a time (ballot -> candidate mask); the candidates are then
 // visited in index order, each by the whole warp:
 //   * tool kernel: lanes take x-runs of the precomputed kernel (32 runs per
@@ -26,12 +30,14 @@
 // of the heaviest point.
 //
 // The device functions live in af_score.cuh.
+#include <algorithm>
+
 #include "af_score.cuh"
 
 namespace af {
 
 // Scores point pi with the whole warp (all 32 lanes call this together).
-template <bool SPLIT>
+template <bool SPLIT, bool SM = false>
 __device__ void score_point(const MapView& M, const ToolView& T, const float* __restrict__ pts,
                             const float* __restrict__ nrm, uint32_t pi,
                             uint8_t* __restrict__ label, int16_t* __restrict__ best_out,
@@ -79,10 +85,11 @@ __device__ void score_point(const MapView& M, const ToolView& T, const float* __
   if (fast) set_rows(M, P); else P.row = P.rowy = P.rowz = 0;
   const NormalFilter F{n0, n1, n2};
   if (!SPLIT)
-    res = fast ? best_direction<true>(M, T, P, F, lane) : best_direction<false>(M, T, P, F, lane);
+    res = fast ? best_direction<true, NormalFilter, SM>(M, T, P, F, lane)
+               : best_direction<false, NormalFilter, SM>(M, T, P, F, lane);
   else
-    res = fast ? best_direction_budget<true>(M, T, P, F, lane, S.budget, &next)
-               : best_direction_budget<false>(M, T, P, F, lane, S.budget, &next);
+    res = fast ? best_direction_budget<true, NormalFilter, SM>(M, T, P, F, lane, S.budget, &next)
+               : best_direction_budget<false, NormalFilter, SM>(M, T, P, F, lane, S.budget, &next);
 
   if (lane == 0) {
     if (next < 0) {
@@ -106,6 +113,49 @@ __global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
   const uint32_t pi = blockIdx.x * WARPS + (threadIdx.x >> 5);
   if (pi >= m) return;  // whole warp
   score_point<SPLIT>(M, T, pts, nrm, pi, label, best_out, threadIdx.x & 31, S);
+}
+
+// Shared-memory bytes of the staged scorer's tables: direction table (16 B
+// per direction), arm offsets (24 B per direction), tool runs (8 B per run).
+__host__ __device__ inline size_t staged_bytes(const ToolView& T) {
+  return (size_t)T.G * 40 + (size_t)T.ntool * 8;
+}
+// Tables up to the default dynamic shared-memory limit are staged; larger ones
+// (many directions, long tools) are read through the read-only path.
+constexpr size_t kStagedMaxBytes = 48 * 1024;
+
+// The staged form of k_score: a persistent CTA copies the direction table,
+// the arm offsets and every direction's tool runs into shared memory once,
+// so that each step of a point's search waits on one L2 load (the plane
+// word) instead of a table entry and then a plane word. A warp scores point
+// (its warp index) first, then takes points from a launch-wide counter; the
+// last warp to finish zeroes the counters for the next launch (every other
+// warp has then taken its last point). The search itself is the same.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
+    k_score_staged(MapView M, ToolView T, const float* __restrict__ pts,
+                   const float* __restrict__ nrm, uint32_t m, uint8_t* __restrict__ label,
+                   int16_t* __restrict__ best_out, uint32_t* __restrict__ work) {
+  short4* s_arm = reinterpret_cast<short4*>(af_staged_tab + T.G);
+  int2* s_runs = reinterpret_cast<int2*>(reinterpret_cast<char*>(af_staged_tab) + 40 * T.G);
+  for (int i = threadIdx.x; i < T.G; i += WARPS * 32) af_staged_tab[i] = __ldg(T.dtab + i);
+  for (int i = threadIdx.x; i < 3 * T.G; i += WARPS * 32) s_arm[i] = __ldg(T.arm + i);
+  for (int i = threadIdx.x; i < T.ntool; i += WARPS * 32) s_runs[i] = __ldg(T.fruns + i);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = gridDim.x * WARPS;
+  uint32_t pi = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  while (pi < m) {
+    score_point<false, true>(M, T, pts, nrm, pi, label, best_out, lane,
+                             ScoreSplit{nullptr, nullptr, nullptr, -1, nullptr});
+    uint32_t nxt = 0;
+    if (lane == 0) nxt = nw + atomicAdd(work, 1u);
+    pi = __shfl_sync(0xffffffffu, nxt, 0);
+  }
+  if (lane == 0 && atomicAdd(work + 1, 1u) == nw - 1u) {
+    work[0] = 0u;
+    work[1] = 0u;
+  }
 }
 
 // One (point, direction) item of a handed-off search; the whole warp.
@@ -185,6 +235,19 @@ cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts
                          const float* d_nrm, uint32_t m, uint8_t* d_label, int16_t* d_best,
                          const ScoreSplit& S, int num_sms, cudaStream_t stream) {
   if (m == 0) return cudaSuccess;
+  constexpr int kStagedWarps = 32;
+  if (S.budget < 0 && S.work != nullptr && staged_bytes(T) <= kStagedMaxBytes) {
+    const size_t smem = staged_bytes(T);
+    int per = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per, k_score_staged<kStagedWarps>, kStagedWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const uint32_t need = (m + kStagedWarps - 1) / kStagedWarps;
+    const uint32_t grid = std::min<uint32_t>(need, (uint32_t)num_sms * (uint32_t)(per > 0 ? per : 1));
+    k_score_staged<kStagedWarps><<<grid, kStagedWarps * 32, smem, stream>>>(
+        M, T, d_pts, d_nrm, m, d_label, d_best, S.work);
+    return cudaGetLastError();
+  }
   constexpr int WARPS = 2;
   if (S.budget >= 0) {
     cudaError_t e = cudaMemsetAsync(S.count, 0, sizeof(uint32_t), stream);

@@ -67,11 +67,27 @@ struct RunEntry {
   int a, b;
 };
 
-template <bool FAST>
+// The staged scorer's copy of the tool tables in dynamic shared memory, in
+// this order: the direction table (G int4), the arm offsets (3 G short4) and
+// the tool runs in fast form (ntool int2, byte offset 40 G).
+extern __shared__ int4 af_staged_tab[];
+
+__device__ __forceinline__ int4 dtab_entry(const ToolView& T, int g, bool staged) {
+  return staged ? af_staged_tab[g] : __ldg(T.dtab + g);
+}
+
+__device__ __forceinline__ short4 arm_entry(const ToolView& T, int i, bool staged) {
+  return staged ? reinterpret_cast<const short4*>(af_staged_tab + T.G)[i] : __ldg(T.arm + i);
+}
+
+// Run r of the tables; SM: a tool run read from the staged copy.
+template <bool FAST, bool SM = false>
 __device__ inline RunEntry load_run(const ToolView& T, int r) {
-  if (!check_index((unsigned)r < (unsigned)T.nruns, T.ctl)) return {0, 0};  // an empty run
+  if (!check_index((unsigned)r < (unsigned)(SM ? T.ntool : T.nruns), T.ctl)) return {0, 0};  // an empty run
   if (FAST) {
-    const int2 f = __ldg(T.fruns + r);
+    const int2 f = SM ? reinterpret_cast<const int2*>(
+                            reinterpret_cast<const char*>(af_staged_tab) + 40 * T.G)[r]
+                      : __ldg(T.fruns + r);
     return {f.x, f.y};
   }
   const short4 s = __ldg(T.runs + r);
@@ -118,11 +134,11 @@ __device__ inline unsigned long long run_bits(const unsigned long long* __restri
 
 // Walks runs [r0, r1) of the tables a warp step (32 runs, one per lane) at a
 // time; the caller's `step(entry, valid)` returns true to stop the walk.
-template <bool FAST, class F>
+template <bool FAST, bool SM, class F>
 __device__ inline void walk_runs(const ToolView& T, int r0, int r1, int lane, F&& step) {
   for (int b = r0; b < r1; b += 32) {
     const int r = b + lane;
-    const RunEntry e = r < r1 ? load_run<FAST>(T, r) : RunEntry{0, 0};
+    const RunEntry e = r < r1 ? load_run<FAST, SM>(T, r) : RunEntry{0, 0};
     if (step(e, r < r1)) return;
   }
 }
@@ -141,12 +157,13 @@ __device__ inline bool bit_at(const unsigned long long* __restrict__ plane, cons
 }
 
 // Occupied tool voxels of direction g at point P, saturated at `sat`.
-template <bool FAST>
+// SM: the direction table and the tool runs are staged in shared memory.
+template <bool FAST, bool SM = false>
 __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, const Pt& P, int sat,
                                  int lane) {
-  const int4 dt = __ldg(T.dtab + g);
+  const int4 dt = dtab_entry(T, g, SM);
   int total = 0;
-  walk_runs<FAST>(T, dt.x, dt.y, lane, [&](RunEntry e, bool valid) {
+  walk_runs<FAST, SM && FAST>(T, dt.x, dt.y, lane, [&](RunEntry e, bool valid) {
     int c = 0;
     if (valid) {
       int len;
@@ -162,11 +179,11 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, con
 // The three arm samples of direction g (one lane): clear iff none is
 // occupied or unknown. All nine loads are issued together (no short
 // circuit), so the screen costs two dependent round trips, not up to nine.
-template <bool FAST>
+template <bool FAST, bool SM = false>
 __device__ inline bool arm_clear(const MapView& M, const ToolView& T, int g, const Pt& P) {
   short4 a[3];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) a[s] = __ldg(T.arm + 3 * g + s);
+  for (int s = 0; s < 3; ++s) a[s] = arm_entry(T, 3 * g + s, SM);
   bool blocked = false;
 #pragma unroll
   for (int s = 0; s < 3; ++s)
@@ -175,12 +192,12 @@ __device__ inline bool arm_clear(const MapView& M, const ToolView& T, int g, con
 }
 
 // Corridor of direction g: any occupied voxel (strict: or unknown) blocks.
-template <bool FAST>
+template <bool FAST, bool SM = false>
 __device__ inline bool corridor_blocked(const MapView& M, const ToolView& T, int g, const Pt& P,
                                         int lane) {
-  const int4 dt = __ldg(T.dtab + g);
+  const int4 dt = dtab_entry(T, g, SM);
   bool blocked = false;
-  walk_runs<FAST>(T, dt.z, dt.w, lane, [&](RunEntry e, bool valid) {
+  walk_runs<FAST, false>(T, dt.z, dt.w, lane, [&](RunEntry e, bool valid) {
     bool h = false;
     if (valid) {
       int len;
@@ -216,7 +233,9 @@ struct NormalFilter {
 // scores, with exact early exits; `cand(T, g)` says whether direction g is a
 // candidate of the point. Returns (best score, best index), (n_c + 2, -1)
 // without candidates.
-template <bool FAST, class Cand>
+// SM: the direction table, the arm offsets and the tool runs are staged in
+// shared memory (af_staged_tab).
+template <bool FAST, class Cand, bool SM = false>
 __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const Pt& P,
                                       const Cand& cand_of, int lane) {
   const int nc = T.n_c;
@@ -225,7 +244,7 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
     // lane-parallel screen: candidates, and the arm samples of each candidate
     const bool cand = cand_of(T, gb + lane);
     unsigned mask = __ballot_sync(0xffffffffu, cand);
-    const unsigned arm_ok = __ballot_sync(0xffffffffu, cand && arm_clear<FAST>(M, T, gb + lane, P));
+    const unsigned arm_ok = __ballot_sync(0xffffffffu, cand && arm_clear<FAST, SM>(M, T, gb + lane, P));
     while (mask) {
       const int bit = __ffs(mask) - 1;
       const int g = gb + bit;
@@ -240,21 +259,21 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
       }
       if (bscore <= nc) {
         // improves only if not blocked and strictly fewer collisions
-        const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
+        const int cnt = tool_count<FAST, SM>(M, T, g, P, bscore, lane);
         if (cnt >= bscore) continue;
-        if (corridor_blocked<FAST>(M, T, g, P, lane)) continue;
+        if (corridor_blocked<FAST, SM>(M, T, g, P, lane)) continue;
         bscore = cnt;
         best = g;
       } else {
         // nothing unblocked yet: any unblocked direction improves
-        if (corridor_blocked<FAST>(M, T, g, P, lane)) {
+        if (corridor_blocked<FAST, SM>(M, T, g, P, lane)) {
           if (best < 0) {
             bscore = nc + 1;
             best = g;
           }
           continue;
         }
-        bscore = tool_count<FAST>(M, T, g, P, nc, lane);
+        bscore = tool_count<FAST, SM>(M, T, g, P, nc, lane);
         best = g;
       }
       if (bscore == 0) break;
@@ -268,7 +287,7 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
 // the arm screen (tool count and corridor). If the search stops early,
 // *next receives the first direction index not searched and the result is
 // exact over the directions before it; *next = -1 when the search finished.
-template <bool FAST, class Cand>
+template <bool FAST, class Cand, bool SM = false>
 __device__ inline int2 best_direction_budget(const MapView& M, const ToolView& T, const Pt& P,
                                              const Cand& cand_of, int lane, int budget,
                                              int* next) {
@@ -278,7 +297,7 @@ __device__ inline int2 best_direction_budget(const MapView& M, const ToolView& T
   for (int gb = 0; gb < T.G && bscore != 0; gb += 32) {
     const bool cand = cand_of(T, gb + lane);
     unsigned mask = __ballot_sync(0xffffffffu, cand);
-    const unsigned arm_ok = __ballot_sync(0xffffffffu, cand && arm_clear<FAST>(M, T, gb + lane, P));
+    const unsigned arm_ok = __ballot_sync(0xffffffffu, cand && arm_clear<FAST, SM>(M, T, gb + lane, P));
     while (mask) {
       const int bit = __ffs(mask) - 1;
       const int g = gb + bit;
@@ -296,20 +315,20 @@ __device__ inline int2 best_direction_budget(const MapView& M, const ToolView& T
       }
       ++spent;
       if (bscore <= nc) {
-        const int cnt = tool_count<FAST>(M, T, g, P, bscore, lane);
+        const int cnt = tool_count<FAST, SM>(M, T, g, P, bscore, lane);
         if (cnt >= bscore) continue;
-        if (corridor_blocked<FAST>(M, T, g, P, lane)) continue;
+        if (corridor_blocked<FAST, SM>(M, T, g, P, lane)) continue;
         bscore = cnt;
         best = g;
       } else {
-        if (corridor_blocked<FAST>(M, T, g, P, lane)) {
+        if (corridor_blocked<FAST, SM>(M, T, g, P, lane)) {
           if (best < 0) {
             bscore = nc + 1;
             best = g;
           }
           continue;
         }
-        bscore = tool_count<FAST>(M, T, g, P, nc, lane);
+        bscore = tool_count<FAST, SM>(M, T, g, P, nc, lane);
         best = g;
       }
       if (bscore == 0) break;
