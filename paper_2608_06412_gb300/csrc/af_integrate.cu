@@ -210,8 +210,9 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   __shared__ float4 s_p[T];        // p, valid flag
   __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
   __shared__ int4 s_b0[T];         // first brick of the cube
-  __shared__ float s_bb[T];        // |p - q|^2 as rounded in single precision
-  __shared__ float s_ir[T];        // RN(1 / |p - q|), for the approximate cone test
+  // what the pair loop reads of a return, in one record: range |p - q|,
+  // RN(|p - q|^2), RN(1 / range) (for the approximate cone test), valid flag
+  __shared__ float4 s_pr[T];
   __shared__ uint32_t s_blk[T][NB];
   // Per return, axis and cube offset k (voxel rel + k - MR on that axis),
   // the rounded per-axis terms of the three sums the arithmetic needs --
@@ -248,8 +249,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     s_p[tid] = p;
     s_rel[tid] = rel;
     s_b0[tid] = b0;
-    s_bb[tid] = bb;
-    s_ir[tid] = ir;
+    s_pr[tid] = make_float4(__int_as_float(rel.w), bb, ir, p.w);
   }
   // The tile's brick tables; bricks created by this scan are looked up now.
   for (int e = tid; e < T * NB; e += NT) {
@@ -311,10 +311,9 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   }
 
   for (int t = 0; t < T; ++t) {
-    const float4 p = s_p[t];
-    if (p.w == 0.f) continue;  // uniform across the block
-    const float range = __int_as_float(s_rel[t].w);
-    const float bb = s_bb[t], ir = s_ir[t];
+    const float4 pr = s_pr[t];
+    if (pr.w == 0.f) continue;  // uniform across the block
+    const float range = pr.x, bb = pr.y, ir = pr.z;
 #pragma unroll
     for (int s = 0; s < OPT; ++s) {
       if (tid + s * NT >= C) break;
