@@ -208,8 +208,6 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   using S = CubeShape<W>;
   constexpr int C = S::C, NT = S::NT, OPT = S::OPT, BA = S::BA, NB = S::NB, MR = S::MR;
   __shared__ float4 s_p[T];        // p, valid flag
-  __shared__ int4 s_rel[T];        // domain-relative voxel of p, w = range bits
-  __shared__ int4 s_b0[T];         // first brick of the cube
   // what the pair loop reads of a return, in one record: range |p - q|,
   // RN(|p - q|^2), RN(1 / range) (for the approximate cone test), valid flag
   __shared__ float4 s_pr[T];
@@ -231,25 +229,37 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   if (tid < T) {
     const uint32_t k = r0 + tid;
     float4 p = k < n ? ret[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int4 rel = make_int4(0, 0, 0, 0), b0 = make_int4(0, 0, 0, 0);
-    float bb = 0.f, ir = 0.f;
+    float bb = 0.f, range = 0.f, ir = 0.f;
     if (p.w != 0.f) {
       const float b[3] = {__fsub_rn(p.x, q0), __fsub_rn(p.y, q1), __fsub_rn(p.z, q2)};
       bb = __fadd_rn(__fadd_rn(__fmul_rn(b[0], b[0]), __fmul_rn(b[1], b[1])), __fmul_rn(b[2], b[2]));
-      const float range = __fsqrt_rn(bb);
+      range = __fsqrt_rn(bb);
       ir = __frcp_rn(range);
-      int i[3];
-      voxel_index(p.x, M, &i[0]);
-      voxel_index(p.y, M, &i[1]);
-      voxel_index(p.z, M, &i[2]);
-      rel = make_int4(i[0] - M.dom_vox[0], i[1] - M.dom_vox[1], i[2] - M.dom_vox[2],
-                      __float_as_int(range));
-      b0 = make_int4((rel.x - MR) >> 3, (rel.y - MR) >> 3, (rel.z - MR) >> 3, 0);
     }
     s_p[tid] = p;
-    s_rel[tid] = rel;
-    s_b0[tid] = b0;
-    s_pr[tid] = make_float4(__int_as_float(rel.w), bb, ir, p.w);
+    s_pr[tid] = make_float4(range, bb, ir, p.w);
+  }
+  // Per-axis terms of every (return, axis, offset), each thread from the
+  // return itself (no barrier between the per-return and per-axis steps).
+  const float v = M.v, tau = M.tau, cone = M.cone_cos;
+  for (int e = tid; e < T * 3 * W; e += NT) {
+    const int t = e / (3 * W), ax = (e / W) % 3, k = e % W;
+    if (r0 + t >= n) continue;
+    const float4 p = ret[r0 + t];
+    if (p.w == 0.f) continue;
+    const float pa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+    int i;
+    voxel_index(pa, M, &i);
+    const int rel = i - M.dom_vox[ax];                 // box-relative voxel of p on this axis
+    const int j = rel + k - MR;                        // ... of the cube voxel
+    const float x = voxel_centre(j + M.dom_vox[ax], v);
+    const float a = __fsub_rn(x, pa), b = __fsub_rn(pa, q[ax]), c = __fsub_rn(x, q[ax]);
+    // brick offset within the tile's brick table (weight 1, BA, BA^2) in the
+    // high half, the voxel's slot bits within its brick in the low half
+    const int bk = (j >> 3) - ((rel - MR) >> 3);
+    const int code = ((bk * (ax == 0 ? 1 : (ax == 1 ? BA : BA * BA))) << 16) | ((j & 7) << (3 * ax));
+    s_term[t][ax][k] = make_float4(__fmul_rn(a, a), __fmul_rn(a, b), __fmul_rn(c, c),
+                                   __int_as_float(code));
   }
   // The tile's brick tables; bricks created by this scan are looked up now.
   for (int e = tid; e < T * NB; e += NT) {
@@ -275,27 +285,6 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
       }
     }
     s_blk[t][j] = blk;
-  }
-  __syncthreads();
-
-  // per-axis terms of every (return, axis, offset)
-  const float v = M.v, tau = M.tau, cone = M.cone_cos;
-  for (int e = tid; e < T * 3 * W; e += NT) {
-    const int t = e / (3 * W), ax = (e / W) % 3, k = e % W;
-    const float4 p = s_p[t];
-    if (p.w == 0.f) continue;
-    const int4 rel = s_rel[t];
-    const int4 b0 = s_b0[t];
-    const int j = (ax == 0 ? rel.x : (ax == 1 ? rel.y : rel.z)) + k - MR;  // box-relative voxel
-    const float pa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
-    const float x = voxel_centre(j + M.dom_vox[ax], v);
-    const float a = __fsub_rn(x, pa), b = __fsub_rn(pa, q[ax]), c = __fsub_rn(x, q[ax]);
-    // brick offset within the tile's brick table (weight 1, BA, BA^2) in the
-    // high half, the voxel's slot bits within its brick in the low half
-    const int bk = (j >> 3) - (ax == 0 ? b0.x : (ax == 1 ? b0.y : b0.z));
-    const int code = ((bk * (ax == 0 ? 1 : (ax == 1 ? BA : BA * BA))) << 16) | ((j & 7) << (3 * ax));
-    s_term[t][ax][k] = make_float4(__fmul_rn(a, a), __fmul_rn(a, b), __fmul_rn(c, c),
-                                   __int_as_float(code));
   }
   __syncthreads();
 
@@ -363,7 +352,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     if (s_p[t].w == 0.f) continue;
     const float p[3] = {s_p[t].x, s_p[t].y, s_p[t].z};
     int sv[3];
-    if (!band_sample(M, p, q, __int_as_float(s_rel[t].w), s, sv)) continue;
+    if (!band_sample(M, p, q, s_pr[t].x, s, sv)) continue;
     uint32_t blk, seen;
     const int h = find_slot(M, pack_brick(sv[0] >> 3, sv[1] >> 3, sv[2] >> 3), &blk, &seen);
     if (h < 0 || blk >= M.pool_blocks) continue;
