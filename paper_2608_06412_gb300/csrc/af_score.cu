@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2048 / (WARPS * 32))
 __host__ __device__ inline size_t staged_bytes(const ToolView& T) {
   return (size_t)T.G * 40 + (size_t)T.ntool * 8;
 }
-// Tables up to the default dynamic shared-memory limit are staged; larger ones
-// (many directions, long tools) are read through the read-only path.
-constexpr size_t kStagedMaxBytes = 48 * 1024;
+// Tables up to 100 KB are staged (two CTAs of 32 warps still fit an SM's
+// 228 KB); larger ones (many directions, long tools) are read through the
+// read-only path.
+constexpr size_t kStagedMaxBytes = 100 * 1024;
 
 // The staged form of k_score: a persistent CTA copies the direction table,
 // the arm offsets and every direction's tool runs into shared memory once,
@@ -239,7 +240,13 @@ cudaError_t launch_score(const MapView& M, const ToolView& T, const float* d_pts
   if (S.budget < 0 && S.work != nullptr && staged_bytes(T) <= kStagedMaxBytes) {
     const size_t smem = staged_bytes(T);
     int per = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {  // above the default dynamic shared-memory limit: opt in
+      e = cudaFuncSetAttribute(k_score_staged<kStagedWarps>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per, k_score_staged<kStagedWarps>, kStagedWarps * 32, smem);
     if (e != cudaSuccess) return e;
     const uint32_t need = (m + kStagedWarps - 1) / kStagedWarps;
