@@ -200,11 +200,11 @@ struct CubeShape {
   static constexpr int MR = W / 2;
 };
 
-// Tile `tile` (returns tile*T .. tile*T + T - 1) of one scan; called by the
-// whole CTA of CubeShape<W>::NT threads. W = 2m + 1 voxels per cube edge.
+// A tile of one scan: returns [r0, r1), r1 - r0 <= T; called by the whole
+// CTA of CubeShape<W>::NT threads. W = 2m + 1 voxels per cube edge.
 template <int W, int T>
-__device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret, uint32_t n,
-                               float q0, float q1, float q2, uint32_t frame, uint32_t tile) {
+__device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret, uint32_t r0,
+                               uint32_t r1, float q0, float q1, float q2, uint32_t frame) {
   using S = CubeShape<W>;
   constexpr int C = S::C, NT = S::NT, OPT = S::OPT, BA = S::BA, NB = S::NB, MR = S::MR;
   __shared__ float4 s_p[T];        // p, valid flag
@@ -220,15 +220,17 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   // the same as computing it whole.
   __shared__ float4 s_term[T][3][W];
 
-  if (__ldcg(&M.ctl->status) != 0u) return;  // sticky capacity error: skip the scan
-  __syncthreads();  // a previous tile of this CTA may still read the tables
+  // A latched error (sticky capacity error) skips the scan. Another CTA may
+  // latch one while this CTA runs, so the whole CTA decides together; the
+  // barrier also keeps a previous tile of this CTA from still reading the
+  // tables.
+  if (__syncthreads_or(__ldcg(&M.ctl->status) != 0u)) return;
   const int tid = threadIdx.x;
-  const uint32_t r0 = tile * T;
   const float q[3] = {q0, q1, q2};
 
   if (tid < T) {
     const uint32_t k = r0 + tid;
-    float4 p = k < n ? ret[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 p = k < r1 ? ret[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     float bb = 0.f, range = 0.f, ir = 0.f;
     if (p.w != 0.f) {
       const float b[3] = {__fsub_rn(p.x, q0), __fsub_rn(p.y, q1), __fsub_rn(p.z, q2)};
@@ -244,7 +246,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   const float v = M.v, tau = M.tau, cone = M.cone_cos;
   for (int e = tid; e < T * 3 * W; e += NT) {
     const int t = e / (3 * W), ax = (e / W) % 3, k = e % W;
-    if (r0 + t >= n) continue;
+    if (r0 + t >= r1) continue;
     const float4 p = ret[r0 + t];
     if (p.w == 0.f) continue;
     const float pa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
@@ -266,7 +268,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     const int t = e / NB, j = e % NB;
     const uint32_t k = r0 + t;
     uint32_t blk = kUnused;
-    if (k < n) {
+    if (k < r1) {
       blk = M.rtab[(size_t)k * NB + j];
       if (blk == kNoBlock) {
         const float4 p = ret[k];
@@ -362,8 +364,9 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
   }
 }
 
-// Tiles of 8 returns for the single-map path (measured against 12, 16, 20,
-// 26 and 32 on the pine stream: the finest grid balances the last wave best).
+// Tiles of 8 returns for the single-map path, one CTA each (measured against
+// 12, 16, 20, 26 and 32 on the pine stream, and against persistent CTAs that
+// each take an equal share of the returns: slower, 40.9 against 35.4 us).
 constexpr int kTile = 8;
 
 template <int W>
@@ -371,7 +374,8 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
                                                                 const float4* __restrict__ ret,
                                                                 uint32_t n, float q0, float q1,
                                                                 float q2, uint32_t frame) {
-  integrate_tile<W, kTile>(M, ret, n, q0, q1, q2, frame, blockIdx.x);
+  const uint32_t r0 = blockIdx.x * kTile;
+  integrate_tile<W, kTile>(M, ret, r0, min(r0 + kTile, n), q0, q1, q2, frame);
 }
 
 // Weight cap and bit view of one dirty brick; called by a CTA of 512 threads
@@ -543,8 +547,9 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate_batch(
   for (uint32_t tg = blockIdx.x; tg < total; tg += gridDim.x) {
     const int s = scene_of<1>(D, count, tg);
     const SceneDesc& d = D[s];
-    integrate_tile<W, T>(d.M, d.ret, d.n, d.P.r[0][3], d.P.r[1][3], d.P.r[2][3], d.frame,
-                         tg - d.tile_off);
+    const uint32_t r0 = (tg - d.tile_off) * T;
+    integrate_tile<W, T>(d.M, d.ret, r0, min(r0 + T, d.n), d.P.r[0][3], d.P.r[1][3],
+                         d.P.r[2][3], d.frame);
   }
 }
 
