@@ -29,6 +29,8 @@ Other lines, each with the oracle timed beside it on a bounded sample:
   --large --soft     the differentiable step on it (brick-sparse SDF view);
 and variants of the default line: --projective, --clamp-signed, --ring
 (the paper's yaw ring; with --points also --c2f), --score-split B.
+--noalloc times the allocation-free integration into a dense box of the
+pine map beside the map path's integration of the same frames.
 """
 from __future__ import annotations
 
@@ -81,6 +83,9 @@ def _args():
                     help="projective integration over an octahedral range image (Tab. 3 ablation)")
     ap.add_argument("--c2f", action="store_true",
                     help="--points --ring: coarse-to-fine search (20 degrees, +-24 degrees, 0.3 m)")
+    ap.add_argument("--noalloc", action="store_true",
+                    help="af_integrate_scan_noalloc into a dense box of the pine map, "
+                         "beside the map path's integration")
     ap.add_argument("--clamp-signed", action="store_true",
                     help="the [-tau, tau] clamp ablation (Tab. 4)")
     return ap.parse_args()
@@ -1219,6 +1224,87 @@ def run_points(args, local):
     return out
 
 
+def run_noalloc(args, local):
+    """The allocation-free integration (af_integrate_scan_noalloc) over the
+    pine stream into one caller-owned dense box of the whole map box (51 x 51
+    x 86 bricks: 115M voxels, 1.0 GB of words and flags), timed per frame
+    beside the map path's integration (af_integrate_scan) of the same frames;
+    the box's contents are checked against the map path's export at the end."""
+    import torch
+    from paper_2608_06412_gb300 import af, workload
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = workload.pine_stream()
+    nfr = args.warmup + args.steps
+    frames = _frames(W, 0, nfr)
+    cfg = W.af_config(**workload.BENCH_CAPS, clamp_signed=int(args.clamp_signed))
+    box_min = np.array(W.dom_min) * 8
+    box_dim = np.array(W.dom_bricks) * 8
+    count = int(np.prod(box_dim))
+    vox = torch.zeros(count, dtype=torch.int64, device=dev)
+    flags = torch.zeros(count, dtype=torch.uint8, device=dev)
+    d_xyz = [torch.from_numpy(f[0].pts).to(dev) for f in frames]
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    g = af.Map(cfg)
+
+    def timed(call):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i, k in enumerate(range(args.warmup, nfr)):
+            flush.zero_()
+            ev[i][0].record(stream)
+            call(k)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    for k in range(args.warmup):
+        af.integrate_scan_noalloc(cfg, d_xyz[k], frames[k][0].pose, box_min, box_dim, vox, flags)
+        g.integrate_scan(d_xyz[k], frames[k][0].pose)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    clocks.mark(True)
+    ms = timed(lambda k: af.integrate_scan_noalloc(cfg, d_xyz[k], frames[k][0].pose, box_min,
+                                                   box_dim, vox, flags))
+    ms_map = timed(lambda k: g.integrate_scan(d_xyz[k], frames[k][0].pose))
+    clocks.mark(False)
+    clk = clocks.stop()
+    # the box against the map path's voxels (both integrated every frame)
+    got = vox.cpu().numpy()
+    fl = flags.cpu().numpy()
+    ref = af.export_voxels(g.export_blocks())
+    rel = ref["ijk"] - box_min
+    at = (rel[:, 2] * box_dim[1] + rel[:, 1]) * box_dim[0] + rel[:, 0]
+    want = (ref["S"].astype(np.int64) << 20) | ref["w"].astype(np.int64)
+    want_fl = ref["cleared"] | (ref["occ"] << 1) | (ref["known"] << 2)
+    agree = bool((got[at] == want).all() and (fl[at] == want_fl).all() and
+                 np.count_nonzero(got) == np.count_nonzero(want))
+    returns = sum(int(d_xyz[k].shape[0]) for k in range(args.warmup, nfr))
+    total = sum(ms)
+    g.close()
+    return {
+        "metric": "allocation-free integration returns/s (af_integrate_scan_noalloc, dense box)",
+        "value": returns / (total / 1e3), "unit": "returns/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+        "data": "synthetic",
+        "config": {"workload": W.name, "returns_per_frame": W.params["n_returns"],
+                   "box_voxels": count, "box_bytes": count * 9,
+                   "clamp": "[-tau, tau]" if args.clamp_signed else "[0, tau]",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "max": float(max(ms))},
+        "map_path": {"returns_per_s": returns / (sum(ms_map) / 1e3),
+                     "latency_ms": {"p50": float(np.percentile(ms_map, 50)),
+                                    "p99": float(np.percentile(ms_map, 99))}},
+        "box_equals_map_path": agree,
+        "clocks": clk,
+        "cpu_baseline": None,
+    }
+
+
 def run_soft_large(args, local):
     """The differentiable step on the large map (3,000 frames at 1 cm, K = 256
     of G = 512, 1.5 m corridor): 100k surface points drawn from the stream's
@@ -1454,6 +1540,9 @@ def main():
         return
     if args.large:
         print(json.dumps(run_large(args, local)), flush=True)
+        return
+    if args.noalloc:
+        print(json.dumps(run_noalloc(args, local)), flush=True)
         return
     if ws > 1:
         import torch.distributed as dist
