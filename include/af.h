@@ -534,7 +534,10 @@ af_status af_profile_read(af_ctx *ctx, af_profile *out, int reset);
  * rules, same arithmetic, same weight cap and occupied / known rule; `cfg`'s
  * geometry and map box are used, its capacities are ignored) and ADDS it to
  * the box's current contents, so consecutive calls accumulate scans like a
- * map. The caller clears the box once before the first scan.
+ * map. The caller clears the box once before the first scan. The weight cap
+ * and the flags are applied to the voxels the scan touches (the cubes and
+ * cleared-band samples of its accepted returns); other voxels keep their
+ * words and flags, so the cost follows the scan, not the box.
  *  box_min, box_dim : the output box in absolute voxel indices; voxel
  *                     (x, y, z) is element ((z - z0) * dy + (y - y0)) * dx +
  *                     (x - x0). Contributions outside the box are not kept.

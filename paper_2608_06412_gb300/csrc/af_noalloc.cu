@@ -158,22 +158,63 @@ __global__ void __launch_bounds__(256) k_na_integrate(MapView M, const float4* _
   }
 }
 
-// Weight cap and occupied / known flags of every box voxel.
-__global__ void __launch_bounds__(256) k_na_finalize(MapView M, Box B, uint64_t count) {
-  for (uint64_t at = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; at < count;
-       at += (uint64_t)gridDim.x * blockDim.x) {
-    unsigned long long word = B.vox[at];
-    unsigned long long w = word & kWMask;
-    long long S = word_S(word);
-    if (w > M.w_cap) {
-      S = capped_S(S, M.w_cap, (long long)w);
-      w = M.w_cap;
-      B.vox[at] = make_word(S, w);
-    }
-    const unsigned cl = B.flags[at] & 1u;
-    const unsigned occ = (w >= 1 && S < (long long)M.rcq * (long long)w) ? 1u : 0u;
-    const unsigned kn = (w >= 1 || cl) ? 1u : 0u;
-    B.flags[at] = (uint8_t)(cl | (occ << 1) | (kn << 2));
+// Weight cap and occupied / known flags of box voxel `at`. Idempotent (a
+// capped weight is not capped again), so threads that reach the same voxel
+// through different returns write the same word and flags.
+__device__ inline void finalize_voxel(const MapView& M, const Box& B, size_t at) {
+  unsigned long long word = B.vox[at];
+  unsigned long long w = word & kWMask;
+  long long S = word_S(word);
+  if (w > M.w_cap) {
+    S = capped_S(S, M.w_cap, (long long)w);
+    w = M.w_cap;
+    B.vox[at] = make_word(S, w);
+  }
+  const unsigned cl = B.flags[at] & 1u;
+  const unsigned occ = (w >= 1 && S < (long long)M.rcq * (long long)w) ? 1u : 0u;
+  const unsigned kn = (w >= 1 || cl) ? 1u : 0u;
+  B.flags[at] = (uint8_t)(cl | (occ << 1) | (kn << 2));
+}
+
+// Weight cap and flags of every voxel this scan touched -- the cube voxels
+// and cleared-band samples of its accepted returns, enumerated as in
+// k_na_integrate -- after all of the scan's additions (a launch of its own).
+// Voxels the scan does not touch keep their words and flags.
+__global__ void __launch_bounds__(256) k_na_finalize(MapView M, const float4* __restrict__ scratch,
+                                                      uint32_t n, float q0, float q1, float q2,
+                                                      Box B) {
+  const int W = 2 * M.m + 1;
+  const uint64_t C = (uint64_t)W * W * W;
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t pairs = C * n;
+  const uint64_t band = (uint64_t)M.ns * n;
+  size_t at;
+  if (e < pairs) {
+    const uint32_t k = (uint32_t)(e / C);
+    const int o = (int)(e % C);
+    const float4 p = scratch[k];
+    if (p.w == 0.f) return;
+    int i[3];
+    if (!(voxel_index(p.x, M, &i[0]) && voxel_index(p.y, M, &i[1]) &&
+          voxel_index(p.z, M, &i[2])))
+      return;
+    const int jx = i[0] - M.dom_vox[0] + o % W - M.m;
+    const int jy = i[1] - M.dom_vox[1] + (o / W) % W - M.m;
+    const int jz = i[2] - M.dom_vox[2] + o / (W * W) - M.m;
+    if (box_index(B, jx, jy, jz, &at)) finalize_voxel(M, B, at);
+  } else if (e < pairs + band) {
+    const uint64_t f = e - pairs;
+    const uint32_t k = (uint32_t)(f / M.ns);
+    const int s = (int)(f % M.ns) + 1;
+    const float4 p4 = scratch[k];
+    if (p4.w == 0.f) return;
+    const float p[3] = {p4.x, p4.y, p4.z}, q[3] = {q0, q1, q2};
+    const float b0 = __fsub_rn(p[0], q0), b1 = __fsub_rn(p[1], q1), b2 = __fsub_rn(p[2], q2);
+    const float range =
+        __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(b0, b0), __fmul_rn(b1, b1)), __fmul_rn(b2, b2)));
+    int sv[3];
+    if (!band_sample(M, p, q, range, s, sv)) return;
+    if (box_index(B, sv[0], sv[1], sv[2], &at)) finalize_voxel(M, B, at);
   }
 }
 
@@ -262,11 +303,10 @@ extern "C" af_status af_integrate_scan_noalloc(const af_config* cfg, const float
     k_na_prepare<<<(n + 255) / 256, 256, 0, s>>>(M, d_xyz, n, P, scratch);
     const int W = 2 * M.m + 1;
     const uint64_t work = (uint64_t)n * W * W * W + (uint64_t)n * M.ns;
-    k_na_integrate<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(M, scratch, n, pose[3], pose[7],
-                                                                   pose[11], B);
+    const unsigned grid = (unsigned)((work + 255) / 256);
+    k_na_integrate<<<grid, 256, 0, s>>>(M, scratch, n, pose[3], pose[7], pose[11], B);
+    k_na_finalize<<<grid, 256, 0, s>>>(M, scratch, n, pose[3], pose[7], pose[11], B);
   }
-  const uint64_t blocks = std::min<uint64_t>((count + 255) / 256, 152ull * 64);
-  k_na_finalize<<<(unsigned)blocks, 256, 0, s>>>(M, B, count);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nfail(AF_ERR_CUDA, "af_integrate_scan_noalloc: launch failed: %s",
                                      cudaGetErrorString(e));
