@@ -176,6 +176,38 @@ __device__ inline int tool_count(const MapView& M, const ToolView& T, int g, con
   return total >= sat ? sat : total;
 }
 
+// Occupied tool voxels of directions g1 and g2 at point P, each saturated at
+// `sat`, counted side by side: lanes 0-15 walk g1's runs and lanes 16-31
+// g2's, two runs per lane per step, so both counts take the round trips of
+// one. Each count is what tool_count returns for its direction: every run is
+// counted until the running sum reaches `sat`.
+template <bool FAST, bool SM>
+__device__ inline int2 tool_count2(const MapView& M, const ToolView& T, int g1, int g2,
+                                   const Pt& P, int sat, int lane) {
+  const int half = lane >> 4, hl = lane & 15;
+  const int4 dt = dtab_entry(T, half ? g2 : g1, SM);
+  const int len1 = __shfl_sync(0xffffffffu, dt.y - dt.x, 0);
+  const int len2 = __shfl_sync(0xffffffffu, dt.y - dt.x, 16);
+  int t1 = 0, t2 = 0;
+  for (int b = 0; (b < len1 && t1 < sat) || (b < len2 && t2 < sat); b += 32) {
+    const bool mine = half ? (t2 < sat) : (t1 < sat);
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = dt.x + b + hl + 16 * j;
+      if (mine && r < dt.y) {
+        int len;
+        bool out = false;
+        c += __popcll(run_bits<FAST>(M.occ, M.occ_y, M.occ_z, M, load_run<FAST, SM>(T, r), P,
+                                     &len, &out));
+      }
+    }
+    t1 += __reduce_add_sync(0xffffffffu, half ? 0 : c);
+    t2 += __reduce_add_sync(0xffffffffu, half ? c : 0);
+  }
+  return make_int2(t1 >= sat ? sat : t1, t2 >= sat ? sat : t2);
+}
+
 // The three arm samples of direction g (one lane): clear iff none is
 // occupied or unknown. All nine loads are issued together (no short
 // circuit), so the screen costs two dependent round trips, not up to nine.
@@ -235,6 +267,11 @@ struct NormalFilter {
 // without candidates.
 // SM: the direction table, the arm offsets and the tool runs are staged in
 // shared memory (af_staged_tab).
+// Once a search has a best (score <= n_c), it takes the remaining arm-clear
+// candidates two at a time (tool_count2, FAST path): a long search waits on
+// half as many tool-count round trips. Both counts are saturated at the score
+// to beat before the pair and the pair is then decided in index order, so the
+// result is the sequential one.
 template <bool FAST, class Cand, bool SM = false>
 __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const Pt& P,
                                       const Cand& cand_of, int lane) {
@@ -255,6 +292,27 @@ __device__ inline int2 best_direction(const MapView& M, const ToolView& T, const
           bscore = nc + 1;
           best = g;
         }
+        continue;
+      }
+      const unsigned rest = mask & arm_ok;  // arm-clear candidates after g in this group
+      if (FAST && bscore <= nc && rest) {
+        // g and the next arm-clear candidate g2; the candidates between them
+        // are arm-blocked (n_c + 1) and cannot beat the best there is
+        const int bit2 = __ffs(rest) - 1;
+        const int g2 = gb + bit2;
+        mask &= ~((2u << bit2) - 1u);
+        const int2 c = tool_count2<FAST, SM>(M, T, g, g2, P, bscore, lane);
+        if (c.x < bscore && !corridor_blocked<FAST, SM>(M, T, g, P, lane)) {
+          bscore = c.x;
+          best = g;
+          if (bscore == 0) break;
+        }
+        // c.y saturated at the score before g: at or above any score after it
+        if (c.y < bscore && !corridor_blocked<FAST, SM>(M, T, g2, P, lane)) {
+          bscore = c.y;
+          best = g2;
+        }
+        if (bscore == 0) break;
         continue;
       }
       if (bscore <= nc) {
