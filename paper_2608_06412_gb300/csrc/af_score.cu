@@ -13,7 +13,9 @@
 //     at the score to beat, so counting stops as soon as the direction can
 //     no longer improve the point;
 //   * arm samples: three single-bit lookups (occupied or unknown blocks);
-//   * corridor: runs as above, any set bit blocks (__any_sync early exit).
+//   * corridor: runs as above, any set bit blocks (__any_sync early exit);
+//   * once a best exists, the arm-clear candidates are counted two at a time
+//     (half a warp each) and then decided in index order.
 // The best direction is the lowest-index minimum; a score of 0 ends the
 // point. Every early exit returns exactly what a full evaluation of every
 // candidate would (the score to beat only shrinks; ties keep the lower
