@@ -455,8 +455,8 @@ SCORE_BYTES_PER_POINT = 27.0
 # DRAM bytes (read + write) per launch from one ncu capture of the benchmark
 # (profiles/), valid only while the kernel's sources hash as recorded.
 TRAFFIC = {
-    "k_score": (10040192, {"paper_2608_06412_gb300/csrc/af_score.cu": "457faefbb2e206d2",
-                        "paper_2608_06412_gb300/csrc/af_score.cuh": "eca52daa51452d12",
+    "k_score": (10053760, {"paper_2608_06412_gb300/csrc/af_score.cu": "6a62001b84d4e0b3",
+                        "paper_2608_06412_gb300/csrc/af_score.cuh": "c56e18e35201957e",
                         "paper_2608_06412_gb300/csrc/af_internal.cuh": "ee1a297df623f66b"}),
 }
 
@@ -464,7 +464,7 @@ TRAFFIC = {
 # L2 traffic of k_score per launch (lts__t_sectors.sum x 32 B) from the same
 # capture (profiles/k_score_pine_stream.md), keyed like TRAFFIC; reported
 # against the measured L2 read peak beside the algorithmic fraction.
-L2_TRAFFIC = {"k_score": 358153200}
+L2_TRAFFIC = {"k_score": 375335248}
 
 
 def _l2(kernel: str, avg_ms: float, peak: float):
