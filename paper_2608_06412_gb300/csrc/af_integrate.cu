@@ -378,30 +378,34 @@ __global__ void __launch_bounds__(CubeShape<W>::NT) k_integrate(MapView M,
   integrate_tile<W, kTile>(M, ret, r0, min(r0 + kTile, n), q0, q1, q2, frame);
 }
 
-// Weight cap and bit view of one dirty brick; called by a CTA of 512 threads
-// (one voxel each). The x-row bytes come straight from the ballots; the y-
-// and z-row bytes of the occupied view are gathered from the brick's 512
-// bits in shared memory.
+// Weight cap and bit view of one dirty brick; called by a CTA of NT threads
+// (512 / NT voxels each, NT a multiple of 128). The x-row bytes come straight
+// from the ballots; the y- and z-row bytes of the occupied view are gathered
+// from the brick's 512 bits in shared memory.
+template <int NT>
 __device__ void bitview_brick(const MapView& M, uint32_t blk) {
+  static_assert(NT >= 128 && 512 % NT == 0, "bitview_brick: NT must divide 512, >= 128");
   __shared__ unsigned s_ob[16];
   if (!check_index(blk < M.pool_blocks, M.ctl)) return;  // uniform over the CTA
-  const int l = threadIdx.x;
-  const int lane = l & 31, wi = l >> 5;
+  const int lane = threadIdx.x & 31;
   unsigned char* occ = reinterpret_cast<unsigned char*>(M.occ);
   unsigned char* known = reinterpret_cast<unsigned char*>(M.known);
   const size_t row_bytes = (size_t)M.row_words * 8;
   const uint64_t key = M.bkey[blk];
   const uint32_t bx = (uint32_t)(key & 0x1FFFFF), by = (uint32_t)((key >> 21) & 0x1FFFFF),
                  bz = (uint32_t)(key >> 42);
-  {
-    unsigned long long* wp = M.vox + (size_t)blk * kBrickVox + l;
-    unsigned long long word = *wp;
-    unsigned long long w = word & kWMask;
-    long long S = word_S(word);
+  unsigned long long word[512 / NT];
+#pragma unroll
+  for (int s = 0; s < 512 / NT; ++s) word[s] = M.vox[(size_t)blk * kBrickVox + threadIdx.x + s * NT];
+#pragma unroll
+  for (int s = 0; s < 512 / NT; ++s) {
+    const int l = threadIdx.x + s * NT, wi = l >> 5;
+    unsigned long long w = word[s] & kWMask;
+    long long S = word_S(word[s]);
     if (w > M.w_cap) {
       S = capped_S(S, M.w_cap, (long long)w);  // |S| < 2^40, w_cap < 2^20: no overflow
       w = M.w_cap;
-      *wp = make_word(S, w);
+      M.vox[(size_t)blk * kBrickVox + l] = make_word(S, w);
     }
     const bool o = w >= 1 && S < (long long)M.rcq * (long long)w;
     const bool cl = (M.cleared[blk * 16 + wi] >> lane) & 1u;
@@ -420,6 +424,7 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
     }
   }
   __syncthreads();
+  const int l = threadIdx.x;
   if (l < 128) {
     // l < 64: the y row at (x, z) = (l & 7, l >> 3); else the z row at (x, y)
     const int x = l & 7, c = (l >> 3) & 7;
@@ -445,10 +450,14 @@ __device__ void bitview_brick(const MapView& M, uint32_t blk) {
   __syncthreads();  // s_ob is rewritten for the CTA's next brick
 }
 
-// Weight cap and bit view of every brick touched by the scan.
-__global__ void __launch_bounds__(512) k_bitview(MapView M) {
+// CTAs of 256 threads (two voxels each): eight per SM, so a scan's dirty
+// bricks (about a thousand per pine frame) take one brick per CTA.
+constexpr int kBitviewThreads = 256;
+
+__global__ void __launch_bounds__(kBitviewThreads, 2048 / kBitviewThreads) k_bitview(MapView M) {
   const uint32_t count = __ldcg(&M.ctl->dirty_count);
-  for (uint32_t d = blockIdx.x; d < count; d += gridDim.x) bitview_brick(M, M.dirty[d]);
+  for (uint32_t d = blockIdx.x; d < count; d += gridDim.x)
+    bitview_brick<kBitviewThreads>(M, M.dirty[d]);
 }
 
 // Per-voxel flags of allocated bricks for export: bit0 cleared, bit1
@@ -506,7 +515,7 @@ cudaError_t launch_cube(const MapView& M, uint32_t n, const float pose[16], cons
 }
 
 cudaError_t launch_bitview(const MapView& M, int num_sms, cudaStream_t stream) {
-  k_bitview<<<num_sms * 4, 512, 0, stream>>>(M);
+  k_bitview<<<num_sms * (2048 / kBitviewThreads), kBitviewThreads, 0, stream>>>(M);
   return cudaGetLastError();
 }
 
@@ -563,7 +572,7 @@ __global__ void __launch_bounds__(512) k_bitview_batch(const BatchHdr* __restric
     const uint32_t cnt = __ldcg(&M.ctl->dirty_count);
     // this CTA takes the global indices acc + r with (acc + r) % grid == blockIdx.x
     for (uint32_t r = (blockIdx.x + grid - acc % grid) % grid; r < cnt; r += grid)
-      bitview_brick(M, M.dirty[r]);
+      bitview_brick<512>(M, M.dirty[r]);
     acc += cnt;
   }
 }
