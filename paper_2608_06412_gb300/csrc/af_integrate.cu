@@ -72,12 +72,14 @@ __device__ uint32_t insert_brick(const MapView& M, uint64_t key, uint32_t* slot,
 // dirty list once per scan: the stamp decides which thread appends. Appends
 // are aggregated over the threads of the same map (`group`) that call
 // together: one counter atomic per map and call instead of one per brick.
-// Threads of different maps may call together (batched ticks), and each
-// map's appends go through its own counter.
+// Threads of different maps may call together (batched ticks, MULTI), and
+// each map's appends go through its own counter; without MULTI every calling
+// thread belongs to the same map.
+template <bool MULTI>
 __device__ inline void mark_dirty(const MapView& M, uint32_t h, uint32_t blk, uint32_t frame,
                                   uint32_t seen, uint32_t group) {
   const unsigned active = __activemask();
-  const unsigned same = __match_any_sync(active, group);
+  const unsigned same = MULTI ? __match_any_sync(active, group) : active;
   const bool need = seen != frame && atomicExch(&M.slots[h].stamp, frame) != frame;
   const unsigned nm = __ballot_sync(active, need) & same;
   const int lane = threadIdx.x & 31;
@@ -103,8 +105,10 @@ __device__ inline void cube_bricks(const MapView& M, const int rel[3], int b0[3]
 // pose transform is recomputed by every thread of a return (cheap next to an
 // L2 probe); slot 0 also writes the return's world position for k_integrate.
 // All 32 lanes of the warp call this together; `group` tells lanes of
-// different maps apart (0 for a single map), `e` is the thread's slot index
-// within its map's scan (slots past the scan are inactive).
+// different maps apart (MULTI; without it every lane is of one map), `e` is
+// the thread's slot index within its map's scan (slots past the scan are
+// inactive).
+template <bool MULTI>
 __device__ void alloc_slot(const MapView& M, const float* __restrict__ xyz, uint32_t n,
                            const Pose& P, float4* __restrict__ ret, uint32_t frame, uint32_t e,
                            uint32_t group) {
@@ -121,7 +125,7 @@ __device__ void alloc_slot(const MapView& M, const float* __restrict__ xyz, uint
     valid = prepare_return(M, P, xyz[3 * k], xyz[3 * k + 1], xyz[3 * k + 2], p, &range, rel);
     if (j == 0) ret[k] = make_float4(p[0], p[1], p[2], valid ? 1.f : 0.f);
   }
-  const unsigned same_map = __match_any_sync(0xffffffffu, group);
+  const unsigned same_map = MULTI ? __match_any_sync(0xffffffffu, group) : 0xffffffffu;
   const unsigned acc = __ballot_sync(0xffffffffu, valid && j == 0) & same_map;
   if (lane == __ffs(same_map) - 1 && acc)
     atomicAdd(&M.ctl->returns_accepted, (unsigned long long)__popc(acc));
@@ -155,12 +159,13 @@ __device__ void alloc_slot(const MapView& M, const float* __restrict__ xyz, uint
   const unsigned act = __ballot_sync(0xffffffffu, ins);
   uint32_t blk = kNoBlock;
   if (ins) {
-    const unsigned peers = __match_any_sync(act, key) & __match_any_sync(act, group);
+    const unsigned peers =
+        __match_any_sync(act, key) & (MULTI ? __match_any_sync(act, group) : act);
     const int leader = __ffs(peers) - 1;
     if (lane == leader) {
       uint32_t h, seen;
       blk = insert_brick(M, key, &h, &seen);
-      if (blk != kNoBlock) mark_dirty(M, h, blk, frame, seen, group);
+      if (blk != kNoBlock) mark_dirty<MULTI>(M, h, blk, frame, seen, group);
     }
     blk = __shfl_sync(peers, blk, leader);
   }
@@ -172,7 +177,7 @@ __device__ void alloc_slot(const MapView& M, const float* __restrict__ xyz, uint
 __global__ void __launch_bounds__(256) k_alloc(MapView M, const float* __restrict__ xyz,
                                                 uint32_t n, Pose P, float4* __restrict__ ret,
                                                 uint32_t frame) {
-  alloc_slot(M, xyz, n, P, ret, frame, blockIdx.x * blockDim.x + threadIdx.x, 0u);
+  alloc_slot<false>(M, xyz, n, P, ret, frame, blockIdx.x * blockDim.x + threadIdx.x, 0u);
 }
 
 // Approximate square root (MUFU reciprocal square root), relative error well
@@ -283,7 +288,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
         uint32_t val, seen;
         const int h = find_slot(M, pack_brick(b0[0] + bx, b0[1] + by, b0[2] + bz), &val, &seen);
         blk = (h >= 0 && val < M.pool_blocks) ? val : kNoBlock;
-        if (blk != kNoBlock) mark_dirty(M, (uint32_t)h, blk, frame, seen, 0u);
+        if (blk != kNoBlock) mark_dirty<false>(M, (uint32_t)h, blk, frame, seen, 0u);
       }
     }
     s_blk[t][j] = blk;
@@ -360,7 +365,7 @@ __device__ void integrate_tile(const MapView& M, const float4* __restrict__ ret,
     if (h < 0 || blk >= M.pool_blocks) continue;
     const int l = (sv[0] & 7) | ((sv[1] & 7) << 3) | ((sv[2] & 7) << 6);
     atomicOr(M.cleared + blk * 16 + (l >> 5), 1u << (l & 31));
-    mark_dirty(M, (uint32_t)h, blk, frame, seen, 0u);
+    mark_dirty<false>(M, (uint32_t)h, blk, frame, seen, 0u);
   }
 }
 
@@ -543,7 +548,7 @@ __global__ void __launch_bounds__(256) k_alloc_batch(const BatchHdr* __restrict_
     const bool act = e < total;
     const int s = act ? scene_of<0>(D, count, e) : 0;
     const SceneDesc& d = D[s];
-    alloc_slot(d.M, d.xyz, act ? d.n : 0u, d.P, d.ret, d.frame, act ? e - d.alloc_off : 0u,
+    alloc_slot<true>(d.M, d.xyz, act ? d.n : 0u, d.P, d.ret, d.frame, act ? e - d.alloc_off : 0u,
                act ? (uint32_t)s : 0xFFFFFFFFu);
   }
 }
