@@ -334,7 +334,7 @@ def test_projective_concentric_sphere():
             if oracle.octa_bin(xs[k], N) in hit and R - dist[k] >= -tau + 1e-4:
                 want.add(tuple(j[k]))
             elif oracle.octa_bin(xs[k], N) in hit and R - dist[k] > -tau - 1e-4:
-                want.add(None)                              # too close to the cut to judge
+                want.add(None)                              # too close to the cut to decide
     got_set = {tuple(x) for x in e["ijk"]}
     want.discard(None)
     assert want <= got_set and len(got_set - want) < 0.01 * len(got_set)
